@@ -1,0 +1,385 @@
+"""Benchmark: recurrent arc consistency (Eq. 1) to its fixpoint on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--impl ours|reference]
+
+One step = one enforcement to the fixpoint (every sweep of the hot path:
+support test, AND-reduction over C_x, change and wipe-out flags, the
+device-side fixpoint loop) of one batch of domain states of the workload,
+through the C ABI, with the network already resident on the device.  The L2
+cache is flushed between timed steps (outside the timed events); each step is
+timed with CUDA events on the stream it runs on.
+
+Prints ONE JSON line.  Under torchrun every rank runs its own replica of the
+workload (the fixpoints are independent), `value` is the units of all ranks
+over the slowest rank's time.  `--impl reference` times the CPU oracle (the
+literal Eq. 1 recurrence) on the same workload instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RAC fixpoints/s and relation-bits/s vs plain GPU RAC; % of HBM/tensor roofline"
+
+# Synthetic workloads (random binary CSPs of the experiments' model, Sec. 5:
+# every pair of variables constrained with probability `density`, every value
+# pair of a constraint disallowed with probability `tightness`).
+WORKLOADS = {
+    "dense_n500_d20": dict(n=500, d=20, density=1.0, tightness=0.35, states="full", n_states=1),
+    "rb_n50_d10": dict(n=50, d=10, density=0.5, tightness=0.3, states="full", n_states=1),
+    "dense_n2000_d32": dict(n=2000, d=32, density=0.9, tightness=0.3, states="full", n_states=1),
+    "n1000_d24_b32": dict(n=1000, d=24, density=0.8, tightness=0.3, states="assign",
+                          n_states=32),
+}
+DEFAULT_WORKLOAD = "dense_n500_d20"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--flags", type=int, default=0, help="enforce flags (1 stop, 2 incremental)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def make_inputs(wl, seed):
+    import racgen
+    spec = WORKLOADS[wl]
+    net = racgen.random_network(seed, 0, spec["n"], spec["d"], spec["density"], spec["tightness"])
+    if spec["states"] == "full":
+        doms = np.tile(racgen.full_domain(spec["n"], spec["d"]), (spec["n_states"], 1))
+    else:
+        doms = np.array([racgen.assignment_state(seed, 0, s, spec["n"], spec["d"])
+                         for s in range(spec["n_states"])])
+    return spec, net, doms
+
+
+def config_of(wl, spec, net, flush):
+    return {"workload": wl, "n": spec["n"], "d": spec["d"], "density": spec["density"],
+            "tightness": spec["tightness"], "constraints": net.m, "states": spec["n_states"],
+            "state_kind": spec["states"], "seed_generated": True,
+            "l2": "flushed between timed steps" if flush else "inputs larger than L2"}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2407_11388_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(wl):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = data.get(wl)
+    if not ent or ent.get("source_hash") != source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """NVML samples of SM clock and throttle reasons while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.reasons = set()
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._t = None
+        self.error = None
+
+    def __enter__(self):
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self._h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
+            self._nv = pynvml
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+        except Exception as e:  # noqa: BLE001 - clocks are reported, not required
+            self.error = str(e)
+        return self
+
+    def _run(self):
+        nv = self._nv
+        names = {
+            "hw_slowdown": getattr(nv, "nvmlClocksEventReasonHwSlowdown", 0x8),
+            "hw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonHwThermalSlowdown", 0x40),
+            "sw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonSwThermalSlowdown", 0x20),
+            "sw_power_cap": getattr(nv, "nvmlClocksEventReasonSwPowerCap", 0x4),
+            "hw_power_brake_slowdown": getattr(nv, "nvmlClocksEventReasonHwPowerBrakeSlowdown", 0x80),
+        }
+        while not self._stop.is_set():
+            try:
+                self.samples.append(nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM))
+                fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                    nv.nvmlDeviceGetCurrentClocksThrottleReasons
+                r = fn(self._h)
+                for k, bit in names.items():
+                    if r & bit:
+                        self.reasons.add(k)
+            except Exception as e:  # noqa: BLE001
+                self.error = str(e)
+                break
+            time.sleep(0.005)
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=2)
+
+    def summary(self):
+        med = float(np.median(self.samples)) if self.samples else None
+        out = {"sm_mhz": med, "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons),
+               "samples": len(self.samples)}
+        if self.error and not self.samples:
+            out["error"] = self.error
+        return out
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(spec, net, doms, budget_s=15.0):
+    """The oracle (literal Eq. 1 sweeps, OpenMP over variables) on a bounded
+    sample of the same workload: whole fixpoints of the first states until the
+    time budget is used."""
+    import oracle
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    done = 0
+    sweeps = 0
+    while True:
+        s = done % doms.shape[0]
+        _, it, _ = oracle.rac(spec["n"], spec["d"], net.scope, net.rel, doms[s], threads=threads)
+        done += 1
+        sweeps += it
+        el = time.perf_counter() - t0
+        if el >= budget_s or done >= 1000:
+            break
+    return {"value": done / el, "unit": "fixpoints/s", "cores": threads, "kind": "oracle",
+            "sample": "%d whole fixpoints (%d sweeps) of this workload's states, %.1f s" % (
+                done, sweeps, el)}, sweeps / done
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    spec, net, doms = make_inputs(args.workload, args.seed)
+    import oracle
+    threads = os.cpu_count() or 1
+    # one step = one whole fixpoint of one state; cap the steps to a few minutes
+    t0 = time.perf_counter()
+    oracle.rac(spec["n"], spec["d"], net.scope, net.rel, doms[0], threads=threads)
+    est = time.perf_counter() - t0
+    steps = max(1, min(args.steps, int(150.0 / max(est, 1e-6))))
+    warm = max(0, min(args.warmup, 3))
+    for w in range(warm):
+        oracle.rac(spec["n"], spec["d"], net.scope, net.rel, doms[w % doms.shape[0]], threads=threads)
+    sweeps = 0
+    t0 = time.perf_counter()
+    for s in range(steps):
+        _, it, _ = oracle.rac(spec["n"], spec["d"], net.scope, net.rel, doms[s % doms.shape[0]],
+                              threads=threads)
+        sweeps += it
+    el = time.perf_counter() - t0
+    value = steps / el
+    line = {"metric": METRIC, "value": value, "unit": "fixpoints/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": steps, "warmup": warm,
+            "ms_per_step": 1000.0 * el / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": config_of(args.workload, spec, net, True),
+            "relation_bits_per_s": float(net.m) * spec["d"] ** 2 * sweeps / el,
+            "cpu_baseline": {"value": value, "unit": "fixpoints/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": "%d whole fixpoints (requested %d steps)" % (steps, args.steps)},
+            "e2e": {"value": value, "unit": "fixpoints/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2407_11388_b300 as rac
+
+    world, rank, local = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    spec, net_np, doms = make_inputs(args.workload, args.seed)
+    n, d, B = spec["n"], spec["d"], spec["n_states"]
+    net = rac.Network(n, d, net_np.scope, net_np.rel)
+    stream = torch.cuda.current_stream()
+    din = torch.from_numpy(doms.reshape(-1).view(np.int32)).to(dev)
+    dout = torch.empty_like(din)
+    it = torch.empty(B, dtype=torch.int32, device=dev)
+    st = torch.empty(B, dtype=torch.int32, device=dev)
+    offs = np.arange(B, dtype=np.int64) * n
+    items = np.zeros(B, np.int32)
+
+    def step():
+        if B == 1:
+            rac.enforce(net, din, dout, it, st, flags=args.flags, stream=stream)
+        else:
+            rac.enforce_batch([net], items, offs, din, dout, it, st, flags=args.flags,
+                              stream=stream)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+    for _ in range(max(3, args.warmup)):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    sweeps = int(it.max().item())
+    total_sweeps = int(it.sum().item())
+    statuses = st.cpu().numpy()
+
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        w0 = time.perf_counter()
+        for i in range(K):
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+            flush.zero_()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+    if pg:
+        pg.barrier()
+    dev_ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+    if pg:
+        t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        dev_ms = float(t.item())
+    per_step_s = dev_ms / 1000.0 / K
+    fix_per_s = world * B / per_step_s
+    bits_per_fix = float(net_np.m) * d * d * total_sweeps / B  # m d^2 bits per plain sweep
+    value = fix_per_s
+
+    # end to end through the host entry point (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(doms.reshape(-1).view(np.int32).copy()).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        hit = torch.empty(B, dtype=torch.int32).pin_memory()
+        hst = torch.empty(B, dtype=torch.int32).pin_memory()
+        L = rac.lib()
+        sh = stream.cuda_stream
+
+        def host_step():
+            rc = L.rac_enforce_host(net.handle, B, host_in.data_ptr(), host_out.data_ptr(),
+                                    hit.data_ptr(), hst.data_ptr(), 0, args.flags, sh)
+            if rc != 0:
+                raise rac.RacError(rc, rac.last_error())
+
+        for _ in range(3):
+            host_step()
+        Ke = max(10, min(K, 500))
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            host_step()
+        el = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            el = float(t.item())
+        if not np.array_equal(host_out.numpy().view(np.uint32), dout.cpu().numpy().view(np.uint32)):
+            raise SystemExit("host entry point disagrees with the device entry point")
+        e2e = {"value": world * B * Ke / el, "unit": "fixpoints/s",
+               "h2d_bytes_per_step": int(B * n * 4), "d2h_bytes_per_step": int(B * n * 4 + B * 8),
+               "steps": Ke}
+
+    peaks = measured_peaks()
+    hbm_peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6400.0
+    # a launch reads each relation once per sweep, for all its states at once
+    alg_bytes_per_launch = float(net_np.m) * d * d / 8.0 * sweeps
+    achieved = alg_bytes_per_launch / per_step_s / 1e9
+    traffic = traffic_from_profiles(args.workload)
+    clocks = clk.summary()
+
+    line = {"metric": METRIC, "value": value, "unit": "fixpoints/s", "n_gpus": world,
+            "steps": K, "warmup": max(3, args.warmup), "ms_per_step": per_step_s * 1000.0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded random binary CSP, generated in-process)",
+            "config": config_of(args.workload, spec, net_np, True),
+            "relation_bits_per_s": world * bits_per_fix * B / per_step_s,
+            "sweeps_per_fixpoint": total_sweeps / B,
+            "status_counts": {str(k): int(v) for k, v in zip(*np.unique(statuses, return_counts=True))},
+            "wall_s_timed_region": wall,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": traffic,
+                         "peak_source": "measured" if peaks else "fallback",
+                         "kernel": "rac_bits_kernel",
+                         "alg_bytes_per_launch": alg_bytes_per_launch},
+            "clocks": clocks,
+            "gpu_launches": K,
+            "e2e": e2e}
+    if rank == 0 and not args.no_cpu_baseline:
+        cb, _ = cpu_baseline(spec, net_np, doms)
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    net.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

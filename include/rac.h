@@ -1,0 +1,194 @@
+/*
+ * rac.h -- C ABI of the B300 arc-consistency library (librac.so).
+ *
+ * The library enforces arc consistency on binary constraint networks with
+ * the recurrent formulation of "Paralleling and Accelerating Arc Consistency
+ * Enforcement with Recurrent Tensor Computations" (arXiv 2407.11388):
+ *
+ *   Eq. 1 (Sec. 3):  Dt^(0) = {},
+ *                    Dt^(k) = Dt^(k-1) U {(x,a) | exists y: c_xy|_(x,a) is a
+ *                                          subset of Dt^(k-1)},
+ *
+ * swept synchronously until a sweep removes nothing; the result D \ Dt^(K) is
+ * D_ac, the union of every arc-consistent subset of D (Sec. 3, Prop. 1).  In
+ * tensor form (Sec. 4, Fig. 1, Algorithm 1 `tensorRevise`) each sweep counts
+ * Sup_xy[a] = sum_b R_xy[a][b] * D[y][b] for every value (x,a) and every
+ * constraint c_xy on x, and keeps (x,a) only if every count is non-zero.
+ *
+ * Conventions shared by every entry point:
+ *  - A network has n_vars variables, all with values 0..d-1, 1 <= d <= 32.
+ *  - A domain state is n_vars uint32 words; bit a of word x is set iff value
+ *    a is in dom(x).  Bits >= d must be zero.
+ *  - Supports are taken inside the domain passed in (the paper's listing
+ *    multiplies the constraint tensor by the domain mask, Appendix E): a
+ *    value with no allowed partner left in the neighbour's domain is removed.
+ *  - `iterations` counts every sweep executed, including the last sweep,
+ *    which removes nothing (the loop trips of Algorithm 1).  A domain that is
+ *    already arc consistent takes 1 sweep.
+ *  - Per-state results: status RAC_OK (fixpoint, no empty domain),
+ *    RAC_WIPEOUT (some domain of the result is empty), RAC_ETIMEOUT (the
+ *    sweep cap was reached first) or RAC_EBARRIER (a device-side wait gave
+ *    up; the domains are then unspecified).
+ *  - Functions return RAC_OK or a negative error code; on error nothing has
+ *    been launched and rac_last_error() describes the cause.  No C++
+ *    exception crosses this boundary.
+ *  - Device pointers are plain CUDA device addresses (for example the
+ *    data_ptr() of a torch tensor on the same device).  `stream` is a
+ *    cudaStream_t; NULL means the legacy default stream.  Work is enqueued on
+ *    `stream` and the call returns without waiting unless stated otherwise.
+ */
+#ifndef RAC_H
+#define RAC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RAC_API __attribute__((visibility("default")))
+#else
+#define RAC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rac_network rac_network;
+typedef struct CUstream_st *rac_stream_t; /* same type as cudaStream_t */
+typedef int32_t rac_status;
+
+/* Return and per-state status codes. */
+#define RAC_OK 0
+#define RAC_WIPEOUT 1
+#define RAC_EINVAL (-1)
+#define RAC_ENOMEM (-2)
+#define RAC_ECUDA (-3)
+#define RAC_ETIMEOUT (-4)
+#define RAC_EBARRIER (-5)
+#define RAC_ENOTSUP (-6)
+
+/* layout_flags of rac_create_network */
+#define RAC_LAYOUT_BITS 0x1u /* bit-packed relation slabs (always built) */
+
+/* flags of the enforce calls */
+#define RAC_STOP_ON_WIPEOUT 0x1u /* end after the first sweep that leaves a domain
+                                    empty and return that sweep's state
+                                    (Algorithm 1 throws there; the listing of
+                                    Appendix E returns None there).  Default: run
+                                    Eq. 1 to its fixpoint. */
+#define RAC_INCREMENTAL 0x2u     /* Proposition 2: sweep k >= 2 re-reads only
+                                    the relation slabs touching a variable whose
+                                    domain changed in sweep k-1.  The result,
+                                    every sweep's removals and the sweep count
+                                    are identical to the plain recurrence. */
+
+/*
+ * rac_create_network -- copy a network into device memory in the library's
+ * own layout.
+ *
+ *  n_vars     number of variables, 1 <= n_vars <= 2,000,000.
+ *  d          domain size, 1 <= d <= 32.
+ *  n_cons     number of constraints (>= 0).
+ *  scope      HOST, n_cons x 2 int32: constraint c has scope (scope[2c],
+ *             scope[2c+1]); both in [0, n_vars), different, and each
+ *             unordered pair at most once (several relations on one pair
+ *             would have to be intersected first).
+ *  rel_bits   HOST, n_cons x d uint32: word a of constraint c has bit b set
+ *             iff the pair (first variable = a, second variable = b) is
+ *             allowed, i.e. R_xy[a][b] of the paper's relation tensor
+ *             Cons[x][y][a][b] (Algorithm 2 `init`).  R_yx is R_xy
+ *             transposed (one relation per scope, Sec. 2).  Bits >= d must be
+ *             zero.  Variables with no constraint between them are
+ *             unconstrained (only real constraints are in C_x).
+ *  layout_flags  RAC_LAYOUT_BITS (0 means the same).
+ *  out        receives the network handle.
+ *
+ * The library keeps its own copy; the host arrays may be freed on return.
+ * The call synchronises with the device (allocation and upload).
+ * Errors: RAC_EINVAL (bad argument, duplicate pair, bit >= d set),
+ * RAC_ENOMEM (host or device allocation failed), RAC_ECUDA.
+ */
+RAC_API rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const int32_t *scope,
+                              const uint32_t *rel_bits, uint32_t layout_flags,
+                              rac_network **out);
+
+/* rac_destroy -- free a network and all device memory it owns (NULL-safe).
+ * The caller must make sure no enforcement on it is still running. */
+RAC_API void rac_destroy(rac_network *net);
+
+/*
+ * rac_enforce -- arc consistency for one domain state (Eq. 1 to its
+ * fixpoint, one persistent kernel launch, no host round trip per sweep).
+ *
+ *  dom_in      DEVICE, n_vars words: the input domain D.
+ *  dom_out     DEVICE, n_vars words: receives D_ac (or the state at which
+ *              enforcement stopped).  dom_out == dom_in is allowed; any
+ *              other overlap is not.
+ *  iterations  DEVICE int32: sweeps executed.
+ *  status      DEVICE int32: per-state status (see above).
+ *  max_sweeps  sweep cap; <= 0 means none (Prop. 1 bounds the sweeps by
+ *              |D| + 1 anyway).
+ *  flags       RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL.
+ *
+ * Scratch memory comes from a per-(network, stream) workspace that the first
+ * call on a stream allocates; calls on one stream reuse it, so capture such
+ * calls in a CUDA graph only after one call on that stream has run.
+ * Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA.
+ */
+RAC_API rac_status rac_enforce(const rac_network *net, const uint32_t *dom_in, uint32_t *dom_out,
+                       int32_t *iterations, int32_t *status, int32_t max_sweeps, uint32_t flags,
+                       rac_stream_t stream);
+
+/*
+ * rac_enforce_batch -- many independent (network, domain state) items.
+ *
+ *  nets          HOST array of network handles.
+ *  n_nets        entries in nets.
+ *  n_items       number of items (>= 0).
+ *  item_net      HOST, n_items int32: index into nets of each item.
+ *  item_dom_off  HOST, n_items int64: word offset of the item's state in
+ *                dom_in and dom_out (the state occupies that network's
+ *                n_vars words).  Offsets may be in any order; the states of
+ *                different items must not overlap.
+ *  dom_in, dom_out  DEVICE word arrays (dom_out == dom_in allowed).
+ *  iterations, status  DEVICE, n_items int32 each.
+ *  max_sweeps, flags, stream  as for rac_enforce.
+ *
+ * Items on the same network are enforced together so that each relation
+ * slab is read once per sweep for all of them.
+ * Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA.
+ */
+RAC_API rac_status rac_enforce_batch(const rac_network *const *nets, int32_t n_nets, int32_t n_items,
+                             const int32_t *item_net, const int64_t *item_dom_off,
+                             const uint32_t *dom_in, uint32_t *dom_out, int32_t *iterations,
+                             int32_t *status, int32_t max_sweeps, uint32_t flags,
+                             rac_stream_t stream);
+
+/*
+ * rac_enforce_host -- rac_enforce on HOST buffers: copies the n_states
+ * states (n_states x n_vars words, state s at word s*n_vars) to the device,
+ * enforces them as one batch on `net`, copies domains, iterations and status
+ * back, and waits for `stream` before returning.  Pinned host memory makes
+ * the copies asynchronous-capable; pageable memory also works.
+ * Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA.
+ */
+RAC_API rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint32_t *dom_in,
+                            uint32_t *dom_out, int32_t *iterations, int32_t *status,
+                            int32_t max_sweeps, uint32_t flags, rac_stream_t stream);
+
+/*
+ * rac_network_info -- describe a network: writes up to n_info int64 values
+ * to info, in this order: n_vars, d, n_cons, relation-slab bytes on the
+ * device, number of relation slabs, rows per slab, words per stored relation
+ * row group (d rounded up to a multiple of 4).  Returns the number written.
+ */
+RAC_API int32_t rac_network_info(const rac_network *net, int64_t *info, int32_t n_info);
+
+/* rac_last_error -- message for the last failing call on this host thread
+ * ("" if none).  The string stays valid until the next call on the thread. */
+RAC_API const char *rac_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RAC_H */

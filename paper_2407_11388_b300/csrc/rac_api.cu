@@ -1,0 +1,512 @@
+// Host side of librac: argument checking, the bit-packed relation layout,
+// per-stream workspaces and the extern "C" entry points declared in rac.h.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "rac_internal.h"
+
+namespace rac {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+rac_status cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return RAC_ECUDA;
+}
+
+NetDev net_dev(const rac_network *net) {
+  NetDev N;
+  N.n = net->n;
+  N.d = net->d;
+  N.dp = net->dp;
+  N.q = net->q;
+  N.nb = net->nb;
+  N.rows_per_slab = net->rows_per_slab;
+  N.n_slabs = int32_t(net->n_slabs);
+  N.rel = static_cast<const uint4 *>(net->d_rel);
+  N.slabs = net->d_slabs;
+  N.pmask = net->d_pmask;
+  N.roff = net->d_roff;
+  return N;
+}
+
+void free_workspace(Workspace *w) {
+  if (!w) return;
+  cudaFree(w->bufB);
+  cudaFree(w->flags);
+  cudaFree(w->sync);
+  cudaFree(w->state_off);
+  cudaFree(w->res_idx);
+  cudaFree(w->host_dom);
+  cudaFree(w->host_res);
+  delete w;
+}
+
+namespace {
+size_t flag_words(int states, int nb) {
+  return size_t(6) * states + size_t(3) * states * nb + size_t(3) * nb;
+}
+}  // namespace
+
+Workspace *get_workspace(const rac_network *cnet, cudaStream_t stream, int n_states, int n_items,
+                         rac_status *rc) {
+  rac_network *net = const_cast<rac_network *>(cnet);
+  std::lock_guard<std::mutex> lock(net->mu);
+  Workspace *&w = net->ws[stream];
+  if (w && w->cap_states >= n_states && w->cap_items >= n_items) return w;
+  // grow: the old workspace may still be in use by work queued on `stream`
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    *rc = cuda_fail(e, "cudaStreamSynchronize before workspace growth");
+    return nullptr;
+  }
+  const int states = std::max(n_states, w ? w->cap_states : 0);
+  const int items = std::max(n_items, w ? w->cap_items : 0);
+  free_workspace(w);
+  w = new (std::nothrow) Workspace();
+  if (!w) {
+    set_error("out of host memory");
+    *rc = RAC_ENOMEM;
+    return nullptr;
+  }
+  w->cap_states = states;
+  w->cap_items = items;
+  w->nb = net->nb;
+  w->n = net->n;
+  const size_t nwords = size_t(states) * size_t(net->n);
+  bool ok = cudaMalloc(&w->bufB, std::max<size_t>(nwords, 1) * 4) == cudaSuccess &&
+            cudaMalloc(&w->flags, flag_words(states, net->nb) * 4) == cudaSuccess &&
+            cudaMalloc(&w->sync, sizeof(Sync)) == cudaSuccess &&
+            cudaMalloc(&w->state_off, std::max(items, 1) * sizeof(int64_t)) == cudaSuccess &&
+            cudaMalloc(&w->res_idx, std::max(items, 1) * sizeof(int32_t)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_workspace(w);
+    w = nullptr;
+    set_error("device allocation of the enforcement workspace failed");
+    *rc = RAC_ENOMEM;
+    return nullptr;
+  }
+  e = cudaMemset(w->sync, 0, sizeof(Sync));
+  if (e == cudaSuccess) e = cudaMemset(w->flags, 0, flag_words(states, net->nb) * 4);
+  if (e != cudaSuccess) {
+    free_workspace(w);
+    w = nullptr;
+    *rc = cuda_fail(e, "cudaMemset of the workspace");
+    return nullptr;
+  }
+  return w;
+}
+
+namespace {
+
+bool check_device(const rac_network *net) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != net->device) {
+    set_error("the current CUDA device is not the network's device");
+    return false;
+  }
+  return true;
+}
+
+LaunchParams base_params(const rac_network *net, Workspace *w, int n_states, int32_t max_sweeps,
+                         uint32_t flags) {
+  LaunchParams P = {};
+  P.net = net_dev(net);
+  P.n_states = n_states;
+  P.bufB = w->bufB;
+  P.any = w->flags;
+  P.wipe = P.any + 3 * size_t(n_states);
+  P.chg = P.wipe + 3 * size_t(n_states);
+  P.chgU = P.chg + 3 * size_t(n_states) * net->nb;
+  P.sync = w->sync;
+  P.max_sweeps = max_sweeps;
+  const int64_t bound = int64_t(net->n) * net->d + 2;
+  P.sweep_bound = int32_t(std::min<int64_t>(bound, 0xFFFFF0));
+  P.flags = flags;
+  return P;
+}
+
+constexpr uint32_t kKnownFlags = RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL;
+
+// Largest power of two rows (<= 32) whose slab fits one ring stage.
+int rows_per_slab_for(int dp) {
+  int rows = 32;
+  while (rows > 1 && size_t(rows) * 32 * dp * 4 > size_t(kStageBytes)) rows >>= 1;
+  return rows;
+}
+
+}  // namespace
+}  // namespace rac
+
+using namespace rac;
+
+extern "C" {
+
+const char *rac_last_error(void) { return rac::g_last_error.c_str(); }
+
+rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const int32_t *scope,
+                              const uint32_t *rel_bits, uint32_t layout_flags,
+                              rac_network **out) {
+  set_error("");
+  if (!out) {
+    set_error("out is NULL");
+    return RAC_EINVAL;
+  }
+  *out = nullptr;
+  if (n_vars < 1 || n_vars > 2000000) {
+    set_error("n_vars must be in [1, 2000000]");
+    return RAC_EINVAL;
+  }
+  if (d < 1 || d > 32) {
+    set_error("d must be in [1, 32]");
+    return RAC_EINVAL;
+  }
+  if (n_cons < 0 || (n_cons > 0 && (!scope || !rel_bits))) {
+    set_error("n_cons < 0 or NULL scope / rel_bits");
+    return RAC_EINVAL;
+  }
+  if (layout_flags & ~RAC_LAYOUT_BITS) {
+    set_error("unknown layout flag");
+    return RAC_EINVAL;
+  }
+  const uint32_t full = d == 32 ? 0xFFFFFFFFu : ((1u << d) - 1u);
+  const int nb = (n_vars + 31) / 32;
+  const int dp = (d + 3) & ~3;
+  const int q = dp / 4;
+  const int rows = rows_per_slab_for(dp);
+
+  // orient every constraint as (lo, hi) and sort by (I, J, i, j)
+  std::vector<std::pair<uint64_t, int64_t>> order;
+  try {
+    order.resize(size_t(n_cons));
+  } catch (const std::bad_alloc &) {
+    set_error("out of host memory");
+    return RAC_ENOMEM;
+  }
+  for (int64_t c = 0; c < n_cons; ++c) {
+    const int32_t x = scope[2 * c], y = scope[2 * c + 1];
+    if (x < 0 || x >= n_vars || y < 0 || y >= n_vars || x == y) {
+      set_error("constraint " + std::to_string(c) + " has a bad scope");
+      return RAC_EINVAL;
+    }
+    for (int a = 0; a < d; ++a)
+      if (rel_bits[c * d + a] & ~full) {
+        set_error("constraint " + std::to_string(c) + " sets a relation bit >= d");
+        return RAC_EINVAL;
+      }
+    const uint32_t lo = uint32_t(std::min(x, y)), hi = uint32_t(std::max(x, y));
+    const uint64_t key = ((uint64_t(lo >> 5) * uint64_t(nb) + (hi >> 5)) << 10) |
+                         (uint64_t(lo & 31u) << 5) | (hi & 31u);
+    order[size_t(c)] = {key, c};
+  }
+  std::sort(order.begin(), order.end());
+  for (size_t i = 1; i < order.size(); ++i)
+    if (order[i].first == order[i - 1].first) {
+      set_error("two constraints on the same pair of variables (constraints " +
+                std::to_string(order[i - 1].second) + " and " + std::to_string(order[i].second) +
+                ")");
+      return RAC_EINVAL;
+    }
+
+  // slabs: (I, J, i / rows)
+  std::vector<SlabDesc> slabs;
+  std::vector<uint32_t> pmask, roff;
+  std::vector<uint32_t> relw;
+  try {
+    relw.assign(size_t(n_cons) * dp, 0u);
+    size_t i = 0;
+    while (i < order.size()) {
+      const uint64_t key = order[i].first;
+      const uint64_t tile = key >> 10;
+      const uint32_t row_group = uint32_t((key >> 5) & 31u) / uint32_t(rows);
+      SlabDesc sd = {};
+      sd.I = uint32_t(tile / uint64_t(nb));
+      sd.J = uint32_t(tile % uint64_t(nb));
+      sd.row0 = row_group * rows;
+      sd.nrows = uint32_t(rows);
+      sd.meta_off = uint32_t(pmask.size());
+      sd.rel_off16 = uint32_t((i * size_t(dp) * 4) / 16);
+      pmask.resize(pmask.size() + rows, 0u);
+      roff.resize(roff.size() + rows, 0u);
+      size_t j = i;
+      uint32_t count = 0;
+      while (j < order.size() && (order[j].first >> 10) == tile &&
+             uint32_t((order[j].first >> 5) & 31u) / uint32_t(rows) == row_group) {
+        const uint32_t ri = uint32_t((order[j].first >> 5) & 31u) - sd.row0;
+        const uint32_t cj = uint32_t(order[j].first & 31u);
+        pmask[sd.meta_off + ri] |= 1u << cj;
+        ++count;
+        // relation rows in the (lo, hi) orientation
+        const int64_t c = order[j].second;
+        const bool swap = scope[2 * c] > scope[2 * c + 1];
+        uint32_t *dst = relw.data() + j * size_t(dp);
+        if (!swap) {
+          for (int a = 0; a < d; ++a) dst[a] = rel_bits[c * d + a];
+        } else {
+          for (int a = 0; a < d; ++a) {
+            uint32_t w = 0;
+            for (int b = 0; b < d; ++b) w |= ((rel_bits[c * d + b] >> a) & 1u) << b;
+            dst[a] = w;
+          }
+        }
+        ++j;
+      }
+      uint32_t acc = 0;
+      for (int r = 0; r < rows; ++r) {
+        roff[sd.meta_off + r] = acc;
+        acc += uint32_t(__builtin_popcount(pmask[sd.meta_off + r]));
+      }
+      sd.nbytes = count * uint32_t(dp) * 4u;
+      slabs.push_back(sd);
+      i = j;
+    }
+  } catch (const std::bad_alloc &) {
+    set_error("out of host memory");
+    return RAC_ENOMEM;
+  }
+  if ((relw.size() * 4) / 16 > 0xFFFFFFFFull) {
+    set_error("relation store too large");
+    return RAC_ENOTSUP;
+  }
+
+  rac_network *net = new (std::nothrow) rac_network();
+  if (!net) {
+    set_error("out of host memory");
+    return RAC_ENOMEM;
+  }
+  net->n = n_vars;
+  net->d = d;
+  net->dp = dp;
+  net->q = q;
+  net->nb = nb;
+  net->rows_per_slab = rows;
+  net->m = n_cons;
+  net->n_slabs = int64_t(slabs.size());
+  net->rel_bytes = relw.size() * 4;
+  cudaError_t e = cudaGetDevice(&net->device);
+  auto fail = [&](cudaError_t err, const char *what) {
+    rac_status rc = err == cudaErrorMemoryAllocation ? RAC_ENOMEM : cuda_fail(err, what);
+    if (rc == RAC_ENOMEM) set_error(std::string(what) + ": out of device memory");
+    rac_destroy(net);
+    return rc;
+  };
+  if (e != cudaSuccess) return fail(e, "cudaGetDevice");
+  auto upload = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
+    cudaError_t er = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+    if (er != cudaSuccess) return er;
+    if (bytes) er = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    return er;
+  };
+  if ((e = upload(&net->d_rel, relw.data(), relw.size() * 4)) != cudaSuccess)
+    return fail(e, "upload of the relation slabs");
+  if ((e = upload(reinterpret_cast<void **>(&net->d_slabs), slabs.data(),
+                  slabs.size() * sizeof(SlabDesc))) != cudaSuccess)
+    return fail(e, "upload of the slab table");
+  if ((e = upload(reinterpret_cast<void **>(&net->d_pmask), pmask.data(), pmask.size() * 4)) !=
+      cudaSuccess)
+    return fail(e, "upload of the row masks");
+  if ((e = upload(reinterpret_cast<void **>(&net->d_roff), roff.data(), roff.size() * 4)) !=
+      cudaSuccess)
+    return fail(e, "upload of the row offsets");
+  *out = net;
+  return RAC_OK;
+}
+
+void rac_destroy(rac_network *net) {
+  if (!net) return;
+  for (auto &kv : net->ws) free_workspace(kv.second);
+  net->ws.clear();
+  cudaFree(net->d_rel);
+  cudaFree(net->d_slabs);
+  cudaFree(net->d_pmask);
+  cudaFree(net->d_roff);
+  delete net;
+}
+
+int32_t rac_network_info(const rac_network *net, int64_t *info, int32_t n_info) {
+  if (!net || !info || n_info <= 0) return 0;
+  const int64_t v[7] = {net->n, net->d, net->m, int64_t(net->rel_bytes), net->n_slabs,
+                        net->rows_per_slab, net->dp};
+  const int32_t k = std::min<int32_t>(n_info, 7);
+  for (int32_t i = 0; i < k; ++i) info[i] = v[i];
+  return k;
+}
+
+rac_status rac_enforce(const rac_network *net, const uint32_t *dom_in, uint32_t *dom_out,
+                       int32_t *iterations, int32_t *status, int32_t max_sweeps, uint32_t flags,
+                       rac_stream_t stream) {
+  set_error("");
+  if (!net || !dom_in || !dom_out || !iterations || !status) {
+    set_error("NULL argument");
+    return RAC_EINVAL;
+  }
+  if (flags & ~kKnownFlags) {
+    set_error("unknown flag");
+    return RAC_EINVAL;
+  }
+  if (!check_device(net)) return RAC_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  rac_status rc = RAC_OK;
+  Workspace *w = get_workspace(net, s, 1, 0, &rc);
+  if (!w) return rc;
+  LaunchParams P = base_params(net, w, 1, max_sweeps, flags);
+  P.contiguous = 1;
+  P.dom_in = dom_in;
+  P.dom_out = dom_out;
+  P.iterations = iterations;
+  P.status = status;
+  return launch_bits(P, s);
+}
+
+rac_status rac_enforce_batch(const rac_network *const *nets, int32_t n_nets, int32_t n_items,
+                             const int32_t *item_net, const int64_t *item_dom_off,
+                             const uint32_t *dom_in, uint32_t *dom_out, int32_t *iterations,
+                             int32_t *status, int32_t max_sweeps, uint32_t flags,
+                             rac_stream_t stream) {
+  set_error("");
+  if (n_items < 0 || n_nets < 0) {
+    set_error("negative count");
+    return RAC_EINVAL;
+  }
+  if (n_items == 0) return RAC_OK;
+  if (!nets || !item_net || !item_dom_off || !dom_in || !dom_out || !iterations || !status) {
+    set_error("NULL argument");
+    return RAC_EINVAL;
+  }
+  if (flags & ~kKnownFlags) {
+    set_error("unknown flag");
+    return RAC_EINVAL;
+  }
+  std::vector<std::vector<int32_t>> groups(size_t(std::max(n_nets, 1)));
+  for (int32_t i = 0; i < n_items; ++i) {
+    const int32_t k = item_net[i];
+    if (k < 0 || k >= n_nets || !nets[k]) {
+      set_error("item " + std::to_string(i) + " names a bad network");
+      return RAC_EINVAL;
+    }
+    if (item_dom_off[i] < 0) {
+      set_error("item " + std::to_string(i) + " has a negative offset");
+      return RAC_EINVAL;
+    }
+    groups[size_t(k)].push_back(i);
+  }
+  for (int32_t k = 0; k < n_nets; ++k)
+    if (!groups[size_t(k)].empty() && !check_device(nets[k])) return RAC_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<int64_t> off;
+  std::vector<int32_t> idx;
+  for (int32_t k = 0; k < n_nets; ++k) {
+    const std::vector<int32_t> &g = groups[size_t(k)];
+    for (size_t base = 0; base < g.size(); base += kMaxStatesPerLaunch) {
+      const int cnt = int(std::min<size_t>(kMaxStatesPerLaunch, g.size() - base));
+      rac_status rc = RAC_OK;
+      Workspace *w = get_workspace(nets[k], s, cnt, cnt, &rc);
+      if (!w) return rc;
+      off.assign(size_t(cnt), 0);
+      idx.assign(size_t(cnt), 0);
+      for (int j = 0; j < cnt; ++j) {
+        off[size_t(j)] = item_dom_off[g[base + j]];
+        idx[size_t(j)] = g[base + j];
+      }
+      cudaError_t e = cudaMemcpyAsync(w->state_off, off.data(), cnt * sizeof(int64_t),
+                                      cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w->res_idx, idx.data(), cnt * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return cuda_fail(e, "upload of the item table");
+      // pageable sources: the copies above are staged before they return
+      LaunchParams P = base_params(nets[k], w, cnt, max_sweeps, flags);
+      P.contiguous = 0;
+      P.state_off = w->state_off;
+      P.res_idx = w->res_idx;
+      P.dom_in = dom_in;
+      P.dom_out = dom_out;
+      P.iterations = iterations;
+      P.status = status;
+      // a later chunk on this workspace is stream-ordered after this launch
+      rc = launch_bits(P, s);
+      if (rc != RAC_OK) return rc;
+    }
+  }
+  return RAC_OK;
+}
+
+rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint32_t *dom_in,
+                            uint32_t *dom_out, int32_t *iterations, int32_t *status,
+                            int32_t max_sweeps, uint32_t flags, rac_stream_t stream) {
+  set_error("");
+  if (!net || !dom_in || !dom_out || !iterations || !status || n_states < 0) {
+    set_error("NULL argument or negative state count");
+    return RAC_EINVAL;
+  }
+  if (flags & ~kKnownFlags) {
+    set_error("unknown flag");
+    return RAC_EINVAL;
+  }
+  if (n_states == 0) return RAC_OK;
+  if (!check_device(net)) return RAC_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t words = size_t(n_states) * net->n;
+  rac_status rc = RAC_OK;
+  Workspace *w0 = get_workspace(net, s, std::min<int32_t>(n_states, kMaxStatesPerLaunch), 0, &rc);
+  if (!w0) return rc;
+  if (w0->host_cap < words) {
+    cudaError_t er = cudaStreamSynchronize(s);
+    if (er != cudaSuccess) return cuda_fail(er, "cudaStreamSynchronize");
+    cudaFree(w0->host_dom);
+    cudaFree(w0->host_res);
+    w0->host_dom = nullptr;
+    w0->host_res = nullptr;
+    w0->host_cap = 0;
+    if (cudaMalloc(&w0->host_dom, words * 4) != cudaSuccess ||
+        cudaMalloc(&w0->host_res, size_t(n_states) * 8 + 8) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(w0->host_dom);
+      w0->host_dom = nullptr;
+      set_error("out of device memory for the host-path staging buffers");
+      return RAC_ENOMEM;
+    }
+    w0->host_cap = words;
+    w0->host_res_cap = size_t(n_states);
+  }
+  uint32_t *d_dom = w0->host_dom;
+  int32_t *d_res = w0->host_res;
+  cudaError_t e = cudaMemcpyAsync(d_dom, dom_in, words * 4, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) rc = cuda_fail(e, "host-to-device copy");
+  for (int32_t base = 0; rc == RAC_OK && base < n_states; base += kMaxStatesPerLaunch) {
+    const int cnt = std::min<int32_t>(kMaxStatesPerLaunch, n_states - base);
+    Workspace *w = get_workspace(net, s, cnt, 0, &rc);
+    if (!w) break;
+    LaunchParams P = base_params(net, w, cnt, max_sweeps, flags);
+    P.contiguous = 1;
+    P.dom_in = d_dom + size_t(base) * net->n;
+    P.dom_out = d_dom + size_t(base) * net->n;
+    P.iterations = d_res + base;
+    P.status = d_res + n_states + base;
+    rc = launch_bits(P, s);
+  }
+  if (rc == RAC_OK) {
+    e = cudaMemcpyAsync(dom_out, d_dom, words * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(iterations, d_res, size_t(n_states) * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(status, d_res + n_states, size_t(n_states) * 4, cudaMemcpyDeviceToHost,
+                          s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "device-to-host copy");
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess && rc == RAC_OK) rc = cuda_fail(e, "cudaStreamSynchronize");
+  return rc;
+}
+
+}  // extern "C"

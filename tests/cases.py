@@ -124,3 +124,33 @@ def load_golden(name):
 
 def golden_names():
     return sorted(f for f in os.listdir(GOLDEN) if f.endswith(".txt") and f != "README.txt")
+
+
+def tuned_tightness(n, d, density, c):
+    """Tightness at which a full-domain value lacks a support on about c of
+    its ~n*density constraints: near the point where removals start to
+    cascade, so that enforcement runs for several sweeps."""
+    return min(0.95, (c / max(1.0, n * density)) ** (1.0 / d))
+
+
+def mixed_states(rng, n, d):
+    """Three input domains: every variable randomly restricted (no empty
+    domain), four variables restricted and the rest full, and all full."""
+    full = np.full(n, full_word(d), np.uint32)
+    a = random_tiny(rng, n, d, 0.0, 0.0, restrict=0.3)[2]
+    a[a == 0] = 1
+    b = full.copy()
+    for x in rng.choice(n, size=min(n, 4), replace=False):
+        b[x] = np.uint32(int(rng.integers(1, 1 << min(d, 31))) & full_word(d))
+    return np.array([a, b, full], dtype=np.uint32)
+
+
+# (n, density, c) of the per-width parity cases
+WIDTH_CASES = [(37, 0.5, 0.3), (70, 0.15, 0.03), (33, 1.0, 0.01)]
+
+
+def width_cases(d):
+    rng = np.random.default_rng(1000 + d)
+    for n, dens, c in WIDTH_CASES:
+        scope, rel, _ = random_tiny(rng, n, d, dens, tuned_tightness(n, d, dens, c))
+        yield n, scope, rel, mixed_states(rng, n, d)

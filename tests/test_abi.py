@@ -1,0 +1,90 @@
+"""The C-ABI library loads, exports every symbol include/rac.h declares, and
+rejects bad arguments before touching the device (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2407_11388_b300 as rac
+from paper_2407_11388_b300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build()
+    return rac.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "rac.h")).read()
+    return re.findall(r"^RAC_API\s+[\w\s\*]+?\b(rac_\w+)\s*\(", src, flags=re.M)
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert set(names) >= set(rac.ABI_FUNCTIONS)
+    for name in names:
+        assert hasattr(L, name), name
+    # and nothing internal leaks out of the library
+    out = os.popen("nm -D --defined-only %s" % rac.build.LIB).read()
+    exported = set(re.findall(r"\b(rac_\w+)\b", out))
+    assert exported == set(names)
+
+
+def _create(L, n, d, scope, rel, flags=1):
+    h = ctypes.c_void_p()
+    scope = np.ascontiguousarray(scope, np.int32)
+    rel = np.ascontiguousarray(rel, np.uint32)
+    rc = L.rac_create_network(n, d, scope.shape[0], scope.ctypes.data, rel.ctypes.data, flags,
+                              ctypes.byref(h))
+    return rc, h
+
+
+@pytest.mark.parametrize("case", ["d0", "d33", "n0", "self_loop", "out_of_range", "dup_pair",
+                                  "dup_pair_reversed", "bit_above_d", "bad_layout"])
+def test_create_rejects(L, case):
+    n, d = 4, 3
+    scope = np.array([[0, 1], [1, 2]], np.int32)
+    rel = np.full((2, 3), 7, np.uint32)
+    flags = 1
+    if case == "d0":
+        d = 0
+    elif case == "d33":
+        d = 33
+    elif case == "n0":
+        n = 0
+    elif case == "self_loop":
+        scope[1] = (2, 2)
+    elif case == "out_of_range":
+        scope[1] = (1, 4)
+    elif case == "dup_pair":
+        scope[1] = (0, 1)
+    elif case == "dup_pair_reversed":
+        scope[1] = (1, 0)
+    elif case == "bit_above_d":
+        rel[1, 2] = 8
+    elif case == "bad_layout":
+        flags = 0x100
+    rc, h = _create(L, n, d, scope, rel.reshape(2, -1) if d == 3 else np.zeros((2, max(d, 1)), np.uint32), flags)
+    assert rc == rac.EINVAL
+    assert h.value is None
+    assert L.rac_last_error().decode() != ""
+
+
+def test_null_and_flag_checks(L):
+    assert L.rac_enforce(None, None, None, None, None, 0, 0, None) == rac.EINVAL
+    assert L.rac_enforce_batch(None, 0, 0, None, None, None, None, None, None, 0, 0, None) == rac.OK
+    assert L.rac_enforce_batch(None, 1, 1, None, None, None, None, None, None, 0, 0, None) == rac.EINVAL
+    assert L.rac_enforce_host(None, 1, None, None, None, None, 0, 0, None) == rac.EINVAL
+    L.rac_destroy(None)  # NULL-safe
+    assert L.rac_network_info(None, None, 0) == 0
+
+
+def test_python_binding_wraps_errors(L):
+    with pytest.raises(rac.RacError) as e:
+        rac.Network(3, 40, np.zeros((0, 2), np.int32), np.zeros((0, 40), np.uint32))
+    assert e.value.code == rac.EINVAL

@@ -1,0 +1,245 @@
+"""CUDA path versus the CPU oracle, bit for bit: domains, sweep counts and
+status (GPU).  Every case goes through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+import racgen
+import paper_2407_11388_b300 as rac
+from cases import (chain, chain_closed_form, full_word, golden_names, load_golden, random_tiny,
+                   width_cases)
+from gpu_helpers import assert_same, from_dev, gpu_enforce, oracle_enforce, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+FLAG_SETS = [0, rac.INCREMENTAL, rac.STOP_ON_WIPEOUT, rac.STOP_ON_WIPEOUT | rac.INCREMENTAL]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2407_11388_b300.build import build
+    build()
+
+
+@pytest.mark.parametrize("name", golden_names())
+def test_golden(name):
+    g = load_golden(name)
+    flags = rac.STOP_ON_WIPEOUT if g["stop"] else 0
+    for extra in (0, rac.INCREMENTAL):
+        out, it, st = gpu_enforce(g["n"], g["d"], g["scope"], g["rel"], g["dom"], flags | extra)
+        assert np.array_equal(out[0], g["expected"]), (name, out[0], g["expected"])
+        assert it[0] == g["iterations"] and st[0] == g["status"], (name, it, st)
+
+
+@pytest.mark.parametrize("n_chain,d", [(2, 2), (5, 9), (17, 20), (32, 32), (9, 8)])
+def test_chain_spread_over_tiles(n_chain, d):
+    """The chain closed form with the chain's variables scattered over 300
+    variables, so every link crosses tiles; d < n_chain wipes out."""
+    n = 300
+    perm = np.random.default_rng(n_chain * 100 + d).permutation(n)[:n_chain]
+    s, r = chain(n_chain, d)
+    scope = perm[s]
+    dom = np.full(n, full_word(d), np.uint32)
+    ref = oracle_enforce(n, d, scope, r, dom)
+    if d >= n_chain:
+        want = np.full(n, full_word(d), np.uint32)
+        want[perm] = chain_closed_form(n_chain, d)
+        assert np.array_equal(ref[0][0], want) and ref[1][0] == n_chain
+    for flags in FLAG_SETS:
+        assert_same(gpu_enforce(n, d, scope, r, dom, flags), oracle_enforce(n, d, scope, r, dom, flags),
+                    "chain %d/%d flags %d" % (n_chain, d, flags))
+
+
+@pytest.mark.parametrize("d", list(range(1, 33)))
+def test_random_every_width(d):
+    """Every relation width (all kernel instantiations), ragged n, dense and
+    sparse graphs, tightness near the cascade point, three kinds of input
+    domain; single-state and batched launches, all flag combinations."""
+    for n, scope, rel, doms in width_cases(d):
+        for flags in FLAG_SETS:
+            ref = oracle_enforce(n, d, scope, rel, doms, flags)
+            assert_same(gpu_enforce(n, d, scope, rel, doms[:1], flags),
+                        (ref[0][:1], ref[1][:1], ref[2][:1]), "d=%d n=%d single" % (d, n))
+            assert_same(gpu_enforce(n, d, scope, rel, doms, flags, shuffle_seed=d), ref,
+                        "d=%d n=%d batch" % (d, n))
+
+
+@pytest.mark.parametrize("B", [2, 3, 5, 8, 40])
+def test_state_groupings(B):
+    """Warp-to-state mappings for different state counts in one launch."""
+    rng = np.random.default_rng(B)
+    n, d = 150, 12
+    scope, rel, _ = random_tiny(rng, n, d, 0.3, 0.62)
+    doms = np.array([random_tiny(rng, n, d, 0.0, 0.0, restrict=0.25)[2] for _ in range(B)])
+    for flags in (0, rac.INCREMENTAL | rac.STOP_ON_WIPEOUT):
+        assert_same(gpu_enforce(n, d, scope, rel, doms, flags, shuffle_seed=B),
+                    oracle_enforce(n, d, scope, rel, doms, flags), "B=%d" % B)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_small_random_csp_config(seed):
+    """n=50, d=10, density 0.5, tightness 0.3: full domains and assignment
+    states (1-5 variables reduced to one value), seeds 0-9."""
+    net = racgen.random_network(seed, 0, 50, 10, 0.5, 0.3)
+    doms = np.array([racgen.full_domain(50, 10)] +
+                    [racgen.assignment_state(seed, 0, s, 50, 10) for s in range(16)])
+    for flags in (0, rac.INCREMENTAL):
+        assert_same(gpu_enforce(50, 10, net.scope, net.rel, doms, flags, shuffle_seed=seed),
+                    oracle_enforce(50, 10, net.scope, net.rel, doms, flags), "seed %d" % seed)
+        assert_same(gpu_enforce(50, 10, net.scope, net.rel, doms[:1], flags),
+                    oracle_enforce(50, 10, net.scope, net.rel, doms[:1], flags), "seed %d" % seed)
+
+
+def test_dense_500_config():
+    """n=500, d=20, complete graph, tightness 0.35, full domains (the
+    single-state launch the benchmark times) plus assignment states."""
+    net = racgen.random_network(0, 0, 500, 20, 1.0, 0.35)
+    full = racgen.full_domain(500, 20)
+    assert_same(gpu_enforce(500, 20, net.scope, net.rel, full),
+                oracle_enforce(500, 20, net.scope, net.rel, full), "dense500 full")
+    doms = np.array([racgen.assignment_state(0, 0, s, 500, 20) for s in range(6)])
+    assert_same(gpu_enforce(500, 20, net.scope, net.rel, doms, rac.INCREMENTAL, shuffle_seed=1),
+                oracle_enforce(500, 20, net.scope, net.rel, doms), "dense500 states")
+
+
+def test_dense_2000_config():
+    """n=2000, d=32, density 0.9, tightness 0.3 (a 230 MB relation store),
+    full domains and two assignment states."""
+    net = racgen.random_network(0, 0, 2000, 32, 0.9, 0.3)
+    full = racgen.full_domain(2000, 32)
+    assert_same(gpu_enforce(2000, 32, net.scope, net.rel, full),
+                oracle_enforce(2000, 32, net.scope, net.rel, full, threads=32), "dense2000 full")
+    doms = np.array([racgen.assignment_state(0, 0, s, 2000, 32) for s in range(2)])
+    assert_same(gpu_enforce(2000, 32, net.scope, net.rel, doms, shuffle_seed=3),
+                oracle_enforce(2000, 32, net.scope, net.rel, doms, threads=32), "dense2000 states")
+
+
+def test_search_path_states():
+    """States built the way backtrack search builds them (Algorithm 2):
+    enforce, assign one more variable, enforce again -- the multi-sweep regime
+    of Table 1.  The states come from the oracle."""
+    n, d = 120, 10
+    net = racgen.random_network(4, 0, n, d, 0.5, 0.3)
+    rng = np.random.default_rng(4)
+    dom, _, _ = oracle.rac(n, d, net.scope, net.rel, racgen.full_domain(n, d))
+    states = []
+    for _ in range(12):
+        free = [x for x in range(n) if bin(int(dom[x])).count("1") > 1]
+        if not free:
+            break
+        x = int(rng.choice(free))
+        vals = [a for a in range(d) if (int(dom[x]) >> a) & 1]
+        nxt = dom.copy()
+        nxt[x] = 1 << int(rng.choice(vals))
+        states.append(nxt)
+        out, it, st = oracle.rac(n, d, net.scope, net.rel, nxt)
+        if st == oracle.OK:
+            dom = out
+    doms = np.array(states)
+    ref = oracle_enforce(n, d, net.scope, net.rel, doms)
+    assert ref[1].max() >= 3
+    for flags in FLAG_SETS:
+        assert_same(gpu_enforce(n, d, net.scope, net.rel, doms, flags, shuffle_seed=2),
+                    oracle_enforce(n, d, net.scope, net.rel, doms, flags), "search path")
+
+
+def test_sweep_cap():
+    scope, rel = chain(12, 16)
+    dom = np.full(12, full_word(16), np.uint32)
+    for cap in (1, 2, 5, 11, 12, 13):
+        for flags in (0, rac.INCREMENTAL):
+            assert_same(gpu_enforce(12, 16, scope, rel, dom, flags, max_sweeps=cap),
+                        oracle_enforce(12, 16, scope, rel, dom, flags, max_sweeps=cap), "cap %d" % cap)
+
+
+def test_in_place_and_repeat():
+    """dom_out == dom_in, and repeated launches on one workspace."""
+    T = torch()
+    net_np = racgen.random_network(9, 0, 90, 7, 0.4, 0.55)
+    dom = racgen.assignment_state(9, 0, 0, 90, 7)
+    ref = oracle_enforce(90, 7, net_np.scope, net_np.rel, dom)
+    with rac.Network(90, 7, net_np.scope, net_np.rel) as net:
+        it = T.empty(1, dtype=T.int32, device="cuda:0")
+        st = T.empty(1, dtype=T.int32, device="cuda:0")
+        for _ in range(5):
+            buf = to_dev(dom)
+            rac.enforce(net, buf, buf, it, st)
+            T.cuda.synchronize()
+            assert_same((from_dev(buf)[None], it.cpu().numpy(), st.cpu().numpy()), ref, "in place")
+
+
+def test_batch_of_different_networks():
+    """rac_enforce_batch over networks of different n and d, items
+    interleaved and stored at scattered offsets."""
+    T = torch()
+    rng = np.random.default_rng(21)
+    specs = [(64, 8, 0.6, 0.5), (200, 16, 0.3, 0.6), (33, 32, 1.0, 0.45), (5, 3, 1.0, 0.5)]
+    nps = [racgen.random_network(21, i, n, d, p, t) for i, (n, d, p, t) in enumerate(specs)]
+    nets = [rac.Network(x.n, x.d, x.scope, x.rel) for x in nps]
+    items, offs, doms = [], [], []
+    pos = 7
+    for i in range(23):
+        k = int(rng.integers(0, len(specs)))
+        dom = racgen.assignment_state(21, k, i, nps[k].n, nps[k].d)
+        items.append(k)
+        offs.append(pos)
+        doms.append(dom)
+        pos += nps[k].n + int(rng.integers(0, 5))
+    flat = np.zeros(pos + 3, np.uint32)
+    for o, dmn in zip(offs, doms):
+        flat[o:o + dmn.size] = dmn
+    din = to_dev(flat)
+    dout = T.zeros_like(din)
+    it = T.empty(len(items), dtype=T.int32, device="cuda:0")
+    st = T.empty(len(items), dtype=T.int32, device="cuda:0")
+    rac.enforce_batch(nets, items, offs, din, dout, it, st, flags=rac.INCREMENTAL)
+    T.cuda.synchronize()
+    got = from_dev(dout)
+    its, sts = it.cpu().numpy(), st.cpu().numpy()
+    for j, (k, o, dmn) in enumerate(zip(items, offs, doms)):
+        x = nps[k]
+        ro, ri, rs = oracle.rac(x.n, x.d, x.scope, x.rel, dmn)
+        assert np.array_equal(got[o:o + x.n], ro) and its[j] == ri and sts[j] == rs, j
+    for n in nets:
+        n.close()
+
+
+def test_host_entry_point():
+    net_np = racgen.random_network(2, 0, 300, 24, 0.7, 0.33)
+    doms = np.array([racgen.assignment_state(2, 0, s, 300, 24) for s in range(5)])
+    with rac.Network(300, 24, net_np.scope, net_np.rel) as net:
+        out, it, st = rac.enforce_host(net, doms, flags=rac.INCREMENTAL)
+    assert_same((out, it, st), oracle_enforce(300, 24, net_np.scope, net_np.rel, doms), "host")
+
+
+def test_two_streams():
+    """Each stream gets its own workspace; concurrent calls do not interfere."""
+    T = torch()
+    net_np = racgen.random_network(6, 0, 256, 16, 0.5, 0.5)
+    doms = [racgen.assignment_state(6, 0, s, 256, 16) for s in range(2)]
+    ref = [oracle_enforce(256, 16, net_np.scope, net_np.rel, d_) for d_ in doms]
+    with rac.Network(256, 16, net_np.scope, net_np.rel) as net:
+        streams = [T.cuda.Stream(), T.cuda.Stream()]
+        bufs = [to_dev(d_) for d_ in doms]
+        outs = [T.empty_like(b) for b in bufs]
+        its = [T.empty(1, dtype=T.int32, device="cuda:0") for _ in range(2)]
+        sts = [T.empty(1, dtype=T.int32, device="cuda:0") for _ in range(2)]
+        T.cuda.synchronize()
+        for rep in range(3):
+            for i in range(2):
+                rac.enforce(net, bufs[i], outs[i], its[i], sts[i], stream=streams[i])
+        T.cuda.synchronize()
+        for i in range(2):
+            assert_same((from_dev(outs[i])[None], its[i].cpu().numpy(), sts[i].cpu().numpy()),
+                        ref[i], "stream %d" % i)
+
+
+def test_no_constraints_and_single_variable():
+    for n, d in [(1, 1), (1, 32), (40, 5)]:
+        dom = np.random.default_rng(n).integers(0, 1 << min(d, 31), n).astype(np.uint32)
+        dom &= np.uint32(full_word(d))
+        scope = np.zeros((0, 2), np.int32)
+        rel = np.zeros((0, d), np.uint32)
+        for flags in FLAG_SETS:
+            assert_same(gpu_enforce(n, d, scope, rel, dom, flags),
+                        oracle_enforce(n, d, scope, rel, dom, flags), "empty net")
