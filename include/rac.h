@@ -176,6 +176,30 @@ RAC_API rac_status rac_enforce_host(const rac_network *net, int32_t n_states, co
                             int32_t max_sweeps, uint32_t flags, rac_stream_t stream);
 
 /*
+ * rac_enforce_noalloc -- rac_enforce without any device allocation.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc while they enforce, such as code running during CUDA graph
+ * capture, loops that cannot take the device-wide synchronisation of
+ * cudaMalloc/cudaFree, or processes whose device memory belongs to another
+ * allocator.
+ *
+ * Arguments, results and errors are those of rac_enforce.  The scratch space
+ * is one static array inside the library (about 312 KiB on every device that
+ * loads it, held until the process exits), so:
+ *  - networks with more than RAC_NOALLOC_MAX_VARS variables are rejected with
+ *    RAC_EINVAL and an explanatory rac_last_error();
+ *  - all calls share the array: calls whose kernels overlap on the GPU (other
+ *    streams, other host threads) race and give undefined results;
+ *  - the first call on a device, with that device current, looks up the
+ *    array's device address (and prepares the kernel launch); make that first
+ *    call before starting any stream capture.
+ */
+#define RAC_NOALLOC_MAX_VARS 65536
+RAC_API rac_status rac_enforce_noalloc(const rac_network *net, const uint32_t *dom_in,
+                                       uint32_t *dom_out, int32_t *iterations, int32_t *status,
+                                       int32_t max_sweeps, uint32_t flags, rac_stream_t stream);
+
+/*
  * rac_network_info -- describe a network: writes up to n_info int64 values
  * to info, in this order: n_vars, d, n_cons, relation-slab bytes on the
  * device, number of relation slabs, rows per slab, words per stored relation

@@ -28,7 +28,8 @@ STATUS_NAMES = {OK: "ok", WIPEOUT: "wipeout", EINVAL: "einval", ENOMEM: "enomem"
                 ECUDA: "ecuda", ETIMEOUT: "etimeout", EBARRIER: "ebarrier", ENOTSUP: "enotsup"}
 
 ABI_FUNCTIONS = ("rac_create_network", "rac_destroy", "rac_enforce", "rac_enforce_batch",
-                 "rac_enforce_host", "rac_network_info", "rac_last_error")
+                 "rac_enforce_host", "rac_enforce_noalloc", "rac_network_info", "rac_last_error")
+NOALLOC_MAX_VARS = 65536
 
 
 class RacError(RuntimeError):
@@ -58,6 +59,8 @@ def lib():
         L.rac_enforce_batch.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, i32, u32, vp]
         L.rac_enforce_host.restype = i32
         L.rac_enforce_host.argtypes = [vp, i32, vp, vp, vp, vp, i32, u32, vp]
+        L.rac_enforce_noalloc.restype = i32
+        L.rac_enforce_noalloc.argtypes = [vp, vp, vp, vp, vp, i32, u32, vp]
         L.rac_network_info.restype = i32
         L.rac_network_info.argtypes = [vp, ctypes.POINTER(i64), i32]
         L.rac_last_error.restype = ctypes.c_char_p
@@ -151,6 +154,18 @@ def enforce(net, dom_in, dom_out, iterations, status, max_sweeps=0, flags=0, str
     _check(lib().rac_enforce(net.handle, _ptr(dom_in), _ptr(dom_out), _ptr(iterations),
                              _ptr(status), int(max_sweeps), int(flags), _stream(stream)),
            "rac_enforce")
+
+
+def enforce_noalloc(net, dom_in, dom_out, iterations, status, max_sweeps=0, flags=0,
+                    stream=None):
+    """rac_enforce_noalloc: like enforce(), with the library's static scratch
+    array instead of an allocated workspace, for callers that cannot allocate
+    device memory at call time (for example while a CUDA graph is being
+    captured).  At most NOALLOC_MAX_VARS variables; calls must not overlap on
+    the GPU; the first call on a device should precede any stream capture."""
+    _check(lib().rac_enforce_noalloc(net.handle, _ptr(dom_in), _ptr(dom_out), _ptr(iterations),
+                                     _ptr(status), int(max_sweeps), int(flags), _stream(stream)),
+           "rac_enforce_noalloc")
 
 
 def enforce_batch(nets, item_net, item_dom_off, dom_in, dom_out, iterations, status,
