@@ -28,7 +28,9 @@
  *  - Per-state results: status RAC_OK (fixpoint, no empty domain),
  *    RAC_WIPEOUT (some domain of the result is empty), RAC_ETIMEOUT (the
  *    sweep cap was reached first) or RAC_EBARRIER (a device-side wait gave
- *    up; the domains are then unspecified).
+ *    up after its time limit; the domains are then unspecified, and the
+ *    scratch workspace of that (network, stream) is poisoned: every later
+ *    call on it reports RAC_EBARRIER without enforcing).
  *  - Functions return RAC_OK or a negative error code; on error nothing has
  *    been launched and rac_last_error() describes the cause.  No C++
  *    exception crosses this boundary.

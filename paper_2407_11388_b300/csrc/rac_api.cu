@@ -34,8 +34,6 @@ NetDev net_dev(const rac_network *net) {
   N.n_slabs = int32_t(net->n_slabs);
   N.rel = static_cast<const uint4 *>(net->d_rel);
   N.slabs = net->d_slabs;
-  N.pmask = net->d_pmask;
-  N.roff = net->d_roff;
   return N;
 }
 
@@ -96,8 +94,11 @@ Workspace *get_workspace(const rac_network *cnet, cudaStream_t stream, int n_sta
     *rc = RAC_ENOMEM;
     return nullptr;
   }
+  // the state every launch expects: scratch domains all ones, flags and
+  // sync words zero
   e = cudaMemset(w->sync, 0, sizeof(Sync));
   if (e == cudaSuccess) e = cudaMemset(w->flags, 0, flag_words(states, net->nb) * 4);
+  if (e == cudaSuccess) e = cudaMemset(w->bufB, 0xFF, std::max<size_t>(nwords, 1) * 4);
   if (e != cudaSuccess) {
     free_workspace(w);
     w = nullptr;
@@ -124,15 +125,21 @@ LaunchParams base_params(const rac_network *net, Workspace *w, int n_states, int
   P.net = net_dev(net);
   P.n_states = n_states;
   P.bufB = w->bufB;
+  // flag slots are strided by the workspace's capacity, not by this launch's
+  // state count, so launches of different sizes agree on where they are
+  const size_t cap = size_t(w->cap_states);
   P.any = w->flags;
-  P.wipe = P.any + 3 * size_t(n_states);
-  P.chg = P.wipe + 3 * size_t(n_states);
-  P.chgU = P.chg + 3 * size_t(n_states) * net->nb;
+  P.wipe = P.any + 3 * cap;
+  P.chg = P.wipe + 3 * cap;
+  P.chgU = P.chg + 3 * cap * net->nb;
   P.sync = w->sync;
+  P.flag_stride = w->cap_states;
   P.max_sweeps = max_sweeps;
   const int64_t bound = int64_t(net->n) * net->d + 2;
   P.sweep_bound = int32_t(std::min<int64_t>(bound, 0xFFFFF0));
   P.flags = flags;
+  P.n_first = int32_t(std::min<size_t>(net->first.size(), kMaxFirst));
+  for (int32_t i = 0; i < P.n_first; ++i) P.first[i] = net->first[size_t(i)];
   return P;
 }
 
@@ -141,7 +148,7 @@ constexpr uint32_t kKnownFlags = RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL;
 // Largest power of two rows (<= 32) whose slab fits one ring stage.
 int rows_per_slab_for(int dp) {
   int rows = 32;
-  while (rows > 1 && size_t(rows) * 32 * dp * 4 > size_t(kStageBytes)) rows >>= 1;
+  while (rows > 1 && size_t(rows) * 32 * dp * 4 > size_t(kSlabRelBytes)) rows >>= 1;
   return rows;
 }
 
@@ -218,55 +225,64 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
       return RAC_EINVAL;
     }
 
-  // slabs: (I, J, i / rows)
+  // slabs: (I, J, i / rows), each a header followed by its relations
   std::vector<SlabDesc> slabs;
-  std::vector<uint32_t> pmask, roff;
   std::vector<uint32_t> relw;
+  const size_t hdr = size_t(2) * rows;  // pm[rows] + roff[rows], a multiple of 4 words
   try {
-    relw.assign(size_t(n_cons) * dp, 0u);
     size_t i = 0;
     while (i < order.size()) {
       const uint64_t key = order[i].first;
       const uint64_t tile = key >> 10;
       const uint32_t row_group = uint32_t((key >> 5) & 31u) / uint32_t(rows);
-      SlabDesc sd = {};
-      sd.I = uint32_t(tile / uint64_t(nb));
-      sd.J = uint32_t(tile % uint64_t(nb));
-      sd.row0 = row_group * rows;
-      sd.nrows = uint32_t(rows);
-      sd.meta_off = uint32_t(pmask.size());
-      sd.rel_off16 = uint32_t((i * size_t(dp) * 4) / 16);
-      pmask.resize(pmask.size() + rows, 0u);
-      roff.resize(roff.size() + rows, 0u);
+      const uint32_t I = uint32_t(tile / uint64_t(nb)), J = uint32_t(tile % uint64_t(nb));
+      const uint32_t row0 = row_group * uint32_t(rows);
       size_t j = i;
-      uint32_t count = 0;
       while (j < order.size() && (order[j].first >> 10) == tile &&
-             uint32_t((order[j].first >> 5) & 31u) / uint32_t(rows) == row_group) {
-        const uint32_t ri = uint32_t((order[j].first >> 5) & 31u) - sd.row0;
-        const uint32_t cj = uint32_t(order[j].first & 31u);
-        pmask[sd.meta_off + ri] |= 1u << cj;
-        ++count;
-        // relation rows in the (lo, hi) orientation
-        const int64_t c = order[j].second;
-        const bool swap = scope[2 * c] > scope[2 * c + 1];
-        uint32_t *dst = relw.data() + j * size_t(dp);
-        if (!swap) {
-          for (int a = 0; a < d; ++a) dst[a] = rel_bits[c * d + a];
-        } else {
-          for (int a = 0; a < d; ++a) {
-            uint32_t w = 0;
-            for (int b = 0; b < d; ++b) w |= ((rel_bits[c * d + b] >> a) & 1u) << b;
-            dst[a] = w;
-          }
-        }
+             uint32_t((order[j].first >> 5) & 31u) / uint32_t(rows) == row_group)
         ++j;
+      const size_t count = j - i;
+      const size_t base = relw.size();
+      relw.resize(base + hdr + count * size_t(dp), 0u);
+      uint32_t *pm = relw.data() + base;
+      uint32_t *roff = pm + rows;
+      uint32_t *rel = pm + hdr;
+      for (size_t t = i; t < j; ++t) {
+        const uint32_t ri = uint32_t((order[t].first >> 5) & 31u) - row0;
+        pm[ri] |= 1u << uint32_t(order[t].first & 31u);
       }
       uint32_t acc = 0;
       for (int r = 0; r < rows; ++r) {
-        roff[sd.meta_off + r] = acc;
-        acc += uint32_t(__builtin_popcount(pmask[sd.meta_off + r]));
+        roff[r] = acc;
+        acc += uint32_t(__builtin_popcount(pm[r]));
       }
-      sd.nbytes = count * uint32_t(dp) * 4u;
+      // Inside a slab row the relations are stored chunk-major: 16-byte chunk
+      // c (rows 4c..4c+3) of the row's t-th relation sits at chunk c * cnt + t
+      // of the row, so the lanes of a warp, one relation each, read
+      // consecutive chunks (no shared-memory bank conflict).
+      for (size_t t = i; t < j; ++t) {
+        const uint32_t ri = uint32_t((order[t].first >> 5) & 31u) - row0;
+        const uint32_t cnt = uint32_t(__builtin_popcount(pm[ri]));
+        const uint32_t rank = uint32_t(t - i) - roff[ri];
+        uint32_t *row_base = rel + size_t(roff[ri]) * dp;
+        // relation rows in the (lo, hi) orientation
+        const int64_t c = order[t].second;
+        const bool swap = scope[2 * c] > scope[2 * c + 1];
+        for (int a = 0; a < dp; ++a) {
+          uint32_t w = 0;
+          if (a < d && !swap) {
+            w = rel_bits[c * d + a];
+          } else if (a < d) {
+            for (int b = 0; b < d; ++b) w |= ((rel_bits[c * d + b] >> a) & 1u) << b;
+          }
+          row_base[(size_t(a / 4) * cnt + rank) * 4 + (a % 4)] = w;
+        }
+      }
+      SlabDesc sd;
+      sd.rel_off16 = uint32_t(base / 4);
+      sd.nbytes = uint32_t((hdr + count * size_t(dp)) * 4);
+      sd.ij = I | (J << 16);
+      sd.rows = row0 | (uint32_t(rows) << 8);
       slabs.push_back(sd);
       i = j;
     }
@@ -274,7 +290,7 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
     set_error("out of host memory");
     return RAC_ENOMEM;
   }
-  if ((relw.size() * 4) / 16 > 0xFFFFFFFFull) {
+  if (relw.size() / 4 > 0xFFFFFFFFull) {
     set_error("relation store too large");
     return RAC_ENOTSUP;
   }
@@ -292,6 +308,7 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
   net->rows_per_slab = rows;
   net->m = n_cons;
   net->n_slabs = int64_t(slabs.size());
+  net->first.assign(slabs.begin(), slabs.begin() + std::min<size_t>(slabs.size(), kMaxFirst));
   net->rel_bytes = relw.size() * 4;
   cudaError_t e = cudaGetDevice(&net->device);
   auto fail = [&](cudaError_t err, const char *what) {
@@ -312,12 +329,6 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
   if ((e = upload(reinterpret_cast<void **>(&net->d_slabs), slabs.data(),
                   slabs.size() * sizeof(SlabDesc))) != cudaSuccess)
     return fail(e, "upload of the slab table");
-  if ((e = upload(reinterpret_cast<void **>(&net->d_pmask), pmask.data(), pmask.size() * 4)) !=
-      cudaSuccess)
-    return fail(e, "upload of the row masks");
-  if ((e = upload(reinterpret_cast<void **>(&net->d_roff), roff.data(), roff.size() * 4)) !=
-      cudaSuccess)
-    return fail(e, "upload of the row offsets");
   *out = net;
   return RAC_OK;
 }
@@ -328,8 +339,6 @@ void rac_destroy(rac_network *net) {
   net->ws.clear();
   cudaFree(net->d_rel);
   cudaFree(net->d_slabs);
-  cudaFree(net->d_pmask);
-  cudaFree(net->d_roff);
   delete net;
 }
 

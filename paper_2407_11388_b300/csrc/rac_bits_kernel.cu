@@ -112,86 +112,82 @@ __device__ __forceinline__ void named_bar(int id, int nthreads) {
 // Domain words change between sweeps through L2 atomics: read them at L2.
 __device__ __forceinline__ uint32_t ld_dom(const uint32_t *p) { return __ldcg(p); }
 
-// ------------------------- bank-conflict-free order -------------------------
-// Relation r of a stage starts at r * 16 Q bytes.  A quarter warp reading one
-// 16-byte chunk per lane is conflict-free when the 8 chunks fall in distinct
-// 16-byte bank groups; starting lane r's walk at chunk rot(r) makes that hold
-// for any 8 consecutive relations (found by exhaustive search over Q <= 8).
-template <int Q>
-__device__ __forceinline__ int chunk_rot(uint32_t r) {
-  if constexpr (Q == 2 || Q == 6) return (r >> 2) & 1;
-  if constexpr (Q == 4) return (r >> 1) & 3;
-  if constexpr (Q == 8) return r & 7;
-  return 0;
-}
-
-// Rotate the low NBITS bits of v right / left by s (0 < s < NBITS).
-template <int NBITS>
-__device__ __forceinline__ uint32_t rotr_field(uint32_t v, int s) {
-  if constexpr (NBITS == 32) {
-    return __funnelshift_r(v, v, s);
-  } else {
-    const uint32_t mask = (1u << NBITS) - 1u;
-    return ((v >> s) | (v << (NBITS - s))) & mask;
-  }
-}
-template <int NBITS>
-__device__ __forceinline__ uint32_t rotl_field(uint32_t v, int s) {
-  if constexpr (NBITS == 32) {
-    return __funnelshift_l(v, v, s);
-  } else {
-    const uint32_t mask = (1u << NBITS) - 1u;
-    return ((v << s) | (v >> (NBITS - s))) & mask;
-  }
-}
-
-// The support test of one relation (rows a = 0..4Q-1, padding rows are 0):
-//   fwd bit a  = (R[a] & Dy) != 0
-//   rev        = OR over a in Dx of R[a]
-template <int Q>
-__device__ __forceinline__ void support_relation(const uint4 *rel, int rot, uint32_t Dx,
+// The support test of one relation, rows a = 0..4Q-1 (padding rows are 0),
+// read as Q 16-byte chunks `stride` chunks apart:
+//   fwd bit a  = (R[a] & Dy) != 0        (Sup_xy[a] > 0, Fig. 1)
+//   rev        = OR over a in Dx of R[a] (bit b: (y,b) has a support in Dx)
+// Two independent accumulators per result keep the OR chains short.
+template <int Q, bool kDxFull>
+__device__ __forceinline__ void support_relation(const uint4 *rel, uint32_t stride, uint32_t Dx,
                                                  uint32_t Dy, uint32_t &fwd, uint32_t &rev) {
-  constexpr int NBITS = 4 * Q;
-  const uint32_t dx = rot ? rotr_field<NBITS>(Dx, 4 * rot) : Dx;
-  uint32_t f = 0, r = 0;
+  uint32_t f0 = 0, f1 = 0, r0 = 0, r1 = 0;
 #pragma unroll
   for (int c = 0; c < Q; ++c) {
-    int cc = c + rot;
-    if (cc >= Q) cc -= Q;
-    const uint4 w = rel[cc];
-    f |= ((w.x & Dy) != 0u ? 1u : 0u) << (4 * c + 0);
-    f |= ((w.y & Dy) != 0u ? 1u : 0u) << (4 * c + 1);
-    f |= ((w.z & Dy) != 0u ? 1u : 0u) << (4 * c + 2);
-    f |= ((w.w & Dy) != 0u ? 1u : 0u) << (4 * c + 3);
-    if (dx & (1u << (4 * c + 0))) r |= w.x;
-    if (dx & (1u << (4 * c + 1))) r |= w.y;
-    if (dx & (1u << (4 * c + 2))) r |= w.z;
-    if (dx & (1u << (4 * c + 3))) r |= w.w;
+    const uint4 w = rel[c * stride];
+    if ((w.x & Dy) != 0u) f0 |= 1u << (4 * c + 0);
+    if ((w.y & Dy) != 0u) f1 |= 1u << (4 * c + 1);
+    if ((w.z & Dy) != 0u) f0 |= 1u << (4 * c + 2);
+    if ((w.w & Dy) != 0u) f1 |= 1u << (4 * c + 3);
+    if (kDxFull) {  // every row of R is in Dx (rows >= d are zero)
+      r0 |= w.x | w.z;
+      r1 |= w.y | w.w;
+    } else {
+      r0 |= w.x & (0u - ((Dx >> (4 * c + 0)) & 1u));
+      r1 |= w.y & (0u - ((Dx >> (4 * c + 1)) & 1u));
+      r0 |= w.z & (0u - ((Dx >> (4 * c + 2)) & 1u));
+      r1 |= w.w & (0u - ((Dx >> (4 * c + 3)) & 1u));
+    }
   }
-  fwd = rot ? rotl_field<NBITS>(f, 4 * rot) : f;
-  rev = r;
+  fwd = f0 | f1;
+  rev = r0 | r1;
 }
+
+struct StageInfo {
+  int32_t sl;  // slab index, -1 = end of the sweep's slabs
+  uint32_t ij, rows, pad;
+};
 
 struct Smem {
   uint64_t full[kStages];
   uint64_t empty[kStages];
-  int32_t stage_slab[kStages];
-  uint32_t bar0_ok;
+  StageInfo stage[kStages];
+  uint32_t stage_ok[kStages];
+  uint32_t base;        // barrier k uses slot (base + k) % 3
+  uint32_t poisoned;    // an earlier launch on this workspace failed
   uint32_t all_done;
   uint32_t abort;
+  uint32_t dom_cached;
+  uint32_t any_total;   // CTAs that removed a value in the last sweep
+  uint32_t wipe_total;  // CTAs that emptied a domain in the last sweep
+  uint32_t failed;      // a wait of this CTA gave up, or another CTA reported one
+  uint32_t cta_any;
+  uint32_t cta_wipe;
   uint32_t red[2][kConsumerWarps][32];
   uint32_t st_info[kMaxStatesPerLaunch];  // see kInfo* below
   uint8_t any_loc[kMaxStatesPerLaunch];
   uint8_t wipe_loc[kMaxStatesPerLaunch];
+  SlabDesc desc[kDescCache];
+  uint32_t dom[kDomWords];  // D_{k-1} of every running state, when it fits
 };
+static_assert(kStages % kGroups == 0, "each ring stage belongs to one consumer group");
+static_assert(size_t(kStages) * kStageBytes + sizeof(Smem) <= 232448,
+              "shared memory of the bit-packed kernel exceeds 227 KB");
 // st_info: bits 0..23 sweep at which the state finished (0 = running),
 // bit 24 result in buffer B, bit 25 some domain emptied so far,
-// bits 28..30 status code + 4.
+// bits 27..31 status code + 8.
 constexpr uint32_t kInfoSweepMask = 0xFFFFFFu;
 constexpr uint32_t kInfoResB = 1u << 24;
 constexpr uint32_t kInfoWiped = 1u << 25;
 __device__ __forceinline__ uint32_t info_status_bits(int st) { return uint32_t(st + 8) << 27; }
 __device__ __forceinline__ int info_status(uint32_t v) { return int((v >> 27) & 31u) - 8; }
+
+// named barriers: 1 = all consumer warps, 2 + cg = the warps of consumer group
+// cg, 2 + kGroups + 2 cg + g = the warps of state group g (g < 2) inside
+// consumer group cg (only needed when a state group has several warps)
+constexpr int kAllConsumersBar = 1;
+__device__ __forceinline__ int group_bar(int cg) { return 2 + cg; }
+__device__ __forceinline__ int state_group_bar(int cg, int g) { return 2 + kGroups + 2 * cg + g; }
+static_assert(2 + kGroups + 2 * kGroups <= 16, "named barrier ids");
 
 struct StateView {
   const uint32_t *C;  // D_{k-1}
@@ -222,97 +218,110 @@ __device__ __forceinline__ StateView state_view(const LaunchParams &P, int s, in
   return v;
 }
 
-__device__ __forceinline__ void wait_bar0(Smem &S, const LaunchParams &P) {
-  if (S.bar0_ok) return;
-  const uint64_t t0 = global_timer();
-  while (ld_acquire(&P.sync->bar0) < gridDim.x) {
-    if (global_timer() - t0 > kWaitLimitNs) {
-      atomicOr(&P.sync->err, kErrGridWait);
-      break;
-    }
-    __nanosleep(32);
-  }
-  S.bar0_ok = 1;
-}
-
 // Apply a removal: D_k[v] &= keep, where keep is a strict subset of D_{k-1}[v].
-__device__ __forceinline__ void remove_values(Smem &S, const LaunchParams &P, int s, int k,
+__device__ __forceinline__ void remove_values(Smem &S, const LaunchParams &P, int s, int slot_w,
                                               uint32_t *T, uint32_t v, uint32_t keep) {
-  if (k == 1) wait_bar0(S, P);
   const uint32_t old = atomicAnd(T + v, keep);
   S.any_loc[s] = 1;
   if (old != 0u && (old & keep) == 0u) S.wipe_loc[s] = 1;
-  const int slot = k % 3;
   const int nb = P.net.nb;
   const uint32_t bit = 1u << (v & 31u);
-  atomicOr(P.chg + (int64_t(slot) * P.n_states + s) * nb + (v >> 5), bit);
-  if (P.flags & RAC_INCREMENTAL) atomicOr(P.chgU + int64_t(slot) * nb + (v >> 5), bit);
+  atomicOr(P.chg + (int64_t(slot_w) * P.flag_stride + s) * nb + (v >> 5), bit);
+  if (P.flags & RAC_INCREMENTAL) atomicOr(P.chgU + int64_t(slot_w) * nb + (v >> 5), bit);
 }
 
-// Bounded grid barrier over all CTAs (co-resident: cooperative launch).
-__device__ void grid_barrier(const LaunchParams &P, uint32_t target) {
+// Bounded grid barrier over all CTAs (co-resident: cooperative launch).  The
+// arrival also counts the CTAs that removed values, emptied a domain or failed
+// a wait in the sweep; the totals land in S.any_total, S.wipe_total and
+// S.failed, so no flag needs a separate load after the barrier.
+__device__ void grid_barrier(Smem &S, const LaunchParams &P, int slot) {
   __syncthreads();
   if (threadIdx.x == 0) {
+    unsigned long long *w = &P.sync->bar[slot];
+    constexpr unsigned long long kMask = (1ull << kBarCountBits) - 1ull;
+    const unsigned long long mine = 1ull |
+                                    (uint64_t(S.cta_any ? 1u : 0u) << kBarCountBits) |
+                                    (uint64_t(S.cta_wipe ? 1u : 0u) << (2 * kBarCountBits)) |
+                                    (uint64_t(S.failed ? 1u : 0u) << (3 * kBarCountBits));
     __threadfence();
-    atomicAdd(&P.sync->bar_main, 1u);
+    unsigned long long v = atomicAdd(w, mine) + mine;
     const uint64_t t0 = global_timer();
-    for (;;) {
-      if (ld_acquire(&P.sync->bar_main) >= target) break;
-      if (ld_acquire(&P.sync->err) != 0u) break;
+    while ((v & kMask) < gridDim.x) {
+      if (ld_acquire(&P.sync->err) != 0u) {
+        S.failed = 1;
+        break;
+      }
       if (global_timer() - t0 > kWaitLimitNs) {
         atomicOr(&P.sync->err, kErrGridWait);
+        S.failed = 1;
         break;
       }
       __nanosleep(20);
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(w) : "memory");
     }
     __threadfence();
+    S.any_total = uint32_t((v >> kBarCountBits) & kMask);
+    S.wipe_total = uint32_t((v >> (2 * kBarCountBits)) & kMask);
+    if ((v >> (3 * kBarCountBits)) & kMask) S.failed = 1;
   }
   __syncthreads();
 }
 
 template <int Q>
-__device__ void consume_slab(Smem &S, const LaunchParams &P, const uint4 *stage, int sl, int k,
-                             int warp, int lane, uint32_t &red_iter) {
+__device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char *stage,
+                             const StageInfo &si, int k, int slot_r, int slot_w, int warp,
+                             int lane, uint32_t &red_iter) {
+  const int cg = warp / kGroupWarps, lw = warp % kGroupWarps;
   const NetDev &N = P.net;
-  const SlabDesc sd = N.slabs[sl];
   const int n = N.n;
-  const int y = int(sd.J) * 32 + lane;
+  const uint32_t I = si.ij & 0xFFFFu, J = si.ij >> 16;
+  const uint32_t row0 = si.rows & 0xFFu, nrows = si.rows >> 8;
+  const uint32_t *hdr = reinterpret_cast<const uint32_t *>(stage);
+  const uint4 *rel = reinterpret_cast<const uint4 *>(stage) + (2 * nrows) / 4;
+  const int y = int(J) * 32 + lane;
   const bool y_ok = y < n;
   // states are split over warp groups, rows over the warps of a group
-  const int wps = P.n_states >= 8 ? 1 : (P.n_states >= 4 ? 2 : (P.n_states >= 2 ? 4 : 8));
-  const int groups = kConsumerWarps / wps;
-  const int g = warp / wps, sub = warp % wps;
+  static_assert(kGroupWarps == 4, "state grouping below assumes 4 warps per consumer group");
+  const int wps = P.n_states >= 4 ? 1 : (P.n_states >= 2 ? 2 : 4);
+  const int groups = kGroupWarps / wps;
+  const int g = lw / wps, sub = lw % wps;
+  const uint32_t dfull = N.d >= 32 ? kFull : ((1u << N.d) - 1u);
   const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
-  const uint32_t rowmask =
-      (sd.nrows >= 32 ? kFull : ((1u << sd.nrows) - 1u)) << sd.row0;
-  const int slot_r = (k + 2) % 3;
+  const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
+  const bool cached = S.dom_cached != 0;
   for (int s = g; s < P.n_states; s += groups) {
     if (S.st_info[s] & kInfoSweepMask) continue;  // finished state
     if (incr) {
-      const uint32_t *ch = P.chg + (int64_t(slot_r) * P.n_states + s) * N.nb;
-      if (ld_dom(ch + sd.J) == 0u && (ld_dom(ch + sd.I) & rowmask) == 0u) continue;
+      const uint32_t *ch = P.chg + (int64_t(slot_r) * P.flag_stride + s) * N.nb;
+      if (ld_dom(ch + J) == 0u && (ld_dom(ch + I) & rowmask) == 0u) continue;
     }
     const StateView V = state_view(P, s, k);
-    const uint32_t Dy = y_ok ? ld_dom(V.C + y) : 0u;
+    const uint32_t *Dc = cached ? S.dom + s * n : V.C;
+    const uint32_t Dy = y_ok ? (cached ? Dc[y] : ld_dom(Dc + y)) : 0u;
     uint32_t racc = kFull;
-    for (int r = sub; r < int(sd.nrows); r += wps) {
-      const uint32_t pm = __ldg(N.pmask + sd.meta_off + r);
+    for (int r = sub; r < int(nrows); r += wps) {
+      const uint32_t pm = hdr[r];
       if (pm == 0u) continue;
-      const int x = int(sd.I) * 32 + int(sd.row0) + r;
-      const uint32_t Dx = ld_dom(V.C + x);
+      const int x = int(I) * 32 + int(row0) + r;
+      const uint32_t Dx = cached ? Dc[x] : ld_dom(Dc + x);
       uint32_t fwd = kFull, rev = kFull;
       if ((pm >> lane) & 1u) {
-        const uint32_t ridx = __ldg(N.roff + sd.meta_off + r) + __popc(pm & lanemask_lt());
-        support_relation<Q>(stage + ridx * Q, chunk_rot<Q>(ridx), Dx, Dy, fwd, rev);
+        // this lane's relation: rank t in the row, chunk c at c * cnt + t
+        const uint32_t t = __popc(pm & lanemask_lt());
+        const uint4 *mine = rel + hdr[nrows + r] * Q + t;
+        if (Dx == dfull)
+          support_relation<Q, true>(mine, __popc(pm), Dx, Dy, fwd, rev);
+        else
+          support_relation<Q, false>(mine, __popc(pm), Dx, Dy, fwd, rev);
       }
       const uint32_t keep_x = __reduce_and_sync(kFull, fwd) & Dx;
-      if (keep_x != Dx && lane == 0) remove_values(S, P, s, k, V.T, uint32_t(x), keep_x);
+      if (keep_x != Dx && lane == 0) remove_values(S, P, s, slot_w, V.T, uint32_t(x), keep_x);
       racc &= rev;
     }
     if (wps > 1) {
       const int buf = red_iter & 1;
       S.red[buf][warp][lane] = racc;
-      named_bar(1 + g, wps * 32);
+      named_bar(state_group_bar(cg, g), wps * 32);
       if (sub == 0) {
         for (int j = 1; j < wps; ++j) racc &= S.red[buf][warp + j][lane];
       }
@@ -320,7 +329,7 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const uint4 *stage,
     }
     if (sub == 0 && y_ok) {
       const uint32_t keep_y = racc & Dy;
-      if (keep_y != Dy) remove_values(S, P, s, k, V.T, uint32_t(y), keep_y);
+      if (keep_y != Dy) remove_values(S, P, s, slot_w, V.T, uint32_t(y), keep_y);
     }
   }
 }
@@ -337,16 +346,23 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
   const int n = N.n;
   const int64_t gtid = int64_t(cta) * blockDim.x + tid;
   const int64_t gstride = int64_t(G) * blockDim.x;
+  const int my_slabs = cta < N.n_slabs ? (N.n_slabs - cta + G - 1) / G : 0;
+  const bool is_producer = warp == kConsumerWarps;
+  // consumer thread index and grid-wide consumer stride
+  const int ctid = tid;
+  const int64_t cgtid = int64_t(cta) * (kConsumerWarps * 32) + ctid;
+  const int64_t cgstride = int64_t(G) * (kConsumerWarps * 32);
 
   if (tid == 0) {
     for (int i = 0; i < kStages; ++i) {
       mbar_init(&S.full[i], 1);
-      mbar_init(&S.empty[i], kConsumerWarps);
+      mbar_init(&S.empty[i], kGroupWarps);
     }
     fence_mbar_init();
-    S.bar0_ok = 0;
     S.all_done = 0;
     S.abort = 0;
+    S.failed = 0;
+    S.dom_cached = int64_t(B) * n <= kDomWords ? 1u : 0u;
   }
   for (int s = tid; s < B; s += blockDim.x) {
     S.st_info[s] = 0;
@@ -355,177 +371,233 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
   }
   __syncthreads();
 
-  // Phase 0: B := dom_in, A := dom_in, note empty input domains, clear the
-  // flag slots written by sweeps 1 and 2.  Removals of sweep 1 wait for all
-  // CTAs to pass this point (bar0).
-  for (int64_t i = gtid; i < int64_t(B) * n; i += gstride) {
-    const int s = int(i / n), x = int(i % n);
-    const int64_t off = state_offset(P, s);
-    const uint32_t v = P.dom_in[off + x];
-    P.bufB[int64_t(s) * n + x] = v;
-    if (P.dom_out != P.dom_in) P.dom_out[off + x] = v;
-    if (v == 0u) S.wipe_loc[s] = 1;  // D_1 will hold this empty domain
-  }
-  {
-    const int64_t per_slot = int64_t(B) * N.nb;
-    for (int slot = 1; slot <= 2; ++slot) {
-      for (int64_t i = gtid; i < B; i += gstride) {
-        P.any[slot * B + i] = 0u;
-        P.wipe[slot * B + i] = 0u;
-      }
-      for (int64_t i = gtid; i < per_slot; i += gstride) P.chg[slot * per_slot + i] = 0u;
-      for (int64_t i = gtid; i < N.nb; i += gstride) P.chgU[int64_t(slot) * N.nb + i] = 0u;
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    atomicAdd(&P.sync->bar0, 1u);
-  }
-
-  uint32_t ring_it = 0;   // consumer-side position in the ring
+  uint32_t ring_it = 0;   // consumer-side position in the ring (per consumer group)
   uint32_t prod_it = 0;   // producer-side position in the ring
   uint32_t red_iter = 0;  // parity of the cross-warp reduction buffer
-  int k = 0;
-  for (;;) {
-    ++k;
-    const int slot_w = k % 3, slot_r = (k + 2) % 3, slot_c = (k + 1) % 3;
-    if (k >= 2) {
-      // clear the slot written next sweep (last read in sweep k-1)
-      const int64_t per_slot = int64_t(B) * N.nb;
-      for (int64_t i = gtid; i < B; i += gstride) {
-        P.any[slot_c * B + i] = 0u;
-        P.wipe[slot_c * B + i] = 0u;
-      }
-      for (int64_t i = gtid; i < per_slot; i += gstride) P.chg[slot_c * per_slot + i] = 0u;
-      for (int64_t i = gtid; i < N.nb; i += gstride) P.chgU[int64_t(slot_c) * N.nb + i] = 0u;
-      // owner step: T still holds D_{k-2}; AND D_{k-1} into it where it differs
-      for (int64_t i = gtid; i < per_slot; i += gstride) {
-        const int s = int(i / N.nb), blk = int(i % N.nb);
-        if (S.st_info[s] & kInfoSweepMask) continue;
-        uint32_t w = ld_dom(P.chg + slot_r * per_slot + i);
-        if (w == 0u) continue;
-        const StateView V = state_view(P, s, k);
-        while (w) {
-          const int b = __ffs(w) - 1;
-          w &= w - 1u;
-          const int x = blk * 32 + b;
-          atomicAnd(V.T + x, ld_dom(V.C + x));
-        }
-      }
+  if (is_producer) {
+    if (lane == 0 && my_slabs > 0 && cta < P.n_first) {
+      // the first slab's descriptor came with the launch: no load before it
+      const SlabDesc sd = P.first[cta];
+      S.stage[0].sl = cta;
+      S.stage[0].ij = sd.ij;
+      S.stage[0].rows = sd.rows;
+      mbar_arrive_expect_tx(&S.full[0], sd.nbytes);
+      bulk_copy_g2s(ring, N.rel + size_t(sd.rel_off16), sd.nbytes, &S.full[0]);
+      prod_it = 1;
     }
+    prod_it = __shfl_sync(kFull, prod_it, 0);
+    // this CTA's slab descriptors (slabs cta, cta + G, ...)
+    for (int j = lane; j < my_slabs && j < kDescCache; j += 32) S.desc[j] = N.slabs[cta + j * G];
+    __syncwarp();
+  } else if (ctid == 0) {
+    S.base = ld_acquire(&P.sync->base);
+    S.poisoned = ld_acquire(&P.sync->err) != 0u ? 1u : 0u;
+  }
+  __syncthreads();
+  const uint32_t base = S.base;
 
-    if (warp == kConsumerWarps) {
-      // producer: stream this CTA's active slabs through the ring
-      if (lane == 0) {
-        const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
-        const uint32_t *cu = P.chgU + int64_t(slot_r) * N.nb;
-        bool ok = true;
-        for (int sl = cta; sl < N.n_slabs && ok; sl += G) {
-          const SlabDesc sd = N.slabs[sl];
-          if (incr) {
-            const uint32_t rowmask =
-                (sd.nrows >= 32 ? kFull : ((1u << sd.nrows) - 1u)) << sd.row0;
-            if (ld_dom(cu + sd.J) == 0u && (ld_dom(cu + sd.I) & rowmask) == 0u) continue;
+  int k = 0;
+  if (S.poisoned) {
+    S.failed = 1;
+  } else {
+    for (;;) {
+      ++k;
+      const int slot_w = int((base + k) % 3), slot_r = int((base + k + 2) % 3);
+      const int slot_c = int((base + k + 1) % 3);
+
+      if (is_producer) {
+        // producer: stream this CTA's active slabs through the ring
+        if (lane == 0) {
+          if (cta == 0) P.sync->bar[slot_c] = 0ull;  // last used two sweeps (or a launch) ago
+          const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
+          const uint32_t *cu = P.chgU + int64_t(slot_r) * N.nb;
+          bool ok = true;
+          // in sweep 1 the first slab may already be on its way
+          for (int j = (k == 1 && prod_it == 1) ? 1 : 0; j < my_slabs; ++j) {
+            const int sl = cta + j * G;
+            const SlabDesc sd = j < kDescCache ? S.desc[j] : N.slabs[sl];
+            if (incr) {
+              const uint32_t I = sd.ij & 0xFFFFu, J = sd.ij >> 16;
+              const uint32_t row0 = sd.rows & 0xFFu, nrows = sd.rows >> 8;
+              const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
+              if (ld_dom(cu + J) == 0u && (ld_dom(cu + I) & rowmask) == 0u) continue;
+            }
+            const int stg = prod_it % kStages;
+            const uint32_t par = (prod_it / kStages) & 1u;
+            if (!mbar_wait(&S.empty[stg], par ^ 1u, P.sync)) {
+              ok = false;
+              break;
+            }
+            S.stage[stg].sl = sl;
+            S.stage[stg].ij = sd.ij;
+            S.stage[stg].rows = sd.rows;
+            mbar_arrive_expect_tx(&S.full[stg], sd.nbytes);
+            bulk_copy_g2s(ring + size_t(stg) * kStageBytes, N.rel + size_t(sd.rel_off16),
+                          sd.nbytes, &S.full[stg]);
+            ++prod_it;
           }
-          const int stg = prod_it % kStages;
-          const uint32_t par = (prod_it / kStages) & 1u;
-          if (!mbar_wait(&S.empty[stg], par ^ 1u, P.sync)) {
-            ok = false;
+          // end of this sweep's slabs: one marker for each consumer group
+          for (int e = 0; e < kGroups && ok; ++e) {
+            const int stg = prod_it % kStages;
+            const uint32_t par = (prod_it / kStages) & 1u;
+            if (!mbar_wait(&S.empty[stg], par ^ 1u, P.sync)) {
+              ok = false;
+              break;
+            }
+            S.stage[stg].sl = -1;
+            mbar_arrive(&S.full[stg]);
+            ++prod_it;
+          }
+          if (!ok) S.abort = 1;
+        }
+      } else {
+        const int64_t stride = P.flag_stride;
+        // this sweep's domains D_{k-1} into shared memory
+        if (S.dom_cached) {
+          for (int i = ctid; i < B * n; i += kConsumerWarps * 32) {
+            const int s = i / n;
+            if (S.st_info[s] & kInfoSweepMask) continue;
+            S.dom[i] = ld_dom(state_view(P, s, k).C + (i - s * n));
+          }
+        }
+        // clear the slot written next sweep (last read two sweeps ago)
+        for (int64_t i = cgtid; i < stride; i += cgstride) {
+          P.any[slot_c * stride + i] = 0u;
+          P.wipe[slot_c * stride + i] = 0u;
+        }
+        for (int64_t i = cgtid; i < stride * N.nb; i += cgstride)
+          P.chg[slot_c * stride * N.nb + i] = 0u;
+        for (int64_t i = cgtid; i < N.nb; i += cgstride) P.chgU[int64_t(slot_c) * N.nb + i] = 0u;
+        named_bar(kAllConsumersBar, kConsumerWarps * 32);
+        if (k == 1) {
+          // A := dom_in; B (all ones between launches) &= dom_in -- an AND,
+          // so it needs no ordering against this sweep's removals; note
+          // empty input domains.
+          for (int64_t i = cgtid; i < int64_t(B) * n; i += cgstride) {
+            const int s = int(i / n), x = int(i % n);
+            const int64_t off = state_offset(P, s);
+            const uint32_t v = S.dom_cached ? S.dom[i] : P.dom_in[off + x];
+            atomicAnd(P.bufB + i, v);
+            if (P.dom_out != P.dom_in) P.dom_out[off + x] = v;
+            if (v == 0u) S.wipe_loc[s] = 1;  // D_1 will hold this empty domain
+          }
+        } else {
+          // owner step: T still holds D_{k-2}; AND D_{k-1} into it where it differs
+          for (int64_t i = cgtid; i < int64_t(B) * N.nb; i += cgstride) {
+            const int s = int(i / N.nb), blk = int(i % N.nb);
+            if (S.st_info[s] & kInfoSweepMask) continue;
+            uint32_t w = ld_dom(P.chg + (int64_t(slot_r) * stride + s) * N.nb + blk);
+            if (w == 0u) continue;
+            const StateView V = state_view(P, s, k);
+            while (w) {
+              const int b = __ffs(w) - 1;
+              w &= w - 1u;
+              const int x = blk * 32 + b;
+              atomicAnd(V.T + x, S.dom_cached ? S.dom[s * n + x] : ld_dom(V.C + x));
+            }
+          }
+        }
+        // consumer group cg takes ring positions cg, cg + kGroups, ...
+        const int cg = warp / kGroupWarps;
+        const bool group_leader = (warp % kGroupWarps) == 0 && lane == 0;
+        for (;;) {
+          const uint32_t pos = ring_it * kGroups + cg;
+          const int stg = pos % kStages;
+          const uint32_t par = (pos / kStages) & 1u;
+          // One thread takes the bounded wait and every warp of the group
+          // follows its outcome, so a wait that gives up never leaves a peer
+          // warp blocked on a named barrier inside the slab evaluation.
+          if (group_leader) S.stage_ok[stg] = mbar_wait(&S.full[stg], par, P.sync) ? 1u : 0u;
+          named_bar(group_bar(cg), kGroupWarps * 32);
+          if (!S.stage_ok[stg]) {
+            if (group_leader) S.abort = 1;
             break;
           }
-          S.stage_slab[stg] = sl;
-          mbar_arrive_expect_tx(&S.full[stg], sd.nbytes);
-          bulk_copy_g2s(ring + size_t(stg) * kStageBytes, N.rel + size_t(sd.rel_off16),
-                        sd.nbytes, &S.full[stg]);
-          ++prod_it;
-        }
-        const int stg = prod_it % kStages;
-        const uint32_t par = (prod_it / kStages) & 1u;
-        if (ok && mbar_wait(&S.empty[stg], par ^ 1u, P.sync)) {
-          S.stage_slab[stg] = -1;  // end of this sweep's slabs
-          mbar_arrive(&S.full[stg]);
-          ++prod_it;
-        } else {
-          S.abort = 1;
+          if (lane == 0) mbar_try_wait(&S.full[stg], par);  // completed: acquire the copy
+          __syncwarp();
+          const StageInfo si = S.stage[stg];
+          if (si.sl >= 0)
+            consume_slab<Q>(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_r, slot_w, warp,
+                            lane, red_iter);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&S.empty[stg]);
+          ++ring_it;
+          if (si.sl < 0) break;
         }
       }
-    } else {
-      for (;;) {
-        const int stg = ring_it % kStages;
-        const uint32_t par = (ring_it / kStages) & 1u;
-        bool ok = true;
-        if (lane == 0) ok = mbar_wait(&S.full[stg], par, P.sync);
-        ok = __shfl_sync(kFull, ok ? 1 : 0, 0) != 0;
-        if (!ok || S.abort) break;
-        const int sl = S.stage_slab[stg];
-        if (sl >= 0) {
-          consume_slab<Q>(S, P, reinterpret_cast<const uint4 *>(ring + size_t(stg) * kStageBytes),
-                          sl, k, warp, lane, red_iter);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.empty[stg]);
-        ++ring_it;
-        if (sl < 0) break;
-      }
-    }
-    __syncthreads();
+      __syncthreads();
 
-    // publish this CTA's per-state flags for sweep k
-    if (k == 1 && tid == 0) wait_bar0(S, P);
-    __syncthreads();
-    for (int s = tid; s < B; s += blockDim.x) {
-      if (S.any_loc[s]) {
-        atomicOr(P.any + slot_w * B + s, 1u);
-        S.any_loc[s] = 0;
+      // this CTA's flags for sweep k (per state only when there are several)
+      if (tid == 0) {
+        S.cta_any = 0;
+        S.cta_wipe = 0;
       }
-      if (S.wipe_loc[s]) {
-        atomicOr(P.wipe + slot_w * B + s, 1u);
-        S.wipe_loc[s] = 0;
+      __syncthreads();
+      for (int s = tid; s < B; s += blockDim.x) {
+        if (S.any_loc[s]) {
+          if (B > 1) atomicOr(P.any + slot_w * P.flag_stride + s, 1u);
+          S.cta_any = 1;
+          S.any_loc[s] = 0;
+        }
+        if (S.wipe_loc[s]) {
+          if (B > 1) atomicOr(P.wipe + slot_w * P.flag_stride + s, 1u);
+          S.cta_wipe = 1;
+          S.wipe_loc[s] = 0;
+        }
       }
-    }
-    grid_barrier(P, uint32_t(k) * uint32_t(G));
-    if (ld_acquire(&P.sync->err) != 0u || S.abort) break;
+      if (S.abort) S.failed = 1;
+      grid_barrier(S, P, slot_w);
+      if (S.failed) break;
 
-    // decisions (every CTA reads the same flags and takes the same ones)
-    const bool stop = (P.flags & RAC_STOP_ON_WIPEOUT) != 0;
-    for (int s = tid; s < B; s += blockDim.x) {
-      uint32_t info = S.st_info[s];
-      if (info & kInfoSweepMask) continue;
-      const bool any = ld_dom(P.any + slot_w * B + s) != 0u;
-      const bool wp = ld_dom(P.wipe + slot_w * B + s) != 0u;
-      if (wp) info |= kInfoWiped;
-      const uint32_t t_is_b = (k & 1) ? kInfoResB : 0u;           // T of sweep k
-      const uint32_t c_is_b = (k >= 2 && !(k & 1)) ? kInfoResB : 0u;  // C of sweep k
-      if (stop && wp) {
-        info |= uint32_t(k) | t_is_b | info_status_bits(RAC_WIPEOUT);
-      } else if (!any) {
-        info |= uint32_t(k) | c_is_b |
-                info_status_bits((info & kInfoWiped) ? RAC_WIPEOUT : RAC_OK);
-      } else if ((P.max_sweeps > 0 && k >= P.max_sweeps) || k >= P.sweep_bound) {
-        info |= uint32_t(k) | t_is_b | info_status_bits(RAC_ETIMEOUT);
-        if (k >= P.sweep_bound && !(P.max_sweeps > 0 && k >= P.max_sweeps) && cta == 0)
-          atomicOr(&P.sync->err, kErrSweepBound);
+      // decisions (every CTA reads the same flags and takes the same ones)
+      const bool stop = (P.flags & RAC_STOP_ON_WIPEOUT) != 0;
+      const bool any_at_all = S.any_total != 0u, wipe_at_all = S.wipe_total != 0u;
+      for (int s = tid; s < B; s += blockDim.x) {
+        uint32_t info = S.st_info[s];
+        if (info & kInfoSweepMask) continue;
+        bool any = any_at_all, wp = wipe_at_all;
+        if (B > 1) {
+          any = any && ld_dom(P.any + slot_w * P.flag_stride + s) != 0u;
+          wp = wp && ld_dom(P.wipe + slot_w * P.flag_stride + s) != 0u;
+        }
+        if (wp) info |= kInfoWiped;
+        const uint32_t t_is_b = (k & 1) ? kInfoResB : 0u;               // T of sweep k
+        const uint32_t c_is_b = (k >= 2 && !(k & 1)) ? kInfoResB : 0u;  // C of sweep k
+        if (stop && wp) {
+          info |= uint32_t(k) | t_is_b | info_status_bits(RAC_WIPEOUT);
+        } else if (!any) {
+          info |= uint32_t(k) | c_is_b |
+                  info_status_bits((info & kInfoWiped) ? RAC_WIPEOUT : RAC_OK);
+        } else if ((P.max_sweeps > 0 && k >= P.max_sweeps) || k >= P.sweep_bound) {
+          info |= uint32_t(k) | t_is_b | info_status_bits(RAC_ETIMEOUT);
+        }
+        S.st_info[s] = info;
       }
-      S.st_info[s] = info;
+      if (tid == 0) S.all_done = 1;
+      __syncthreads();
+      for (int s = tid; s < B; s += blockDim.x)
+        if (!(S.st_info[s] & kInfoSweepMask)) S.all_done = 0;
+      __syncthreads();
+      if (S.all_done) break;
     }
-    if (tid == 0) S.all_done = 1;
-    __syncthreads();
-    for (int s = tid; s < B; s += blockDim.x)
-      if (!(S.st_info[s] & kInfoSweepMask)) S.all_done = 0;
-    __syncthreads();
-    if (S.all_done) break;
   }
 
-  // Epilogue: results that ended in buffer B move to dom_out.
-  const bool failed = ld_acquire(&P.sync->err) != 0u || S.abort;
-  if (!failed) {
+  // Epilogue: results that ended in buffer B move to dom_out and B goes back
+  // to all ones.  The next launch on this workspace starts at the barrier
+  // slot after this launch's last one (see Sync).
+  if (S.abort) S.failed = 1;
+  __syncthreads();
+  const bool failed = S.failed != 0u;
+  if (!S.poisoned) {
     for (int64_t i = gtid; i < int64_t(B) * n; i += gstride) {
       const int s = int(i / n), x = int(i % n);
-      if (S.st_info[s] & kInfoResB) P.dom_out[state_offset(P, s) + x] = ld_dom(P.bufB + i);
+      if (!failed && (S.st_info[s] & kInfoResB))
+        P.dom_out[state_offset(P, s) + x] = ld_dom(P.bufB + i);
+      P.bufB[i] = kFull;
     }
   }
   if (cta == 0) {
+    if (tid == 0 && !failed) P.sync->base = (base + uint32_t(k)) % 3u;
     for (int s = tid; s < B; s += blockDim.x) {
       const uint32_t info = S.st_info[s];
       const int idx = P.contiguous ? s : P.res_idx[s];
@@ -533,24 +605,13 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
       P.status[idx] = failed ? RAC_EBARRIER : info_status(info);
     }
   }
-  // Drain copies still in flight (only after a failed wait), then leave; the
-  // last CTA out resets the sync words for the next launch on this workspace.
-  if (warp == kConsumerWarps && lane == 0) {
+  if (failed && tid == 0) atomicOr(&P.sync->err, kErrCopyWait);  // poison (idempotent)
+  // Drain copies still in flight (only after a failed wait or on a poisoned
+  // workspace) before the CTA's shared memory goes away.
+  if (is_producer && lane == 0) {
     const uint32_t first = prod_it > uint32_t(kStages) ? prod_it - kStages : 0u;
     for (uint32_t j = first; j < prod_it; ++j)
       mbar_wait(&S.full[j % kStages], (j / kStages) & 1u, P.sync);
-  }
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    const uint32_t prev = atomicAdd(&P.sync->exit_count, 1u);
-    if (prev == uint32_t(G) - 1u) {
-      P.sync->bar0 = 0u;
-      P.sync->bar_main = 0u;
-      P.sync->err = 0u;
-      __threadfence();
-      P.sync->exit_count = 0u;
-    }
   }
 }
 

@@ -19,47 +19,69 @@ namespace rac {
 // Variables are grouped in blocks of 32.  Each constraint is stored once, as
 // R_lo,hi with lo < hi (rows = values of lo, bit b of a row = value b of hi),
 // in tile (I, J) = (lo / 32, hi / 32), I <= J.  A tile is cut into slabs of
-// `rows_per_slab` consecutive rows (values of i = lo % 32); inside a slab the
-// relations are stored row by row, and inside a row by increasing column
-// j = hi % 32, present pairs only.  A relation occupies dp = round_up(d, 4)
-// words (row a in word a, rows >= d zero), so every relation and every slab
-// starts on a 16-byte boundary and a slab is one contiguous bulk copy.
+// `rows_per_slab` consecutive rows (values of i = lo % 32).  A slab is one
+// contiguous, 16-byte aligned record of the relation store:
+//   header:    pm[rows]   bit j set iff the pair (32 I + row0 + r, 32 J + j)
+//                         is constrained,
+//              roff[rows] index of row r's first relation in the slab,
+//   relations: row by row; a row's cnt relations (present pairs only, by
+//              increasing column j) take cnt * dp words, dp = round_up(d, 4),
+//              stored chunk-major: 16-byte chunk c (relation rows 4c..4c+3,
+//              rows >= d zero) of the row's t-th relation is chunk c*cnt + t.
+// so one bulk copy brings everything a slab's evaluation needs.
 // ---------------------------------------------------------------------------
 struct SlabDesc {
-  uint32_t rel_off16;  // offset of the slab's first relation, 16-byte units
-  uint32_t nbytes;     // bytes of relations in the slab (multiple of 16)
-  uint32_t I, J;       // row block (x = 32 I + i) and column block (y = 32 J + j)
-  uint32_t row0;       // first row i of the slab inside block I
-  uint32_t nrows;      // rows of the slab
-  uint32_t meta_off;   // index of the slab's first row in pmask / roff
-  uint32_t pad;
+  uint32_t rel_off16;  // offset of the slab record, 16-byte units
+  uint32_t nbytes;     // bytes of the record (header + relations), multiple of 16
+  uint32_t ij;         // I | J << 16: row block (x = 32 I + i), column block (y = 32 J + j)
+  uint32_t rows;       // row0 | nrows << 8
 };
-static_assert(sizeof(SlabDesc) == 32, "SlabDesc is 32 bytes");
+static_assert(sizeof(SlabDesc) == 16, "SlabDesc is 16 bytes");
 
-constexpr int kConsumerWarps = 8;
-constexpr int kThreads = (kConsumerWarps + 1) * 32;  // 8 consumer warps + 1 producer warp
-constexpr int kStageBytes = 32768;                   // largest slab
-constexpr int kStages = 5;                           // bulk-copy ring depth
+constexpr int kGroupWarps = 4;                        // warps that evaluate one slab together
+constexpr int kGroups = 3;                            // slabs evaluated at the same time
+// 13 warps: at most 4 per SM sub-partition, so 128 registers per thread fit
+constexpr int kConsumerWarps = kGroupWarps * kGroups;
+constexpr int kThreads = (kConsumerWarps + 1) * 32;  // + 1 producer warp
+
+constexpr int kSlabRelBytes = 32768;                 // relation bytes of the largest slab
+constexpr int kStageBytes = kSlabRelBytes + 256;     // + header (at most 32 rows x 2 words)
+// Bulk-copy ring depth: a multiple of kGroups, so that every stage is always
+// consumed by the same group (position p goes to stage p % kStages and group
+// p % kGroups).  A stage shared by two groups could let one group test the
+// next round's phase parity while the current round is still filling, and a
+// parity test cannot tell those two phases apart.
+constexpr int kStages = 6;
 constexpr int kMaxStatesPerLaunch = 1024;
+constexpr int kDescCache = 256;   // slab descriptors a CTA keeps in shared memory
+constexpr int kDomWords = 5120;   // domain words a CTA keeps in shared memory per sweep
 
 struct NetDev {
   int32_t n, d, dp, q, nb, rows_per_slab, n_slabs;
   const uint4 *rel;
   const SlabDesc *slabs;
-  const uint32_t *pmask;  // per slab row: columns j present in the row
-  const uint32_t *roff;   // per slab row: index of the row's first relation in the slab
 };
 
+// Launch-to-launch state of a workspace.  Between launches the scratch
+// domain buffer is all ones and every flag slot the next launch writes
+// before clearing it is zero.  Barrier k of a launch uses slot (base + k) % 3
+// of the barrier words and of the per-sweep flag arrays; during sweep k the
+// slot of sweep k+1 is cleared, and after its last sweep K a launch sets
+// base += K, so the next launch starts on the slot its predecessor cleared
+// last -- no CTA has to reset anything on its way out.
 struct Sync {
-  uint32_t bar0;        // phase-0 arrivals (split barrier before the first removals)
-  uint32_t bar_main;    // one arrival per CTA per sweep, monotone within a launch
-  uint32_t exit_count;  // the last CTA out resets all four words
-  uint32_t err;         // kErr* bits
+  unsigned long long bar[3];  // sweep barrier words, four 16-bit counts: arrivals |
+                              // CTAs that removed values << 16 | CTAs that emptied
+                              // a domain << 32 | CTAs that failed a wait << 48
+  uint32_t base;
+  uint32_t err;  // kErr* bits; sticky: a failed launch poisons the workspace
 };
+constexpr int kBarCountBits = 16;  // grids of at most 65535 CTAs
 
 constexpr uint32_t kErrGridWait = 1u;
 constexpr uint32_t kErrCopyWait = 2u;
-constexpr uint32_t kErrSweepBound = 4u;
+
+constexpr int kMaxFirst = 160;  // per-CTA first slab descriptors passed with the launch
 
 struct LaunchParams {
   NetDev net;
@@ -69,17 +91,20 @@ struct LaunchParams {
   uint32_t *dom_out;
   const int64_t *state_off;  // (contiguous == 0) word offset of state s
   const int32_t *res_idx;    // (contiguous == 0) result slot of state s
-  uint32_t *bufB;            // n_states x n scratch words
+  uint32_t *bufB;            // n_states x n scratch words (all ones between launches)
   int32_t *iterations;
   int32_t *status;
-  uint32_t *any;             // [3][n_states] some value removed in the sweep
-  uint32_t *wipe;            // [3][n_states] some domain emptied in the sweep
-  uint32_t *chg;             // [3][n_states][nb] variables that lost a value
+  uint32_t *any;             // [3][flag_stride] some value removed in the sweep
+  uint32_t *wipe;            // [3][flag_stride] some domain emptied in the sweep
+  uint32_t *chg;             // [3][flag_stride][nb] variables that lost a value
   uint32_t *chgU;            // [3][nb] union of chg over the states
   Sync *sync;
+  int32_t flag_stride;       // state capacity of the workspace (>= n_states)
   int32_t max_sweeps;        // <= 0: none
   int32_t sweep_bound;       // hard bound (|D| + 2), a safety net only
   uint32_t flags;
+  int32_t n_first;           // CTAs whose first slab descriptor is in `first`
+  SlabDesc first[kMaxFirst];
 };
 
 // Per-(network, stream) scratch.
@@ -109,8 +134,7 @@ struct rac_network {
   int device = 0;
   void *d_rel = nullptr;
   rac::SlabDesc *d_slabs = nullptr;
-  uint32_t *d_pmask = nullptr;
-  uint32_t *d_roff = nullptr;
+  std::vector<rac::SlabDesc> first;  // host copy of the first kMaxFirst descriptors
   std::mutex mu;
   std::unordered_map<cudaStream_t, rac::Workspace *> ws;
 };

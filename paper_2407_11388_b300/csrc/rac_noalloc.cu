@@ -11,11 +11,12 @@
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
 // library holds it (kScratchWords words, about 312 KiB) until the process
-// exits.  All calls share it and it keeps the previous call's contents; the
-// kernel re-initialises everything it reads (the scratch domain buffer and
-// the per-sweep flag slots), and the sync words are cleared before each
-// launch.  Two calls whose kernels overlap on the GPU (different streams, or
-// different host threads) race on the array and give undefined results.
+// exits.  All calls share it and it keeps the previous call's contents, so
+// each call first resets, on its stream, what the kernel expects: the sync
+// words and flag slots to zero and the scratch domain buffer to all ones
+// (cudaMemsetAsync, which allocates nothing).  Two calls whose kernels
+// overlap on the GPU (different streams, or different host threads) race on
+// the array and give undefined results.
 //
 // Host code must not use the array's name as a device address: in host code
 // it is a stand-in.  The first call on each device, with that device current,
@@ -115,12 +116,17 @@ extern "C" rac_status rac_enforce_noalloc(const rac_network *net, const uint32_t
   P.chg = P.wipe + 3;
   P.chgU = P.chg + 3 * size_t(net->nb);
   P.bufB = scratch + kBufOffset;
+  P.flag_stride = 1;
   P.max_sweeps = max_sweeps;
   const int64_t bound = int64_t(net->n) * net->d + 2;
   P.sweep_bound = int32_t(bound < 0xFFFFF0 ? bound : 0xFFFFF0);
   P.flags = flags;
-  // the sync words must start at zero; a previous call may have left them set
-  e = cudaMemsetAsync(scratch, 0, sizeof(Sync), s);
-  if (e != cudaSuccess) return cuda_fail(e, "rac_enforce_noalloc: clearing the sync words");
+  P.n_first = int32_t(net->first.size() < size_t(kMaxFirst) ? net->first.size() : kMaxFirst);
+  for (int32_t i = 0; i < P.n_first; ++i) P.first[i] = net->first[size_t(i)];
+  // what the kernel expects to find: sync words and flags zero, the scratch
+  // domain buffer all ones (a previous call may have left anything there)
+  e = cudaMemsetAsync(scratch, 0, size_t(kBufOffset) * sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.bufB, 0xFF, size_t(net->n) * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return cuda_fail(e, "rac_enforce_noalloc: resetting the scratch array");
   return launch_bits(P, s);
 }

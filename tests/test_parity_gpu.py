@@ -243,3 +243,29 @@ def test_no_constraints_and_single_variable():
         for flags in FLAG_SETS:
             assert_same(gpu_enforce(n, d, scope, rel, dom, flags),
                         oracle_enforce(n, d, scope, rel, dom, flags), "empty net")
+
+
+def test_many_launches_on_one_workspace():
+    """Back-to-back launches on the same (network, stream) workspace with
+    different state counts and flags: the scratch state each launch leaves
+    behind (rotating barrier slots, all-ones scratch domains) must be what
+    the next one expects, and no launch may give up a wait."""
+    T = torch()
+    n, d = 700, 24
+    net_np = racgen.random_network(31, 0, n, d, 0.9, 0.33)
+    states = np.array([racgen.assignment_state(31, 0, s, n, d) for s in range(9)] +
+                      [racgen.full_domain(n, d)])
+    refs = oracle_enforce(n, d, net_np.scope, net_np.rel, states)
+    flush = T.empty(256 << 20, dtype=T.uint8, device="cuda:0")
+    with rac.Network(n, d, net_np.scope, net_np.rel) as net:
+        plan = [(1, 0), (7, rac.INCREMENTAL), (1, rac.STOP_ON_WIPEOUT), (3, 0), (10, 0),
+                (1, rac.INCREMENTAL), (2, rac.STOP_ON_WIPEOUT | rac.INCREMENTAL)] * 4
+        for rep, (B, flags) in enumerate(plan):
+            pick = [(rep + j) % states.shape[0] for j in range(B)]
+            flush.zero_()
+            got = gpu_enforce(n, d, net_np.scope, net_np.rel, states[pick], flags, net=net,
+                              shuffle_seed=rep if B > 1 else None)
+            want = oracle_enforce(n, d, net_np.scope, net_np.rel, states[pick], flags)
+            assert not np.any(got[2] == rac.EBARRIER), "launch %d gave up a wait" % rep
+            assert_same(got, want, "launch %d (B=%d flags=%d)" % (rep, B, flags))
+    assert refs[1].max() >= 3
