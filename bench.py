@@ -47,7 +47,7 @@ DEFAULT_WORKLOAD = "dense_n500_d20"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--steps", type=int, default=10000)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -107,7 +107,13 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """NVML samples of SM clock and throttle reasons while the timed region runs."""
+    """SM clock and throttle reasons sampled while the timed region runs:
+    NVML when the pynvml module is importable, else `nvidia-smi -lms`."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, index):
         self.index = index
@@ -116,7 +122,9 @@ class ClockSampler:
         self.max_mhz = None
         self._stop = threading.Event()
         self._t = None
+        self._proc = None
         self.error = None
+        self.source = None
 
     def __enter__(self):
         try:
@@ -125,26 +133,58 @@ class ClockSampler:
             self._h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
             self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
             self._nv = pynvml
-            self._t = threading.Thread(target=self._run, daemon=True)
+            self.source = "nvml"
+            self._t = threading.Thread(target=self._run_nvml, daemon=True)
             self._t.start()
-        except Exception as e:  # noqa: BLE001 - clocks are reported, not required
-            self.error = str(e)
+            return self
+        except Exception as e:  # noqa: BLE001 - fall back to nvidia-smi
+            self.error = "nvml: %s" % e
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi"
+            first = self._proc.stdout.readline()  # the sampler is running before timing starts
+            self._parse(first)
+            self._t = threading.Thread(target=self._run_smi, daemon=True)
+            self._t.start()
+        except Exception as e:  # noqa: BLE001
+            self.error = (self.error or "") + "; nvidia-smi: %s" % e
         return self
 
-    def _run(self):
+    def _parse(self, line):
+        parts = [p.strip() for p in line.strip().split(",")]
+        if len(parts) < 6:
+            return
+        try:
+            self.samples.append(float(parts[0]))
+            self.max_mhz = float(parts[1])
+        except ValueError:
+            return
+        for name, val in zip(self.NAMES, parts[2:6]):
+            if val.lower() == "active":
+                self.reasons.add(name)
+
+    def _run_smi(self):
+        for line in self._proc.stdout:
+            self._parse(line)
+            if self._stop.is_set():
+                break
+
+    def _run_nvml(self):
         nv = self._nv
         names = {
             "hw_slowdown": getattr(nv, "nvmlClocksEventReasonHwSlowdown", 0x8),
             "hw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonHwThermalSlowdown", 0x40),
             "sw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonSwThermalSlowdown", 0x20),
             "sw_power_cap": getattr(nv, "nvmlClocksEventReasonSwPowerCap", 0x4),
-            "hw_power_brake_slowdown": getattr(nv, "nvmlClocksEventReasonHwPowerBrakeSlowdown", 0x80),
         }
+        fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
         while not self._stop.is_set():
             try:
                 self.samples.append(nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM))
-                fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-                    nv.nvmlDeviceGetCurrentClocksThrottleReasons
                 r = fn(self._h)
                 for k, bit in names.items():
                     if r & bit:
@@ -156,13 +196,20 @@ class ClockSampler:
 
     def __exit__(self, *exc):
         self._stop.set()
+        if self._proc is not None:
+            time.sleep(0.06)  # one more sample after the timed region
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=2)
+            except Exception:  # noqa: BLE001
+                self._proc.kill()
         if self._t:
             self._t.join(timeout=2)
 
     def summary(self):
         med = float(np.median(self.samples)) if self.samples else None
         out = {"sm_mhz": med, "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons),
-               "samples": len(self.samples)}
+               "samples": len(self.samples), "source": self.source}
         if self.error and not self.samples:
             out["error"] = self.error
         return out
