@@ -284,6 +284,7 @@ def run_reference(args):
 def run_ours(args):
     import torch
     import paper_2407_11388_b300 as rac
+    from paper_2407_11388_b300.dist import max_over_ranks
 
     world, rank, local = dist_setup(args)
     if not torch.cuda.is_available():
@@ -340,11 +341,7 @@ def run_ours(args):
         wall = time.perf_counter() - w0
     if pg:
         pg.barrier()
-    dev_ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
-    if pg:
-        t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        dev_ms = float(t.item())
+    dev_ms = max_over_ranks(float(sum(s.elapsed_time(e) for s, e in zip(starts, ends))))
     per_step_s = dev_ms / 1000.0 / K
     fix_per_s = world * B / per_step_s
     bits_per_fix = float(net_np.m) * d * d * total_sweeps / B  # m d^2 bits per plain sweep
@@ -374,11 +371,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(Ke):
             host_step()
-        el = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([el], device=dev, dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0)
         if not np.array_equal(host_out.numpy().view(np.uint32), dout.cpu().numpy().view(np.uint32)):
             raise SystemExit("host entry point disagrees with the device entry point")
         e2e = {"value": world * B * Ke / el, "unit": "fixpoints/s",

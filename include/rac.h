@@ -82,6 +82,14 @@ typedef int32_t rac_status;
                                     domain changed in sweep k-1.  The result,
                                     every sweep's removals and the sweep count
                                     are identical to the plain recurrence. */
+#define RAC_TEST_WITHHOLD_ARRIVAL 0x80000000u
+                                 /* test hook for failure detection: one CTA
+                                    withholds its first grid-barrier arrival,
+                                    so every other CTA's bounded wait runs out
+                                    (after 50 ms instead of 2 s); the call then
+                                    reports RAC_EBARRIER for every state and
+                                    poisons its workspace.  Nothing faults or
+                                    hangs; not for production use. */
 
 /*
  * rac_create_network -- copy a network into device memory in the library's

@@ -23,6 +23,7 @@ EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBARRIER, ENOTSUP = -1, -2, -3, -4, -5, -6
 LAYOUT_BITS = 0x1
 STOP_ON_WIPEOUT = 0x1
 INCREMENTAL = 0x2
+TEST_WITHHOLD_ARRIVAL = 0x80000000  # failure-detection test hook (see include/rac.h)
 
 STATUS_NAMES = {OK: "ok", WIPEOUT: "wipeout", EINVAL: "einval", ENOMEM: "enomem",
                 ECUDA: "ecuda", ETIMEOUT: "etimeout", EBARRIER: "ebarrier", ENOTSUP: "enotsup"}

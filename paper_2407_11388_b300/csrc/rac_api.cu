@@ -138,12 +138,13 @@ LaunchParams base_params(const rac_network *net, Workspace *w, int n_states, int
   const int64_t bound = int64_t(net->n) * net->d + 2;
   P.sweep_bound = int32_t(std::min<int64_t>(bound, 0xFFFFF0));
   P.flags = flags;
+  P.wait_limit_ns = wait_limit_for(flags);
   P.n_first = int32_t(std::min<size_t>(net->first.size(), kMaxFirst));
   for (int32_t i = 0; i < P.n_first; ++i) P.first[i] = net->first[size_t(i)];
   return P;
 }
 
-constexpr uint32_t kKnownFlags = RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL;
+constexpr uint32_t kKnownFlags = RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL | RAC_TEST_WITHHOLD_ARRIVAL;
 
 // Largest power of two rows (<= 32) whose slab fits one ring stage.
 int rows_per_slab_for(int dp) {

@@ -35,7 +35,6 @@
 namespace rac {
 namespace {
 
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s for any device-side wait
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
 // ------------------------------- PTX helpers -------------------------------
@@ -75,13 +74,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait; returns false (and sets the error bit) after kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Sync *sy) {
+// Bounded wait; returns false (and sets the error bit) after `limit_ns`.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Sync *sy,
+                                          uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_timer() - t0 > kWaitLimitNs) {
+    if (global_timer() - t0 > limit_ns) {
       atomicOr(&sy->err, kErrCopyWait);
       return false;
     }
@@ -244,14 +244,16 @@ __device__ void grid_barrier(Smem &S, const LaunchParams &P, int slot) {
                                     (uint64_t(S.cta_wipe ? 1u : 0u) << (2 * kBarCountBits)) |
                                     (uint64_t(S.failed ? 1u : 0u) << (3 * kBarCountBits));
     __threadfence();
-    unsigned long long v = atomicAdd(w, mine) + mine;
+    // test hook: CTA 0 withholds its first arrival, so every wait runs out
+    const bool withhold = (P.flags & RAC_TEST_WITHHOLD_ARRIVAL) && blockIdx.x == 0;
+    unsigned long long v = withhold ? 0ull : atomicAdd(w, mine) + mine;
     const uint64_t t0 = global_timer();
     while ((v & kMask) < gridDim.x) {
       if (ld_acquire(&P.sync->err) != 0u) {
         S.failed = 1;
         break;
       }
-      if (global_timer() - t0 > kWaitLimitNs) {
+      if (global_timer() - t0 > P.wait_limit_ns) {
         atomicOr(&P.sync->err, kErrGridWait);
         S.failed = 1;
         break;
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
             }
             const int stg = prod_it % kStages;
             const uint32_t par = (prod_it / kStages) & 1u;
-            if (!mbar_wait(&S.empty[stg], par ^ 1u, P.sync)) {
+            if (!mbar_wait(&S.empty[stg], par ^ 1u, P.sync, P.wait_limit_ns)) {
               ok = false;
               break;
             }
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
           for (int e = 0; e < kGroups && ok; ++e) {
             const int stg = prod_it % kStages;
             const uint32_t par = (prod_it / kStages) & 1u;
-            if (!mbar_wait(&S.empty[stg], par ^ 1u, P.sync)) {
+            if (!mbar_wait(&S.empty[stg], par ^ 1u, P.sync, P.wait_limit_ns)) {
               ok = false;
               break;
             }
@@ -507,7 +509,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
           // One thread takes the bounded wait and every warp of the group
           // follows its outcome, so a wait that gives up never leaves a peer
           // warp blocked on a named barrier inside the slab evaluation.
-          if (group_leader) S.stage_ok[stg] = mbar_wait(&S.full[stg], par, P.sync) ? 1u : 0u;
+          if (group_leader) S.stage_ok[stg] = mbar_wait(&S.full[stg], par, P.sync, P.wait_limit_ns) ? 1u : 0u;
           named_bar(group_bar(cg), kGroupWarps * 32);
           if (!S.stage_ok[stg]) {
             if (group_leader) S.abort = 1;
@@ -611,7 +613,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
   if (is_producer && lane == 0) {
     const uint32_t first = prod_it > uint32_t(kStages) ? prod_it - kStages : 0u;
     for (uint32_t j = first; j < prod_it; ++j)
-      mbar_wait(&S.full[j % kStages], (j / kStages) & 1u, P.sync);
+      mbar_wait(&S.full[j % kStages], (j / kStages) & 1u, P.sync, P.wait_limit_ns);
   }
 }
 

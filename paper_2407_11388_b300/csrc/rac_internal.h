@@ -81,7 +81,12 @@ constexpr int kBarCountBits = 16;  // grids of at most 65535 CTAs
 constexpr uint32_t kErrGridWait = 1u;
 constexpr uint32_t kErrCopyWait = 2u;
 
-constexpr int kMaxFirst = 160;  // per-CTA first slab descriptors passed with the launch
+constexpr int kMaxFirst = 160;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;      // 2 s
+constexpr uint64_t kTestWaitLimitNs = 50000000ull;    // 50 ms under RAC_TEST_WITHHOLD_ARRIVAL
+inline uint64_t wait_limit_for(uint32_t flags) {
+  return (flags & RAC_TEST_WITHHOLD_ARRIVAL) ? kTestWaitLimitNs : kWaitLimitNs;
+}  // per-CTA first slab descriptors passed with the launch
 
 struct LaunchParams {
   NetDev net;
@@ -103,6 +108,7 @@ struct LaunchParams {
   int32_t max_sweeps;        // <= 0: none
   int32_t sweep_bound;       // hard bound (|D| + 2), a safety net only
   uint32_t flags;
+  uint64_t wait_limit_ns;    // every device-side wait gives up after this long
   int32_t n_first;           // CTAs whose first slab descriptor is in `first`
   SlabDesc first[kMaxFirst];
 };

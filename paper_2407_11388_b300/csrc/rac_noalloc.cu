@@ -80,7 +80,7 @@ extern "C" rac_status rac_enforce_noalloc(const rac_network *net, const uint32_t
     set_error("rac_enforce_noalloc: NULL argument");
     return RAC_EINVAL;
   }
-  if (flags & ~uint32_t(RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL)) {
+  if (flags & ~uint32_t(RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL | RAC_TEST_WITHHOLD_ARRIVAL)) {
     set_error("rac_enforce_noalloc: unknown flag");
     return RAC_EINVAL;
   }
@@ -121,6 +121,7 @@ extern "C" rac_status rac_enforce_noalloc(const rac_network *net, const uint32_t
   const int64_t bound = int64_t(net->n) * net->d + 2;
   P.sweep_bound = int32_t(bound < 0xFFFFF0 ? bound : 0xFFFFF0);
   P.flags = flags;
+  P.wait_limit_ns = wait_limit_for(flags);
   P.n_first = int32_t(net->first.size() < size_t(kMaxFirst) ? net->first.size() : kMaxFirst);
   for (int32_t i = 0; i < P.n_first; ++i) P.first[i] = net->first[size_t(i)];
   // what the kernel expects to find: sync words and flags zero, the scratch

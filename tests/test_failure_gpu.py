@@ -1,0 +1,46 @@
+"""Failure detection without a GPU fault: a device-side wait that runs out
+(one CTA withholds its grid-barrier arrival, a flag nobody else sets) must
+end the launch with RAC_EBARRIER within its short limit, poison only that
+workspace, and leave the CUDA context usable (GPU)."""
+import time
+
+import numpy as np
+import pytest
+
+import racgen
+import paper_2407_11388_b300 as rac
+from gpu_helpers import from_dev, oracle_enforce, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bounded_wait_runs_out_and_reports():
+    T = torch()
+    n, d = 300, 12
+    net_np = racgen.random_network(8, 0, n, d, 0.5, 0.5)
+    dom = racgen.assignment_state(8, 0, 1, n, d)
+    want = oracle_enforce(n, d, net_np.scope, net_np.rel, dom)
+    with rac.Network(n, d, net_np.scope, net_np.rel) as net:
+        bad_stream = T.cuda.Stream()
+        din = to_dev(dom)
+        dout = T.empty_like(din)
+        it = T.full((1,), -7, dtype=T.int32, device="cuda:0")
+        st = T.full((1,), -7, dtype=T.int32, device="cuda:0")
+        t0 = time.perf_counter()
+        rac.enforce(net, din, dout, it, st, flags=rac.TEST_WITHHOLD_ARRIVAL, stream=bad_stream)
+        bad_stream.synchronize()
+        elapsed = time.perf_counter() - t0
+        assert int(st.item()) == rac.EBARRIER
+        assert elapsed < 1.5, "the wait limit under the test hook is 50 ms"
+        # the workspace of that stream is poisoned: later calls report at once
+        st.fill_(-7)
+        rac.enforce(net, din, dout, it, st, stream=bad_stream)
+        bad_stream.synchronize()
+        assert int(st.item()) == rac.EBARRIER
+        # the context and other workspaces still work
+        good = T.cuda.Stream()
+        st.fill_(-7)
+        rac.enforce(net, din, dout, it, st, stream=good)
+        good.synchronize()
+        assert np.array_equal(from_dev(dout), want[0][0])
+        assert int(it.item()) == want[1][0] and int(st.item()) == want[2][0]
