@@ -164,7 +164,11 @@ RAC_API rac_status rac_enforce(const rac_network *net, const uint32_t *dom_in, u
  *  max_sweeps, flags, stream  as for rac_enforce.
  *
  * Items on the same network are enforced together so that each relation
- * slab is read once per sweep for all of them.
+ * slab is read once per sweep for all of them.  When the items span several
+ * networks, all of them run in ONE persistent launch (the batched kernel)
+ * whose tables and scratch are allocated and freed in stream order around
+ * the launch (cudaMallocAsync); for repeated batches over the same networks
+ * a rac_plan avoids that per-call set-up.
  * Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA.
  */
 RAC_API rac_status rac_enforce_batch(const rac_network *const *nets, int32_t n_nets, int32_t n_items,
@@ -172,6 +176,30 @@ RAC_API rac_status rac_enforce_batch(const rac_network *const *nets, int32_t n_n
                              const uint32_t *dom_in, uint32_t *dom_out, int32_t *iterations,
                              int32_t *status, int32_t max_sweeps, uint32_t flags,
                              rac_stream_t stream);
+
+/*
+ * rac_plan -- a fixed batch of (network, domain state) items enforced in one
+ * persistent launch, with its tables and scratch allocated once.
+ *
+ * rac_plan_create: nets / n_nets / n_items / item_net / item_dom_off as for
+ *   rac_enforce_batch (HOST arrays, copied).  Allocates device memory and
+ *   synchronises with the device.  The networks must outlive the plan.
+ * rac_plan_enforce: enforce every item (Eq. 1 to its fixpoint) in ONE
+ *   cooperative launch on `stream`; dom_in / dom_out / iterations / status /
+ *   max_sweeps / flags as for rac_enforce_batch.  Allocates nothing, so it can
+ *   be captured in a CUDA graph.  Launches of one plan must not overlap on
+ *   the GPU (use one plan per stream).
+ * rac_plan_destroy: free the plan (NULL-safe; no launch of it may still run).
+ * Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA.
+ */
+typedef struct rac_plan rac_plan;
+RAC_API rac_status rac_plan_create(const rac_network *const *nets, int32_t n_nets,
+                                   int32_t n_items, const int32_t *item_net,
+                                   const int64_t *item_dom_off, rac_plan **out);
+RAC_API rac_status rac_plan_enforce(rac_plan *plan, const uint32_t *dom_in, uint32_t *dom_out,
+                                    int32_t *iterations, int32_t *status, int32_t max_sweeps,
+                                    uint32_t flags, rac_stream_t stream);
+RAC_API void rac_plan_destroy(rac_plan *plan);
 
 /*
  * rac_enforce_host -- rac_enforce on HOST buffers: copies the n_states

@@ -29,7 +29,8 @@ STATUS_NAMES = {OK: "ok", WIPEOUT: "wipeout", EINVAL: "einval", ENOMEM: "enomem"
                 ECUDA: "ecuda", ETIMEOUT: "etimeout", EBARRIER: "ebarrier", ENOTSUP: "enotsup"}
 
 ABI_FUNCTIONS = ("rac_create_network", "rac_destroy", "rac_enforce", "rac_enforce_batch",
-                 "rac_enforce_host", "rac_enforce_noalloc", "rac_network_info", "rac_last_error")
+                 "rac_enforce_host", "rac_enforce_noalloc", "rac_network_info", "rac_last_error",
+                 "rac_plan_create", "rac_plan_enforce", "rac_plan_destroy")
 NOALLOC_MAX_VARS = 65536
 
 
@@ -62,6 +63,12 @@ def lib():
         L.rac_enforce_host.argtypes = [vp, i32, vp, vp, vp, vp, i32, u32, vp]
         L.rac_enforce_noalloc.restype = i32
         L.rac_enforce_noalloc.argtypes = [vp, vp, vp, vp, vp, i32, u32, vp]
+        L.rac_plan_create.restype = i32
+        L.rac_plan_create.argtypes = [vp, i32, i32, vp, vp, ctypes.POINTER(vp)]
+        L.rac_plan_enforce.restype = i32
+        L.rac_plan_enforce.argtypes = [vp, vp, vp, vp, vp, i32, u32, vp]
+        L.rac_plan_destroy.restype = None
+        L.rac_plan_destroy.argtypes = [vp]
         L.rac_network_info.restype = i32
         L.rac_network_info.argtypes = [vp, ctypes.POINTER(i64), i32]
         L.rac_last_error.restype = ctypes.c_char_p
@@ -180,6 +187,45 @@ def enforce_batch(nets, item_net, item_dom_off, dom_in, dom_out, iterations, sta
                                    _ptr(iterations), _ptr(status), int(max_sweeps), int(flags),
                                    _stream(stream)),
            "rac_enforce_batch")
+
+
+class Plan:
+    """A fixed batch of (network, state) items enforced in one persistent
+    launch (rac_plan_*).  The networks must outlive the plan."""
+
+    def __init__(self, nets, item_net, item_dom_off):
+        handles = (ctypes.c_void_p * max(1, len(nets)))(*[n.handle for n in nets])
+        item_net = np.ascontiguousarray(item_net, dtype=np.int32)
+        item_dom_off = np.ascontiguousarray(item_dom_off, dtype=np.int64)
+        h = ctypes.c_void_p()
+        _check(lib().rac_plan_create(handles, len(nets), item_net.shape[0], item_net.ctypes.data,
+                                     item_dom_off.ctypes.data, ctypes.byref(h)),
+               "rac_plan_create")
+        self.handle = h.value
+        self.nets = list(nets)  # keep the networks alive
+        self.n_items = int(item_net.shape[0])
+
+    def enforce(self, dom_in, dom_out, iterations, status, max_sweeps=0, flags=0, stream=None):
+        _check(lib().rac_plan_enforce(self.handle, _ptr(dom_in), _ptr(dom_out), _ptr(iterations),
+                                      _ptr(status), int(max_sweeps), int(flags), _stream(stream)),
+               "rac_plan_enforce")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rac_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def enforce_host(net, dom_in, max_sweeps=0, flags=0, stream=None):

@@ -413,6 +413,11 @@ rac_status rac_enforce_batch(const rac_network *const *nets, int32_t n_nets, int
   for (int32_t k = 0; k < n_nets; ++k)
     if (!groups[size_t(k)].empty() && !check_device(nets[k])) return RAC_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int32_t used_nets = 0;
+  for (int32_t k = 0; k < n_nets; ++k) used_nets += groups[size_t(k)].empty() ? 0 : 1;
+  if (used_nets > 1)  // one persistent launch over all networks
+    return enforce_batch_multi(nets, n_nets, n_items, item_net, item_dom_off, dom_in, dom_out,
+                               iterations, status, max_sweeps, flags, s);
   std::vector<int64_t> off;
   std::vector<int32_t> idx;
   for (int32_t k = 0; k < n_nets; ++k) {

@@ -1,0 +1,539 @@
+// Batched enforcement: many networks (of any n and d), each with its own
+// domain states, swept to their fixpoints in ONE persistent cooperative
+// launch.  The support test is the one of the single-network kernel (Eq. 1,
+// Fig. 1: per relation, fwd bit a = (R[a] & D_y) != 0, rev = OR of the rows
+// in D_x, both directions from one read), applied to every running state of
+// the relation's network while the slab sits in shared memory, so a slab is
+// read once per sweep for all of its network's states.
+//
+// Work: global slab g of job (network) j; CTA c streams slabs c, c+G, ...
+// through a 6-stage bulk-copy ring (one producer thread).  Three groups of
+// four consumer warps take alternate stages; a group stages the domain words
+// its slab needs (32 column variables + the slab's rows) for 32 states at a
+// time in shared memory and gives each warp one state at a time.  The
+// relation width is dispatched at run time.
+//
+// Per sweep: one barrier after the removals (its word counts the CTAs that
+// removed values), then the owners of the states (state t belongs to CTA
+// t mod G) take the per-state decisions of Algorithm 1 and a second barrier
+// publishes them and the number of states still running.  A sweep in which no
+// CTA removed anything ends every running state at once.
+#include "rac_device.cuh"
+#include "rac_internal.h"
+
+namespace rac {
+namespace {
+
+using namespace dev;
+
+constexpr int kBGroupWarps = 4;
+constexpr int kBGroups = 3;
+constexpr int kBConsumerWarps = kBGroupWarps * kBGroups;
+constexpr int kBThreads = (kBConsumerWarps + 1) * 32;
+constexpr int kBStages = 6;
+static_assert(kBStages % kBGroups == 0, "each ring stage belongs to one consumer group");
+
+struct BStage {
+  int32_t job;   // -1: end of the sweep's slabs
+  int32_t slab;  // slab index inside the job
+  uint32_t ij, rows;
+};
+
+struct BSmem {
+  uint64_t full[kBStages];
+  uint64_t empty[kBStages];
+  BStage stage[kBStages];
+  uint32_t stage_ok[kBStages];
+  uint32_t base, poisoned, abort, failed;
+  uint32_t any_total, wipe_total, running_total;
+  uint32_t cta_any, cta_wipe, cta_running;
+  uint32_t dom[kBGroups][kBatchChunk][kBatchStageWords];  // [0,32): columns, [32,64): rows
+  uint32_t info[kBGroups][kBatchChunk];
+  uint32_t chgJ[kBGroups][kBatchChunk], chgI[kBGroups][kBatchChunk];
+  int64_t chgoff[kBGroups][kBatchChunk];
+};
+static_assert(size_t(kBStages) * kStageBytes + sizeof(BSmem) <= 232448,
+              "shared memory of the batched kernel exceeds 227 KB");
+
+constexpr uint32_t kInfoSweepMask = 0xFFFFFFu;
+constexpr uint32_t kInfoResB = 1u << 24;
+constexpr uint32_t kInfoWiped = 1u << 25;
+__device__ __forceinline__ uint32_t info_status_bits(int st) { return uint32_t(st + 8) << 27; }
+__device__ __forceinline__ int info_status(uint32_t v) { return int((v >> 27) & 31u) - 8; }
+
+__device__ __forceinline__ int group_bar(int cg) { return 1 + cg; }
+
+struct BView {
+  const uint32_t *C;
+  uint32_t *T;
+};
+
+// Buffers as in the single-network kernel: A = dom_out, B = bufB.
+__device__ __forceinline__ BView bview(const BatchParams &P, int t, int k) {
+  uint32_t *A = P.dom_out + P.state_off[t];
+  uint32_t *B = P.bufB + P.scratch_off[t];
+  BView v;
+  if (k == 1) {
+    v.C = P.dom_in + P.state_off[t];
+    v.T = B;
+  } else if (k & 1) {
+    v.C = A;
+    v.T = B;
+  } else {
+    v.C = B;
+    v.T = A;
+  }
+  return v;
+}
+
+__device__ void batch_barrier(const BatchParams &P, unsigned long long *w,
+                              unsigned long long mine, unsigned long long target_mask,
+                              uint32_t G, unsigned long long &out, uint32_t &failed) {
+  // thread 0 only
+  __threadfence();
+  unsigned long long v = atomicAdd(w, mine) + mine;
+  const uint64_t t0 = global_timer();
+  while ((v & target_mask) < G) {
+    if (ld_acquire(&P.sync->err) != 0u) {
+      failed = 1;
+      break;
+    }
+    if (global_timer() - t0 > P.wait_limit_ns) {
+      atomicOr(&P.sync->err, kErrGridWait);
+      failed = 1;
+      break;
+    }
+    __nanosleep(20);
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(w) : "memory");
+  }
+  __threadfence();
+  out = v;
+}
+
+template <int Q>
+__device__ __forceinline__ void support_dispatch_q(const uint4 *mine, uint32_t stride, uint32_t Dx,
+                                                   uint32_t Dy, uint32_t dfull, uint32_t &fwd,
+                                                   uint32_t &rev) {
+  if (Dx == dfull)
+    support_relation<Q, true>(mine, stride, Dx, Dy, fwd, rev);
+  else
+    support_relation<Q, false>(mine, stride, Dx, Dy, fwd, rev);
+}
+
+__device__ __forceinline__ void support_any_q(int q, const uint4 *mine, uint32_t stride,
+                                              uint32_t Dx, uint32_t Dy, uint32_t dfull,
+                                              uint32_t &fwd, uint32_t &rev) {
+  switch (q) {
+    case 1: support_dispatch_q<1>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
+    case 2: support_dispatch_q<2>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
+    case 3: support_dispatch_q<3>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
+    case 4: support_dispatch_q<4>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
+    case 5: support_dispatch_q<5>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
+    case 6: support_dispatch_q<6>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
+    case 7: support_dispatch_q<7>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
+    default: support_dispatch_q<8>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
+  }
+}
+
+__device__ __forceinline__ void batch_remove(BSmem &S, const BatchParams &P, const BatchJob &J,
+                                             int t, int64_t chgoff, int slot_w, uint32_t *T,
+                                             uint32_t v, uint32_t keep) {
+  const uint32_t old = atomicAnd(T + v, keep);
+  S.cta_any = 1;
+  atomicOr(P.any + int64_t(slot_w) * P.total_states + t, 1u);
+  if (old != 0u && (old & keep) == 0u) {
+    S.cta_wipe = 1;
+    atomicOr(P.wipe + int64_t(slot_w) * P.total_states + t, 1u);
+  }
+  const uint32_t bit = 1u << (v & 31u);
+  atomicOr(P.chg + int64_t(slot_w) * P.chg_slot_words + chgoff + (v >> 5), bit);
+  if (P.flags & RAC_INCREMENTAL)
+    atomicOr(P.chgU + int64_t(slot_w) * P.u_slot_words + J.u_off + (v >> 5), bit);
+}
+
+// One slab of job J for every running state of J, by one consumer group.
+__device__ void batch_consume(BSmem &S, const BatchParams &P, const unsigned char *stage,
+                              const BStage &si, int k, int slot_r, int slot_w, int cg, int lw,
+                              int lane) {
+  const BatchJob J = P.jobs[si.job];
+  const int n = J.n;
+  const uint32_t I = si.ij & 0xFFFFu, Jb = si.ij >> 16;
+  const uint32_t row0 = si.rows & 0xFFu, nrows = si.rows >> 8;
+  const uint32_t *hdr = reinterpret_cast<const uint32_t *>(stage);
+  const uint4 *rel = reinterpret_cast<const uint4 *>(stage) + (2 * nrows) / 4;
+  const int y = int(Jb) * 32 + lane;
+  const bool y_ok = y < n;
+  const uint32_t dfull = J.d >= 32 ? kFull : ((1u << J.d) - 1u);
+  const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
+  const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
+  const int gl = lw * 32 + lane;  // thread index inside the group
+  for (int c0 = 0; c0 < J.n_states; c0 += kBatchChunk) {
+    const int cnt = min(kBatchChunk, J.n_states - c0);
+    // stage the chunk's domain words, decisions and change words
+    for (int i = gl; i < cnt * kBatchStageWords; i += kBGroupWarps * 32) {
+      const int q = i / kBatchStageWords, w = i % kBatchStageWords;
+      const int t = J.state_base + c0 + q;
+      const BView V = bview(P, t, k);
+      uint32_t val = 0u;
+      if (w < 32) {
+        const int yy = int(Jb) * 32 + w;
+        if (yy < n) val = ld_dom(V.C + yy);
+      } else if (uint32_t(w - 32) < nrows) {
+        const int xx = int(I) * 32 + int(row0) + (w - 32);
+        if (xx < n) val = ld_dom(V.C + xx);
+      }
+      S.dom[cg][q][w] = val;
+    }
+    for (int q = gl; q < cnt; q += kBGroupWarps * 32) {
+      const int t = J.state_base + c0 + q;
+      S.info[cg][q] = ld_dom(P.st_info + t);
+      const int64_t co = P.chg_off[t];
+      S.chgoff[cg][q] = co;
+      if (incr) {
+        const uint32_t *ch = P.chg + int64_t(slot_r) * P.chg_slot_words + co;
+        S.chgJ[cg][q] = ld_dom(ch + Jb);
+        S.chgI[cg][q] = ld_dom(ch + I);
+      }
+    }
+    named_bar(group_bar(cg), kBGroupWarps * 32);
+    for (int q = lw; q < cnt; q += kBGroupWarps) {
+      if (S.info[cg][q] & kInfoSweepMask) continue;  // finished state
+      if (incr && S.chgJ[cg][q] == 0u && (S.chgI[cg][q] & rowmask) == 0u) continue;
+      const int t = J.state_base + c0 + q;
+      const uint32_t *Dq = S.dom[cg][q];
+      const uint32_t Dy = Dq[lane];
+      uint32_t *T = bview(P, t, k).T;
+      uint32_t racc = kFull;
+      for (int r = 0; r < int(nrows); ++r) {
+        const uint32_t pm = hdr[r];
+        if (pm == 0u) continue;
+        const uint32_t Dx = Dq[32 + r];
+        uint32_t fwd = kFull, rev = kFull;
+        if ((pm >> lane) & 1u) {
+          const uint32_t tt = __popc(pm & lanemask_lt());
+          support_any_q(J.q, rel + hdr[nrows + r] * uint32_t(J.q) + tt, __popc(pm), Dx, Dy,
+                        dfull, fwd, rev);
+        }
+        const uint32_t keep_x = __reduce_and_sync(kFull, fwd) & Dx;
+        if (keep_x != Dx && lane == 0) {
+          const int x = int(I) * 32 + int(row0) + r;
+          batch_remove(S, P, J, t, S.chgoff[cg][q], slot_w, T, uint32_t(x), keep_x);
+        }
+        racc &= rev;
+      }
+      if (y_ok) {
+        const uint32_t keep_y = racc & Dy;
+        if (keep_y != Dy) batch_remove(S, P, J, t, S.chgoff[cg][q], slot_w, T, uint32_t(y), keep_y);
+      }
+    }
+    named_bar(group_bar(cg), kBGroupWarps * 32);
+  }
+}
+
+__global__ void __launch_bounds__(kBThreads, 1) rac_batch_kernel(const BatchParams P) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *ring = smem_raw;
+  BSmem &S = *reinterpret_cast<BSmem *>(smem_raw + size_t(kBStages) * kStageBytes);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int G = gridDim.x, cta = blockIdx.x;
+  const bool is_producer = warp == kBConsumerWarps;
+  const int T_total = P.total_states;
+
+  if (tid == 0) {
+    for (int i = 0; i < kBStages; ++i) {
+      mbar_init(&S.full[i], 1);
+      mbar_init(&S.empty[i], kBGroupWarps);
+    }
+    fence_mbar_init();
+    S.abort = 0;
+    S.failed = 0;
+    S.base = ld_acquire(&P.sync->base);
+    S.poisoned = ld_acquire(&P.sync->err) != 0u ? 1u : 0u;
+    S.cta_any = 0;
+    S.cta_wipe = 0;
+  }
+  __syncthreads();
+  const uint32_t base = S.base;
+  uint32_t ring_it = 0, prod_it = 0;
+  int k = 0;
+  bool ended_quiet = false;  // the last sweep removed nothing anywhere
+  if (S.poisoned) {
+    S.failed = 1;
+  } else {
+    // Phase 0 (owners): A := dom_in, B &= dom_in, note empty input domains.
+    const int slot1 = int((base + 1) % 3);
+    for (int t = cta; t < T_total; t += G) {
+      const int n = P.jobs[P.state_job[t]].n;
+      const int64_t off = P.state_off[t], so = P.scratch_off[t];
+      for (int x = tid; x < n; x += blockDim.x) {
+        const uint32_t v = P.dom_in[off + x];
+        atomicAnd(P.bufB + so + x, v);
+        if (P.dom_out != P.dom_in) P.dom_out[off + x] = v;
+        if (v == 0u) {
+          atomicOr(P.wipe + int64_t(slot1) * T_total + t, 1u);
+          S.cta_wipe = 1;
+        }
+      }
+    }
+    __syncthreads();
+    for (;;) {
+      ++k;
+      const int slot_w = int((base + k) % 3), slot_r = int((base + k + 2) % 3);
+      const int slot_c = int((base + k + 1) % 3);
+      if (is_producer) {
+        if (lane == 0) {
+          if (cta == 0) {  // barrier words last used two sweeps (or a launch) ago
+            P.sync->bar[slot_c] = 0ull;
+            P.sync->bar2[slot_c] = 0ull;
+          }
+          const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
+          bool ok = true;
+          int j = 0;
+          for (int g = cta; g < P.total_slabs; g += G) {
+            while (j + 1 < P.n_jobs && P.jobs[j + 1].slab_base <= g) ++j;
+            const BatchJob &J = P.jobs[j];
+            if (k >= 2 && ld_dom(P.job_alive + int64_t(slot_r) * P.n_jobs + j) == 0u) continue;
+            const int local = g - J.slab_base;
+            const SlabDesc sd = J.slabs[local];
+            if (incr) {
+              const uint32_t I = sd.ij & 0xFFFFu, Jb = sd.ij >> 16;
+              const uint32_t row0 = sd.rows & 0xFFu, nrows = sd.rows >> 8;
+              const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
+              const uint32_t *cu = P.chgU + int64_t(slot_r) * P.u_slot_words + J.u_off;
+              if (ld_dom(cu + Jb) == 0u && (ld_dom(cu + I) & rowmask) == 0u) continue;
+            }
+            const int stg = prod_it % kBStages;
+            const uint32_t par = (prod_it / kBStages) & 1u;
+            if (!mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err,
+                           P.wait_limit_ns)) {
+              ok = false;
+              break;
+            }
+            S.stage[stg].job = j;
+            S.stage[stg].slab = local;
+            S.stage[stg].ij = sd.ij;
+            S.stage[stg].rows = sd.rows;
+            mbar_arrive_expect_tx(&S.full[stg], sd.nbytes);
+            bulk_copy_g2s(ring + size_t(stg) * kStageBytes, J.rel + size_t(sd.rel_off16),
+                          sd.nbytes, &S.full[stg]);
+            ++prod_it;
+          }
+          for (int e = 0; e < kBGroups && ok; ++e) {
+            const int stg = prod_it % kBStages;
+            const uint32_t par = (prod_it / kBStages) & 1u;
+            if (!mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err,
+                           P.wait_limit_ns)) {
+              ok = false;
+              break;
+            }
+            S.stage[stg].job = -1;
+            mbar_arrive(&S.full[stg]);
+            ++prod_it;
+          }
+          if (!ok) S.abort = 1;
+        }
+      } else {
+        // clear the slots written next sweep (last read two sweeps ago)
+        const int64_t cgtid = int64_t(cta) * (kBConsumerWarps * 32) + tid;
+        const int64_t cgstride = int64_t(G) * (kBConsumerWarps * 32);
+        for (int64_t i = cgtid; i < T_total; i += cgstride) {
+          P.any[int64_t(slot_c) * T_total + i] = 0u;
+          P.wipe[int64_t(slot_c) * T_total + i] = 0u;
+        }
+        for (int64_t i = cgtid; i < P.chg_slot_words; i += cgstride)
+          P.chg[int64_t(slot_c) * P.chg_slot_words + i] = 0u;
+        for (int64_t i = cgtid; i < P.u_slot_words; i += cgstride)
+          P.chgU[int64_t(slot_c) * P.u_slot_words + i] = 0u;
+        for (int64_t i = cgtid; i < P.n_jobs; i += cgstride)
+          P.job_alive[int64_t(slot_c) * P.n_jobs + i] = 0u;
+        if (k >= 2) {
+          // owner step: T still holds D_{k-2}; AND D_{k-1} into it where it differs
+          for (int t = cta; t < T_total; t += G) {
+            if (ld_dom(P.st_info + t) & kInfoSweepMask) continue;  // finished state
+            const int nb = P.jobs[P.state_job[t]].nb;
+            const uint32_t *ch = P.chg + int64_t(slot_r) * P.chg_slot_words + P.chg_off[t];
+            for (int blk = tid; blk < nb; blk += kBConsumerWarps * 32) {
+              uint32_t w = ld_dom(ch + blk);
+              if (w == 0u) continue;
+              const BView V = bview(P, t, k);
+              while (w) {
+                const int b = __ffs(w) - 1;
+                w &= w - 1u;
+                const int x = blk * 32 + b;
+                atomicAnd(V.T + x, ld_dom(V.C + x));
+              }
+            }
+          }
+        }
+        const int cg = warp / kBGroupWarps, lw = warp % kBGroupWarps;
+        const bool leader = lw == 0 && lane == 0;
+        for (;;) {
+          const uint32_t pos = ring_it * kBGroups + cg;
+          const int stg = pos % kBStages;
+          const uint32_t par = (pos / kBStages) & 1u;
+          if (leader)
+            S.stage_ok[stg] = mbar_wait(&S.full[stg], par, &P.sync->err,
+                                        P.wait_limit_ns) ? 1u : 0u;
+          named_bar(group_bar(cg), kBGroupWarps * 32);
+          if (!S.stage_ok[stg]) {
+            if (leader) S.abort = 1;
+            break;
+          }
+          if (lane == 0) mbar_try_wait(&S.full[stg], par);
+          __syncwarp();
+          const BStage si = S.stage[stg];
+          if (si.job >= 0)
+            batch_consume(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_r, slot_w, cg, lw,
+                          lane);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&S.empty[stg]);
+          ++ring_it;
+          if (si.job < 0) break;
+        }
+      }
+      __syncthreads();
+      if (S.abort) S.failed = 1;
+      // barrier 1: removals of sweep k done everywhere
+      if (tid == 0) {
+        constexpr unsigned long long kMask = (1ull << kBarCountBits) - 1ull;
+        const unsigned long long mine = 1ull |
+                                        (uint64_t(S.cta_any ? 1u : 0u) << kBarCountBits) |
+                                        (uint64_t(S.cta_wipe ? 1u : 0u) << (2 * kBarCountBits)) |
+                                        (uint64_t(S.failed ? 1u : 0u) << (3 * kBarCountBits));
+        unsigned long long v = 0;
+        uint32_t f = S.failed;
+        batch_barrier(P, &P.sync->bar[slot_w], mine, kMask, uint32_t(G), v, f);
+        S.any_total = uint32_t((v >> kBarCountBits) & kMask);
+        S.wipe_total = uint32_t((v >> (2 * kBarCountBits)) & kMask);
+        if (((v >> (3 * kBarCountBits)) & kMask) || f) S.failed = 1;
+        S.cta_any = 0;
+        S.cta_wipe = 0;
+        S.cta_running = 0;
+      }
+      __syncthreads();
+      if (S.failed) break;
+      if (S.any_total == 0u && S.wipe_total == 0u) {
+        ended_quiet = true;  // D_k = D_{k-1} for every running state
+        break;
+      }
+      // decisions of the states this CTA owns
+      const bool stop = (P.flags & RAC_STOP_ON_WIPEOUT) != 0;
+      for (int t = cta + G * tid; t < T_total; t += G * int(blockDim.x)) {
+        uint32_t info = ld_dom(P.st_info + t);
+        if (info & kInfoSweepMask) continue;
+        const bool any = ld_dom(P.any + int64_t(slot_w) * T_total + t) != 0u;
+        const bool wp = ld_dom(P.wipe + int64_t(slot_w) * T_total + t) != 0u;
+        if (wp) info |= kInfoWiped;
+        const uint32_t t_is_b = (k & 1) ? kInfoResB : 0u;
+        const uint32_t c_is_b = (k >= 2 && !(k & 1)) ? kInfoResB : 0u;
+        if (stop && wp) {
+          info |= uint32_t(k) | t_is_b | info_status_bits(RAC_WIPEOUT);
+        } else if (!any) {
+          info |= uint32_t(k) | c_is_b | info_status_bits((info & kInfoWiped) ? RAC_WIPEOUT : RAC_OK);
+        } else if ((P.max_sweeps > 0 && k >= P.max_sweeps) || k >= 0xFFFFF0) {
+          info |= uint32_t(k) | t_is_b | info_status_bits(RAC_ETIMEOUT);
+        } else {
+          atomicAdd(&S.cta_running, 1u);
+          atomicOr(P.job_alive + int64_t(slot_w) * P.n_jobs + P.state_job[t], 1u);
+        }
+        P.st_info[t] = info;
+      }
+      __syncthreads();
+      // barrier 2: decisions published; how many states still run
+      if (tid == 0) {
+        constexpr unsigned long long kMask = (1ull << kBarCountBits) - 1ull;
+        const unsigned long long mine = 1ull | (uint64_t(S.cta_running) << 32);
+        unsigned long long v = 0;
+        uint32_t f = S.failed;
+        batch_barrier(P, &P.sync->bar2[slot_w], mine, kMask, uint32_t(G), v, f);
+        S.running_total = uint32_t(v >> 32);
+        if (f) S.failed = 1;
+      }
+      __syncthreads();
+      if (S.failed || S.running_total == 0u) break;
+    }
+  }
+
+  // Epilogue (owners): final status and sweep count of every state, results
+  // that ended in B copied to dom_out, B back to all ones, decisions reset.
+  __syncthreads();
+  const bool failed = S.failed != 0u;
+  if (!S.poisoned) {
+    for (int t = cta; t < T_total; t += G) {
+      const uint32_t info = ld_dom(P.st_info + t);
+      const bool done = (info & kInfoSweepMask) != 0u;
+      bool res_b;
+      int sweeps, st;
+      if (done) {
+        res_b = (info & kInfoResB) != 0u;
+        sweeps = int(info & kInfoSweepMask);
+        st = info_status(info);
+      } else {  // still running when the loop ended: a quiet last sweep
+        res_b = ended_quiet && k >= 2 && !(k & 1);
+        sweeps = k;
+        st = ended_quiet ? ((info & kInfoWiped) ? RAC_WIPEOUT : RAC_OK) : RAC_EBARRIER;
+      }
+      const int n = P.jobs[P.state_job[t]].n;
+      const int64_t off = P.state_off[t], so = P.scratch_off[t];
+      for (int x = tid; x < n; x += blockDim.x) {
+        if (!failed && res_b) P.dom_out[off + x] = ld_dom(P.bufB + so + x);
+        P.bufB[so + x] = kFull;
+      }
+      if (tid == 0) {
+        P.iterations[P.res_idx[t]] = sweeps;
+        P.status[P.res_idx[t]] = failed ? RAC_EBARRIER : st;
+        P.st_info[t] = 0u;
+      }
+    }
+  }
+  if (cta == 0 && tid == 0 && !failed) P.sync->base = (base + uint32_t(k)) % 3u;
+  if (failed && tid == 0) atomicOr(&P.sync->err, kErrCopyWait);
+  if (is_producer && lane == 0) {
+    const uint32_t first = prod_it > uint32_t(kBStages) ? prod_it - kBStages : 0u;
+    for (uint32_t j = first; j < prod_it; ++j)
+      mbar_wait(&S.full[j % kBStages], (j / kBStages) & 1u,
+                &P.sync->err, P.wait_limit_ns);
+  }
+}
+
+}  // namespace
+
+rac_status launch_batch(const BatchParams &P, cudaStream_t stream) {
+  static int grid = 0;
+  static int dev_cached = -1;
+  const size_t smem = size_t(kBStages) * kStageBytes + sizeof(BSmem);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (grid == 0 || dev_cached != dev) {
+    e = cudaFuncSetAttribute(rac_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(smem));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute (batch)");
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rac_batch_kernel, kBThreads, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy (batch)");
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    if (per_sm < 1) {
+      set_error("batched kernel does not fit on an SM");
+      return RAC_ECUDA;
+    }
+    grid = per_sm * sms;
+    dev_cached = dev;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(kBThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, rac_batch_kernel, P);
+  if (e != cudaSuccess) return cuda_fail(e, "launch of the batched kernel");
+  return RAC_OK;
+}
+
+}  // namespace rac

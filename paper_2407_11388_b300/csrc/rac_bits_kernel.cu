@@ -30,117 +30,13 @@
 
 #include <cstdio>
 
+#include "rac_device.cuh"
 #include "rac_internal.h"
 
 namespace rac {
 namespace {
 
-constexpr uint32_t kFull = 0xFFFFFFFFu;
-
-// ------------------------------- PTX helpers -------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t global_timer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(
-                   smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n"
-      " mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait; returns false (and sets the error bit) after `limit_ns`.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, Sync *sy,
-                                          uint64_t limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_timer();
-  for (;;) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (global_timer() - t0 > limit_ns) {
-      atomicOr(&sy->err, kErrCopyWait);
-      return false;
-    }
-  }
-}
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
-                                              uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t lanemask_lt() {
-  uint32_t m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
-__device__ __forceinline__ void named_bar(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-// Domain words change between sweeps through L2 atomics: read them at L2.
-__device__ __forceinline__ uint32_t ld_dom(const uint32_t *p) { return __ldcg(p); }
-
-// The support test of one relation, rows a = 0..4Q-1 (padding rows are 0),
-// read as Q 16-byte chunks `stride` chunks apart:
-//   fwd bit a  = (R[a] & Dy) != 0        (Sup_xy[a] > 0, Fig. 1)
-//   rev        = OR over a in Dx of R[a] (bit b: (y,b) has a support in Dx)
-// Two independent accumulators per result keep the OR chains short.
-template <int Q, bool kDxFull>
-__device__ __forceinline__ void support_relation(const uint4 *rel, uint32_t stride, uint32_t Dx,
-                                                 uint32_t Dy, uint32_t &fwd, uint32_t &rev) {
-  uint32_t f0 = 0, f1 = 0, r0 = 0, r1 = 0;
-#pragma unroll
-  for (int c = 0; c < Q; ++c) {
-    const uint4 w = rel[c * stride];
-    if ((w.x & Dy) != 0u) f0 |= 1u << (4 * c + 0);
-    if ((w.y & Dy) != 0u) f1 |= 1u << (4 * c + 1);
-    if ((w.z & Dy) != 0u) f0 |= 1u << (4 * c + 2);
-    if ((w.w & Dy) != 0u) f1 |= 1u << (4 * c + 3);
-    if (kDxFull) {  // every row of R is in Dx (rows >= d are zero)
-      r0 |= w.x | w.z;
-      r1 |= w.y | w.w;
-    } else {
-      r0 |= w.x & (0u - ((Dx >> (4 * c + 0)) & 1u));
-      r1 |= w.y & (0u - ((Dx >> (4 * c + 1)) & 1u));
-      r0 |= w.z & (0u - ((Dx >> (4 * c + 2)) & 1u));
-      r1 |= w.w & (0u - ((Dx >> (4 * c + 3)) & 1u));
-    }
-  }
-  fwd = f0 | f1;
-  rev = r0 | r1;
-}
+using namespace dev;
 
 struct StageInfo {
   int32_t sl;  // slab index, -1 = end of the sweep's slabs
@@ -426,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
             }
             const int stg = prod_it % kStages;
             const uint32_t par = (prod_it / kStages) & 1u;
-            if (!mbar_wait(&S.empty[stg], par ^ 1u, P.sync, P.wait_limit_ns)) {
+            if (!mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err, P.wait_limit_ns)) {
               ok = false;
               break;
             }
@@ -442,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
           for (int e = 0; e < kGroups && ok; ++e) {
             const int stg = prod_it % kStages;
             const uint32_t par = (prod_it / kStages) & 1u;
-            if (!mbar_wait(&S.empty[stg], par ^ 1u, P.sync, P.wait_limit_ns)) {
+            if (!mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err, P.wait_limit_ns)) {
               ok = false;
               break;
             }
@@ -509,7 +405,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
           // One thread takes the bounded wait and every warp of the group
           // follows its outcome, so a wait that gives up never leaves a peer
           // warp blocked on a named barrier inside the slab evaluation.
-          if (group_leader) S.stage_ok[stg] = mbar_wait(&S.full[stg], par, P.sync, P.wait_limit_ns) ? 1u : 0u;
+          if (group_leader) S.stage_ok[stg] = mbar_wait(&S.full[stg], par, &P.sync->err, P.wait_limit_ns) ? 1u : 0u;
           named_bar(group_bar(cg), kGroupWarps * 32);
           if (!S.stage_ok[stg]) {
             if (group_leader) S.abort = 1;
@@ -613,7 +509,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
   if (is_producer && lane == 0) {
     const uint32_t first = prod_it > uint32_t(kStages) ? prod_it - kStages : 0u;
     for (uint32_t j = first; j < prod_it; ++j)
-      mbar_wait(&S.full[j % kStages], (j / kStages) & 1u, P.sync, P.wait_limit_ns);
+      mbar_wait(&S.full[j % kStages], (j / kStages) & 1u, &P.sync->err, P.wait_limit_ns);
   }
 }
 

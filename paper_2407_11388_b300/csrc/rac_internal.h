@@ -113,6 +113,57 @@ struct LaunchParams {
   SlabDesc first[kMaxFirst];
 };
 
+// ---------------------------------------------------------------------------
+// Batched launch: many networks, each with its own states, in one persistent
+// launch.  Global slab g belongs to job j iff slab_base[j] <= g <
+// slab_base[j+1]; states are numbered job by job.
+// ---------------------------------------------------------------------------
+struct BatchJob {
+  const uint4 *rel;
+  const SlabDesc *slabs;
+  int32_t n, d, q, nb;
+  int32_t n_slabs, slab_base;    // first global slab index of the job
+  int32_t n_states, state_base;  // first state of the job
+  int64_t u_off;                 // offset of the job's words in a chgU slot
+  int64_t pad;
+};
+static_assert(sizeof(BatchJob) == 64, "BatchJob is 64 bytes");
+
+struct BatchSync {
+  unsigned long long bar[3];   // end-of-sweep barrier words (as Sync::bar)
+  unsigned long long bar2[3];  // decision barrier words: arrivals | running states << 32
+  uint32_t base;
+  uint32_t err;
+};
+
+constexpr int kBatchChunk = 32;      // states staged together per slab
+constexpr int kBatchStageWords = 64; // domain words staged per state (<= 32 rows + 32 columns)
+
+struct BatchParams {
+  const BatchJob *jobs;
+  int32_t n_jobs, total_slabs, total_states;
+  const int64_t *state_off;    // word offset of state t in dom_in / dom_out
+  const int64_t *scratch_off;  // word offset of state t in bufB
+  const int64_t *chg_off;      // word offset of state t inside a chg slot
+  const int32_t *res_idx;      // result index of state t
+  const uint32_t *dom_in;
+  uint32_t *dom_out;
+  uint32_t *bufB;              // all ones between launches
+  int32_t *iterations;
+  int32_t *status;
+  uint32_t *any, *wipe;        // [3][total_states]
+  uint32_t *chg;               // [3][chg_slot_words]
+  uint32_t *chgU;              // [3][u_slot_words]
+  uint32_t *st_info;           // [total_states], zero between launches
+  uint32_t *job_alive;         // [3][n_jobs] some state of the job still runs
+  const int32_t *state_job;    // job of state t
+  int64_t chg_slot_words, u_slot_words;
+  BatchSync *sync;
+  int32_t max_sweeps;
+  uint32_t flags;
+  uint64_t wait_limit_ns;
+};
+
 // Per-(network, stream) scratch.
 struct Workspace {
   int cap_states = 0;
@@ -154,4 +205,9 @@ rac_status launch_bits(const LaunchParams &P, cudaStream_t stream);
 Workspace *get_workspace(const rac_network *net, cudaStream_t stream, int n_states, int n_items,
                          rac_status *rc);
 void free_workspace(Workspace *w);
+rac_status enforce_batch_multi(const rac_network *const *nets, int32_t n_nets, int32_t n_items,
+                               const int32_t *item_net, const int64_t *item_dom_off,
+                               const uint32_t *dom_in, uint32_t *dom_out, int32_t *iterations,
+                               int32_t *status, int32_t max_sweeps, uint32_t flags,
+                               cudaStream_t s);
 }  // namespace rac
