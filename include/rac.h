@@ -149,6 +149,28 @@ RAC_API rac_status rac_enforce(const rac_network *net, const uint32_t *dom_in, u
                        rac_stream_t stream);
 
 /*
+ * rac_assign_enforce -- one step of backtrack search (Algorithm 2): `assign`
+ * reduces dom(var) to {value}, then `tensorAC(Vars, [idx])` enforces arc
+ * consistency with var as the only changed variable, so sweep 1 examines
+ * only the constraints on var (Proposition 2) instead of every constraint.
+ *
+ *  dom_in      DEVICE, n_vars words: an ARC-CONSISTENT state (for example the
+ *              result of an earlier enforcement).  Under that precondition the
+ *              result, the removals of every sweep and the sweep count equal
+ *              those of rac_enforce on the assigned state; without it the
+ *              result may miss removals.
+ *  var, value  the assignment, 0 <= var < n_vars, 0 <= value < d (a value
+ *              outside dom_in[var] empties that domain: a wipe-out).
+ *  dom_out, iterations, status, max_sweeps, flags, stream: as rac_enforce
+ *              (dom_out receives the assigned and enforced state).
+ * Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA.
+ */
+RAC_API rac_status rac_assign_enforce(const rac_network *net, const uint32_t *dom_in,
+                                      uint32_t *dom_out, int32_t var, int32_t value,
+                                      int32_t *iterations, int32_t *status, int32_t max_sweeps,
+                                      uint32_t flags, rac_stream_t stream);
+
+/*
  * rac_enforce_batch -- many independent (network, domain state) items.
  *
  *  nets          HOST array of network handles.

@@ -30,7 +30,7 @@ STATUS_NAMES = {OK: "ok", WIPEOUT: "wipeout", EINVAL: "einval", ENOMEM: "enomem"
 
 ABI_FUNCTIONS = ("rac_create_network", "rac_destroy", "rac_enforce", "rac_enforce_batch",
                  "rac_enforce_host", "rac_enforce_noalloc", "rac_network_info", "rac_last_error",
-                 "rac_plan_create", "rac_plan_enforce", "rac_plan_destroy")
+                 "rac_plan_create", "rac_plan_enforce", "rac_plan_destroy", "rac_assign_enforce")
 NOALLOC_MAX_VARS = 65536
 
 
@@ -69,6 +69,8 @@ def lib():
         L.rac_plan_enforce.argtypes = [vp, vp, vp, vp, vp, i32, u32, vp]
         L.rac_plan_destroy.restype = None
         L.rac_plan_destroy.argtypes = [vp]
+        L.rac_assign_enforce.restype = i32
+        L.rac_assign_enforce.argtypes = [vp, vp, vp, i32, i32, vp, vp, i32, u32, vp]
         L.rac_network_info.restype = i32
         L.rac_network_info.argtypes = [vp, ctypes.POINTER(i64), i32]
         L.rac_last_error.restype = ctypes.c_char_p
@@ -162,6 +164,17 @@ def enforce(net, dom_in, dom_out, iterations, status, max_sweeps=0, flags=0, str
     _check(lib().rac_enforce(net.handle, _ptr(dom_in), _ptr(dom_out), _ptr(iterations),
                              _ptr(status), int(max_sweeps), int(flags), _stream(stream)),
            "rac_enforce")
+
+
+def assign_enforce(net, dom_in, dom_out, var, value, iterations, status, max_sweeps=0, flags=0,
+                   stream=None):
+    """One backtrack-search step (Algorithm 2): dom(var) := {value}, then
+    enforcement whose first sweep examines only the constraints on var.
+    dom_in must be arc consistent (rac_assign_enforce in include/rac.h)."""
+    _check(lib().rac_assign_enforce(net.handle, _ptr(dom_in), _ptr(dom_out), int(var), int(value),
+                                    _ptr(iterations), _ptr(status), int(max_sweeps), int(flags),
+                                    _stream(stream)),
+           "rac_assign_enforce")
 
 
 def enforce_noalloc(net, dom_in, dom_out, iterations, status, max_sweeps=0, flags=0,

@@ -139,6 +139,8 @@ LaunchParams base_params(const rac_network *net, Workspace *w, int n_states, int
   P.sweep_bound = int32_t(std::min<int64_t>(bound, 0xFFFFF0));
   P.flags = flags;
   P.wait_limit_ns = wait_limit_for(flags);
+  P.seed_var = -1;
+  P.seed_keep = 0xFFFFFFFFu;
   P.n_first = int32_t(std::min<size_t>(net->first.size(), kMaxFirst));
   for (int32_t i = 0; i < P.n_first; ++i) P.first[i] = net->first[size_t(i)];
   return P;
@@ -375,6 +377,38 @@ rac_status rac_enforce(const rac_network *net, const uint32_t *dom_in, uint32_t 
   P.dom_out = dom_out;
   P.iterations = iterations;
   P.status = status;
+  return launch_bits(P, s);
+}
+
+rac_status rac_assign_enforce(const rac_network *net, const uint32_t *dom_in, uint32_t *dom_out,
+                              int32_t var, int32_t value, int32_t *iterations, int32_t *status,
+                              int32_t max_sweeps, uint32_t flags, rac_stream_t stream) {
+  set_error("");
+  if (!net || !dom_in || !dom_out || !iterations || !status) {
+    set_error("NULL argument");
+    return RAC_EINVAL;
+  }
+  if (var < 0 || var >= net->n || value < 0 || value >= net->d) {
+    set_error("assignment out of range");
+    return RAC_EINVAL;
+  }
+  if (flags & ~kKnownFlags) {
+    set_error("unknown flag");
+    return RAC_EINVAL;
+  }
+  if (!check_device(net)) return RAC_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  rac_status rc = RAC_OK;
+  Workspace *w = get_workspace(net, s, 1, 0, &rc);
+  if (!w) return rc;
+  LaunchParams P = base_params(net, w, 1, max_sweeps, flags);
+  P.contiguous = 1;
+  P.dom_in = dom_in;
+  P.dom_out = dom_out;
+  P.iterations = iterations;
+  P.status = status;
+  P.seed_var = var;
+  P.seed_keep = 1u << value;
   return launch_bits(P, s);
 }
 

@@ -85,6 +85,21 @@ __device__ __forceinline__ int group_bar(int cg) { return 2 + cg; }
 __device__ __forceinline__ int state_group_bar(int cg, int g) { return 2 + kGroups + 2 * cg + g; }
 static_assert(2 + kGroups + 2 * kGroups <= 16, "named barrier ids");
 
+// The input domain word of variable x as sweep 1 sees it (the search's
+// assignment, if any, applied).
+__device__ __forceinline__ uint32_t input_word(const LaunchParams &P, int x, uint32_t v) {
+  return x == P.seed_var ? (v & P.seed_keep) : v;
+}
+
+// Does a slab of rows [row0, row0 + nrows) of block I and columns of block J
+// hold a constraint on the seeded variable (sweep 1 of an assignment)?
+__device__ __forceinline__ bool slab_touches_seed(const LaunchParams &P, uint32_t I, uint32_t J,
+                                                  uint32_t row0, uint32_t nrows) {
+  const uint32_t sv = uint32_t(P.seed_var);
+  if ((sv >> 5) == J) return true;
+  return (sv >> 5) == I && (sv & 31u) >= row0 && (sv & 31u) < row0 + nrows;
+}
+
 struct StateView {
   const uint32_t *C;  // D_{k-1}
   uint32_t *T;        // becomes D_k
@@ -187,6 +202,7 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
   const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
   const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
   const bool cached = S.dom_cached != 0;
+  if (k == 1 && P.seed_var >= 0 && !slab_touches_seed(P, I, J, row0, nrows)) return;
   for (int s = g; s < P.n_states; s += groups) {
     if (S.st_info[s] & kInfoSweepMask) continue;  // finished state
     if (incr) {
@@ -195,13 +211,15 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
     }
     const StateView V = state_view(P, s, k);
     const uint32_t *Dc = cached ? S.dom + s * n : V.C;
-    const uint32_t Dy = y_ok ? (cached ? Dc[y] : ld_dom(Dc + y)) : 0u;
+    uint32_t Dy = y_ok ? (cached ? Dc[y] : ld_dom(Dc + y)) : 0u;
+    if (k == 1 && !cached) Dy = input_word(P, y, Dy);
     uint32_t racc = kFull;
     for (int r = sub; r < int(nrows); r += wps) {
       const uint32_t pm = hdr[r];
       if (pm == 0u) continue;
       const int x = int(I) * 32 + int(row0) + r;
-      const uint32_t Dx = cached ? Dc[x] : ld_dom(Dc + x);
+      uint32_t Dx = cached ? Dc[x] : ld_dom(Dc + x);
+      if (k == 1 && !cached) Dx = input_word(P, x, Dx);
       uint32_t fwd = kFull, rev = kFull;
       if ((pm >> lane) & 1u) {
         // this lane's relation: rank t in the row, chunk c at c * cnt + t
@@ -273,7 +291,9 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
   uint32_t prod_it = 0;   // producer-side position in the ring
   uint32_t red_iter = 0;  // parity of the cross-warp reduction buffer
   if (is_producer) {
-    if (lane == 0 && my_slabs > 0 && cta < P.n_first) {
+    if (lane == 0 && my_slabs > 0 && cta < P.n_first &&
+        (P.seed_var < 0 || slab_touches_seed(P, P.first[cta].ij & 0xFFFFu, P.first[cta].ij >> 16,
+                                             P.first[cta].rows & 0xFFu, P.first[cta].rows >> 8))) {
       // the first slab's descriptor came with the launch: no load before it
       const SlabDesc sd = P.first[cta];
       S.stage[0].sl = cta;
@@ -319,6 +339,10 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
               const uint32_t row0 = sd.rows & 0xFFu, nrows = sd.rows >> 8;
               const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
               if (ld_dom(cu + J) == 0u && (ld_dom(cu + I) & rowmask) == 0u) continue;
+            } else if (k == 1 && P.seed_var >= 0 &&
+                       !slab_touches_seed(P, sd.ij & 0xFFFFu, sd.ij >> 16, sd.rows & 0xFFu,
+                                          sd.rows >> 8)) {
+              continue;  // sweep 1 of an assignment: only constraints on the assigned variable
             }
             const int stg = prod_it % kStages;
             const uint32_t par = (prod_it / kStages) & 1u;
@@ -355,7 +379,8 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
           for (int i = ctid; i < B * n; i += kConsumerWarps * 32) {
             const int s = i / n;
             if (S.st_info[s] & kInfoSweepMask) continue;
-            S.dom[i] = ld_dom(state_view(P, s, k).C + (i - s * n));
+            const uint32_t v = ld_dom(state_view(P, s, k).C + (i - s * n));
+            S.dom[i] = k == 1 ? input_word(P, i - s * n, v) : v;
           }
         }
         // clear the slot written next sweep (last read two sweeps ago)
@@ -374,7 +399,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
           for (int64_t i = cgtid; i < int64_t(B) * n; i += cgstride) {
             const int s = int(i / n), x = int(i % n);
             const int64_t off = state_offset(P, s);
-            const uint32_t v = S.dom_cached ? S.dom[i] : P.dom_in[off + x];
+            const uint32_t v = S.dom_cached ? S.dom[i] : input_word(P, x, P.dom_in[off + x]);
             atomicAnd(P.bufB + i, v);
             if (P.dom_out != P.dom_in) P.dom_out[off + x] = v;
             if (v == 0u) S.wipe_loc[s] = 1;  // D_1 will hold this empty domain

@@ -109,6 +109,9 @@ struct LaunchParams {
   int32_t sweep_bound;       // hard bound (|D| + 2), a safety net only
   uint32_t flags;
   uint64_t wait_limit_ns;    // every device-side wait gives up after this long
+  int32_t seed_var;          // >= 0: the search's assignment (one state only): the
+  uint32_t seed_keep;        //   input domain of seed_var is ANDed with seed_keep, and
+                             //   sweep 1 examines only the constraints on seed_var
   int32_t n_first;           // CTAs whose first slab descriptor is in `first`
   SlabDesc first[kMaxFirst];
 };

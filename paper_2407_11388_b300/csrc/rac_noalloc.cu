@@ -122,6 +122,8 @@ extern "C" rac_status rac_enforce_noalloc(const rac_network *net, const uint32_t
   P.sweep_bound = int32_t(bound < 0xFFFFF0 ? bound : 0xFFFFF0);
   P.flags = flags;
   P.wait_limit_ns = wait_limit_for(flags);
+  P.seed_var = -1;
+  P.seed_keep = 0xFFFFFFFFu;
   P.n_first = int32_t(net->first.size() < size_t(kMaxFirst) ? net->first.size() : kMaxFirst);
   for (int32_t i = 0; i < P.n_first; ++i) P.first[i] = net->first[size_t(i)];
   // what the kernel expects to find: sync words and flags zero, the scratch

@@ -1,0 +1,83 @@
+"""Backtrack search over the device enforcement (Algorithm 2 of the paper).
+
+`dfs` follows Algorithm 2: enforce arc consistency on the initial domains
+(`tensorAC(Vars, all)`), then repeatedly pick a variable, try its values in
+order, and after each `assign` enforce with only that variable changed
+(`tensorAC(Vars, [idx])`, rac_assign_enforce), descending while no domain is
+empty and backtracking otherwise.  The states of the levels stay on the
+device; the host reads a state back only to apply the variable-ordering
+heuristic, which the paper leaves open (here: smallest domain of size > 1,
+lowest index first).  Every assignment's sweep count is recorded: it is the
+quantity Table 1 reports as #Recurrence.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import OK, assign_enforce, enforce
+
+
+@dataclass
+class SearchResult:
+    solution: object = None              # uint32 domain words (all singletons) or None
+    steps: list = field(default_factory=list)  # (level, var, value, iterations, status)
+    root_iterations: int = 0
+    root_status: int = OK
+    nodes: int = 0
+    exhausted: bool = False              # the node budget ran out
+
+    def mean_sweeps(self):
+        return float(np.mean([s[3] for s in self.steps])) if self.steps else 0.0
+
+
+def choose_variable(dom):
+    """Smallest domain of size > 1, lowest index; None when all are singletons."""
+    sizes = np.array([bin(int(w)).count("1") for w in dom])
+    open_vars = np.flatnonzero(sizes > 1)
+    if open_vars.size == 0:
+        return None
+    return int(open_vars[np.argmin(sizes[open_vars])])
+
+
+def dfs(net, dom0, max_nodes=10_000, stream=None, flags=0):
+    """Depth-first search of Algorithm 2 on the device.  dom0: host uint32
+    words (n).  Returns a SearchResult."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = net.n
+    res = SearchResult()
+    levels = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(n + 1)]
+    it = torch.empty(1, dtype=torch.int32, device=dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    levels[0].copy_(torch.from_numpy(np.ascontiguousarray(dom0, dtype=np.uint32).view(np.int32)))
+    enforce(net, levels[0], levels[0], it, st, flags=flags, stream=stream)
+    res.root_iterations = int(it.item())
+    res.root_status = int(st.item())
+    if res.root_status != OK:
+        return res
+
+    def rec(level):
+        dom = levels[level].cpu().numpy().view(np.uint32)
+        var = choose_variable(dom)
+        if var is None:
+            res.solution = dom.copy()
+            return True
+        for value in range(net.d):
+            if not (int(dom[var]) >> value) & 1:
+                continue
+            if res.nodes >= max_nodes:
+                res.exhausted = True
+                return False
+            res.nodes += 1
+            assign_enforce(net, levels[level], levels[level + 1], var, value, it, st,
+                           flags=flags, stream=stream)
+            iters, status = int(it.item()), int(st.item())
+            res.steps.append((level, var, value, iters, status))
+            if status == OK and rec(level + 1):
+                return True
+            if res.exhausted:
+                return False
+        return False
+
+    rec(0)
+    return res

@@ -1,0 +1,98 @@
+"""The search driver (Algorithm 2) on the device against the same search
+run with the CPU oracle: the same assignments, the same sweep counts per
+assignment (the seeded first sweep must not change them), the same outcome
+(GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+import racgen
+import paper_2407_11388_b300 as rac
+from paper_2407_11388_b300.search import choose_variable, dfs
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_dfs(n, d, scope, rel, dom0, max_nodes):
+    out = {"steps": [], "nodes": 0, "solution": None, "exhausted": False}
+    root, rit, rst = oracle.rac(n, d, scope, rel, dom0)
+    out["root"] = (rit, rst)
+    if rst != oracle.OK:
+        return out
+
+    def rec(level, dom):
+        var = choose_variable(dom)
+        if var is None:
+            out["solution"] = dom.copy()
+            return True
+        for value in range(d):
+            if not (int(dom[var]) >> value) & 1:
+                continue
+            if out["nodes"] >= max_nodes:
+                out["exhausted"] = True
+                return False
+            out["nodes"] += 1
+            nxt = dom.copy()
+            nxt[var] = np.uint32(1 << value)
+            res, it, st = oracle.rac(n, d, scope, rel, nxt)  # plain recurrence, all constraints
+            out["steps"].append((level, var, value, it, st))
+            if st == oracle.OK and rec(level + 1, res):
+                return True
+            if out["exhausted"]:
+                return False
+        return False
+
+    rec(0, root)
+    return out
+
+
+@pytest.mark.parametrize("seed,n,d,p,t", [(1, 40, 8, 0.3, 0.35), (2, 60, 10, 0.5, 0.3),
+                                          (3, 90, 6, 0.2, 0.25), (4, 150, 12, 0.8, 0.2)])
+def test_search_matches_oracle(seed, n, d, p, t):
+    net_np = racgen.random_network(seed, 0, n, d, p, t)
+    dom0 = racgen.full_domain(n, d)
+    want = oracle_dfs(n, d, net_np.scope, net_np.rel, dom0, max_nodes=200)
+    with rac.Network(n, d, net_np.scope, net_np.rel) as net:
+        for flags in (0, rac.INCREMENTAL):
+            got = dfs(net, dom0, max_nodes=200, flags=flags)
+            assert (got.root_iterations, got.root_status) == want["root"]
+            assert got.steps == want["steps"]
+            assert got.exhausted == want["exhausted"]
+            if want["solution"] is None:
+                assert got.solution is None
+            else:
+                assert np.array_equal(got.solution, want["solution"])
+    assert len(want["steps"]) >= 5
+
+
+def test_assign_enforce_equals_full_enforcement():
+    """From arc-consistent states: the seeded enforcement gives the plain
+    recurrence's result and sweep count for every single assignment."""
+    T = __import__("torch")
+    n, d = 200, 16
+    net_np = racgen.random_network(11, 0, n, d, 0.6, 0.45)
+    base, _, st = oracle.rac(n, d, net_np.scope, net_np.rel, racgen.full_domain(n, d))
+    assert st == oracle.OK
+    rng = np.random.default_rng(11)
+    with rac.Network(n, d, net_np.scope, net_np.rel) as net:
+        din = T.from_numpy(base.view(np.int32)).to("cuda:0")
+        dout = T.empty_like(din)
+        it = T.empty(1, dtype=T.int32, device="cuda:0")
+        stt = T.empty(1, dtype=T.int32, device="cuda:0")
+        for _ in range(25):
+            var = int(rng.integers(0, n))
+            value = int(rng.integers(0, d))  # possibly outside the domain: a wipe-out
+            assigned = base.copy()
+            assigned[var] = base[var] & np.uint32(1 << value)
+            ro, ri, rs = oracle.rac(n, d, net_np.scope, net_np.rel, assigned)
+            for flags in (0, rac.INCREMENTAL, rac.STOP_ON_WIPEOUT):
+                rac.assign_enforce(net, din, dout, var, value, it, stt, flags=flags)
+                T.cuda.synchronize()
+                if flags & rac.STOP_ON_WIPEOUT:
+                    so, si, ss = oracle.rac(n, d, net_np.scope, net_np.rel, assigned,
+                                            stop_on_wipeout=True)
+                    want = (so, si, ss)
+                else:
+                    want = (ro, ri, rs)
+                assert np.array_equal(dout.cpu().numpy().view(np.uint32), want[0])
+                assert int(it.item()) == want[1] and int(stt.item()) == want[2]
