@@ -82,6 +82,12 @@ typedef int32_t rac_status;
                                     domain changed in sweep k-1.  The result,
                                     every sweep's removals and the sweep count
                                     are identical to the plain recurrence. */
+#define RAC_KERNEL_TENSOR 0x10u  /* evaluate the support counts with the tensor-core
+                                    kernel (tcgen05 FP8 GEMMs, FP32 accumulation in
+                                    tensor memory) instead of the bit-packed kernel:
+                                    rac_enforce and single-network rac_enforce_batch
+                                    only, at most 128 states per launch (larger
+                                    batches are split).  Results are identical. */
 #define RAC_TEST_WITHHOLD_ARRIVAL 0x80000000u
                                  /* test hook for failure detection: one CTA
                                     withholds its first grid-barrier arrival,

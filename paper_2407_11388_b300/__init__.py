@@ -23,6 +23,7 @@ EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBARRIER, ENOTSUP = -1, -2, -3, -4, -5, -6
 LAYOUT_BITS = 0x1
 STOP_ON_WIPEOUT = 0x1
 INCREMENTAL = 0x2
+KERNEL_TENSOR = 0x10  # tcgen05 tensor-core kernel (see include/rac.h)
 TEST_WITHHOLD_ARRIVAL = 0x80000000  # failure-detection test hook (see include/rac.h)
 
 STATUS_NAMES = {OK: "ok", WIPEOUT: "wipeout", EINVAL: "einval", ENOMEM: "enomem",

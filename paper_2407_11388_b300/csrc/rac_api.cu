@@ -146,7 +146,12 @@ LaunchParams base_params(const rac_network *net, Workspace *w, int n_states, int
   return P;
 }
 
-constexpr uint32_t kKnownFlags = RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL | RAC_TEST_WITHHOLD_ARRIVAL;
+constexpr uint32_t kKnownFlags =
+    RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL | RAC_KERNEL_TENSOR | RAC_TEST_WITHHOLD_ARRIVAL;
+
+rac_status launch_for(const LaunchParams &P, uint32_t flags, cudaStream_t s) {
+  return (flags & RAC_KERNEL_TENSOR) ? launch_tc(P, s) : launch_bits(P, s);
+}
 
 // Largest power of two rows (<= 32) whose slab fits one ring stage.
 int rows_per_slab_for(int dp) {
@@ -377,7 +382,7 @@ rac_status rac_enforce(const rac_network *net, const uint32_t *dom_in, uint32_t 
   P.dom_out = dom_out;
   P.iterations = iterations;
   P.status = status;
-  return launch_bits(P, s);
+  return launch_for(P, flags, s);
 }
 
 rac_status rac_assign_enforce(const rac_network *net, const uint32_t *dom_in, uint32_t *dom_out,
@@ -395,6 +400,10 @@ rac_status rac_assign_enforce(const rac_network *net, const uint32_t *dom_in, ui
   if (flags & ~kKnownFlags) {
     set_error("unknown flag");
     return RAC_EINVAL;
+  }
+  if (flags & RAC_KERNEL_TENSOR) {
+    set_error("the seeded first sweep of an assignment runs on the bit-packed kernel only");
+    return RAC_ENOTSUP;
   }
   if (!check_device(net)) return RAC_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -449,6 +458,12 @@ rac_status rac_enforce_batch(const rac_network *const *nets, int32_t n_nets, int
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int32_t used_nets = 0;
   for (int32_t k = 0; k < n_nets; ++k) used_nets += groups[size_t(k)].empty() ? 0 : 1;
+  if (used_nets > 1 && (flags & RAC_KERNEL_TENSOR)) {
+    set_error("the tensor-core kernel takes the states of one network per call");
+    return RAC_ENOTSUP;
+  }
+  const size_t chunk = (flags & RAC_KERNEL_TENSOR) ? size_t(kTensorMaxStates)
+                                                   : size_t(kMaxStatesPerLaunch);
   if (used_nets > 1)  // one persistent launch over all networks
     return enforce_batch_multi(nets, n_nets, n_items, item_net, item_dom_off, dom_in, dom_out,
                                iterations, status, max_sweeps, flags, s);
@@ -456,8 +471,8 @@ rac_status rac_enforce_batch(const rac_network *const *nets, int32_t n_nets, int
   std::vector<int32_t> idx;
   for (int32_t k = 0; k < n_nets; ++k) {
     const std::vector<int32_t> &g = groups[size_t(k)];
-    for (size_t base = 0; base < g.size(); base += kMaxStatesPerLaunch) {
-      const int cnt = int(std::min<size_t>(kMaxStatesPerLaunch, g.size() - base));
+    for (size_t base = 0; base < g.size(); base += chunk) {
+      const int cnt = int(std::min<size_t>(chunk, g.size() - base));
       rac_status rc = RAC_OK;
       Workspace *w = get_workspace(nets[k], s, cnt, cnt, &rc);
       if (!w) return rc;
@@ -483,7 +498,7 @@ rac_status rac_enforce_batch(const rac_network *const *nets, int32_t n_nets, int
       P.iterations = iterations;
       P.status = status;
       // a later chunk on this workspace is stream-ordered after this launch
-      rc = launch_bits(P, s);
+      rc = launch_for(P, flags, s);
       if (rc != RAC_OK) return rc;
     }
   }
@@ -532,8 +547,9 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
   int32_t *d_res = w0->host_res;
   cudaError_t e = cudaMemcpyAsync(d_dom, dom_in, words * 4, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) rc = cuda_fail(e, "host-to-device copy");
-  for (int32_t base = 0; rc == RAC_OK && base < n_states; base += kMaxStatesPerLaunch) {
-    const int cnt = std::min<int32_t>(kMaxStatesPerLaunch, n_states - base);
+  const int32_t chunk = (flags & RAC_KERNEL_TENSOR) ? kTensorMaxStates : kMaxStatesPerLaunch;
+  for (int32_t base = 0; rc == RAC_OK && base < n_states; base += chunk) {
+    const int cnt = std::min<int32_t>(chunk, n_states - base);
     Workspace *w = get_workspace(net, s, cnt, 0, &rc);
     if (!w) break;
     LaunchParams P = base_params(net, w, cnt, max_sweeps, flags);
@@ -542,7 +558,7 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
     P.dom_out = d_dom + size_t(base) * net->n;
     P.iterations = d_res + base;
     P.status = d_res + n_states + base;
-    rc = launch_bits(P, s);
+    rc = launch_for(P, flags, s);
   }
   if (rc == RAC_OK) {
     e = cudaMemcpyAsync(dom_out, d_dom, words * 4, cudaMemcpyDeviceToHost, s);

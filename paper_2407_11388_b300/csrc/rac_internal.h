@@ -205,6 +205,9 @@ rac_status cuda_fail(cudaError_t e, const char *what);
 NetDev net_dev(const rac_network *net);
 // Launch the bit-packed kernel for P (grid sized by the callee).
 rac_status launch_bits(const LaunchParams &P, cudaStream_t stream);
+// Launch the tensor-core kernel for P (at most 128 states).
+rac_status launch_tc(const LaunchParams &P, cudaStream_t stream);
+constexpr int kTensorMaxStates = 128;
 Workspace *get_workspace(const rac_network *net, cudaStream_t stream, int n_states, int n_items,
                          rac_status *rc);
 void free_workspace(Workspace *w);

@@ -208,7 +208,7 @@ rac_status plan_launch(const rac_plan *p, const uint32_t *dom_in, uint32_t *dom_
   return launch_batch(P, s);
 }
 
-constexpr uint32_t kPlanFlags = RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL | RAC_TEST_WITHHOLD_ARRIVAL;
+constexpr uint32_t kPlanFlags = RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL | RAC_TEST_WITHHOLD_ARRIVAL;  // no tensor kernel
 
 }  // namespace
 
