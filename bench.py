@@ -40,6 +40,13 @@ WORKLOADS = {
     "dense_n2000_d32": dict(n=2000, d=32, density=0.9, tightness=0.3, states="full", n_states=1),
     "n1000_d24_b32": dict(n=1000, d=24, density=0.8, tightness=0.3, states="assign",
                           n_states=32),
+    "n1000_d24_b64": dict(n=1000, d=24, density=0.8, tightness=0.3, states="assign",
+                          n_states=64),
+    "n1000_d24_b128": dict(n=1000, d=24, density=0.8, tightness=0.3, states="assign",
+                           n_states=128),
+    # 256 networks, n ~ U{50..800}, d ~ U{8..32}, density ~ U[0.3,1],
+    # tightness ~ U[0.2,0.4], 64 assignment states each: one launch per step
+    "batch256_x64": dict(batch=True, networks=256, states_per_net=64),
 }
 DEFAULT_WORKLOAD = "dense_n500_d20"
 
@@ -68,6 +75,24 @@ def make_inputs(wl, seed):
         doms = np.array([racgen.assignment_state(seed, 0, s, spec["n"], spec["d"])
                          for s in range(spec["n_states"])])
     return spec, net, doms
+
+
+def make_batch(seed, networks, states_per_net):
+    """Uneven batch: networks with racgen.batch_params shapes, assignment
+    states interleaved over networks and stored back to back."""
+    import racgen
+    nets = [racgen.random_network(seed, i, *racgen.batch_params(seed, i)) for i in range(networks)]
+    items, offs, doms = [], [], []
+    pos = 0
+    for s in range(states_per_net):
+        for i, x in enumerate(nets):
+            dom = racgen.assignment_state(seed, i, s, x.n, x.d)
+            items.append(i)
+            offs.append(pos)
+            doms.append(dom)
+            pos += x.n
+    flat = np.concatenate(doms).astype(np.uint32)
+    return nets, np.array(items, np.int32), np.array(offs, np.int64), doms, flat
 
 
 def config_of(wl, spec, net, flush):
@@ -222,63 +247,156 @@ def dist_setup(args):
     return world, rank, local
 
 
-def cpu_baseline(spec, net, doms, budget_s=15.0):
+def cpu_baseline(W, budget_s=15.0):
     """The oracle (literal Eq. 1 sweeps, OpenMP over variables) on a bounded
-    sample of the same workload: whole fixpoints of the first states until the
-    time budget is used."""
+    sample of the same workload: whole fixpoints of its items, in order,
+    until the time budget is used."""
     import oracle
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
     done = 0
     sweeps = 0
     while True:
-        s = done % doms.shape[0]
-        _, it, _ = oracle.rac(spec["n"], spec["d"], net.scope, net.rel, doms[s], threads=threads)
+        j = done % W.B
+        x = W.nets_np[int(W.items[j])]
+        _, it, _ = oracle.rac(x.n, x.d, x.scope, x.rel, W.doms[j], threads=threads)
         done += 1
         sweeps += it
         el = time.perf_counter() - t0
         if el >= budget_s or done >= 1000:
             break
     return {"value": done / el, "unit": "fixpoints/s", "cores": threads, "kind": "oracle",
-            "sample": "%d whole fixpoints (%d sweeps) of this workload's states, %.1f s" % (
+            "sample": "%d whole fixpoints (%d sweeps) of this workload's items, %.1f s" % (
                 done, sweeps, el)}, sweeps / done
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle (literal Eq. 1) on this workload's
+    items, one whole fixpoint per step, on all host cores; the step count is
+    capped so the run ends within a few minutes."""
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return
-    spec, net, doms = make_inputs(args.workload, args.seed)
     import oracle
+    spec = WORKLOADS[args.workload]
+    if spec.get("batch"):
+        nets_np, items, _, doms, _ = make_batch(args.seed, spec["networks"], spec["states_per_net"])
+        cfg = {"workload": args.workload, "networks": spec["networks"],
+               "states_per_network": spec["states_per_net"]}
+    else:
+        _, net, dm = make_inputs(args.workload, args.seed)
+        nets_np, items, doms = [net], np.zeros(dm.shape[0], np.int32), list(dm)
+        cfg = config_of(args.workload, spec, net, True)
     threads = os.cpu_count() or 1
-    # one step = one whole fixpoint of one state; cap the steps to a few minutes
+
+    def one(j):
+        x = nets_np[int(items[j % len(items)])]
+        return oracle.rac(x.n, x.d, x.scope, x.rel, doms[j % len(items)], threads=threads)[1]
+
     t0 = time.perf_counter()
-    oracle.rac(spec["n"], spec["d"], net.scope, net.rel, doms[0], threads=threads)
+    one(0)
     est = time.perf_counter() - t0
     steps = max(1, min(args.steps, int(150.0 / max(est, 1e-6))))
     warm = max(0, min(args.warmup, 3))
     for w in range(warm):
-        oracle.rac(spec["n"], spec["d"], net.scope, net.rel, doms[w % doms.shape[0]], threads=threads)
+        one(w)
     sweeps = 0
+    bits = 0.0
     t0 = time.perf_counter()
-    for s in range(steps):
-        _, it, _ = oracle.rac(spec["n"], spec["d"], net.scope, net.rel, doms[s % doms.shape[0]],
-                              threads=threads)
+    for j in range(steps):
+        it = one(j)
+        x = nets_np[int(items[j % len(items)])]
         sweeps += it
+        bits += float(x.m) * x.d * x.d * it
     el = time.perf_counter() - t0
     value = steps / el
     line = {"metric": METRIC, "value": value, "unit": "fixpoints/s", "impl": "reference",
             "n_gpus": args.gpus, "steps": steps, "warmup": warm,
             "ms_per_step": 1000.0 * el / steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": config_of(args.workload, spec, net, True),
-            "relation_bits_per_s": float(net.m) * spec["d"] ** 2 * sweeps / el,
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": cfg,
+            "relation_bits_per_s": bits / el,
             "cpu_baseline": {"value": value, "unit": "fixpoints/s", "cores": threads,
                              "kind": "oracle",
                              "sample": "%d whole fixpoints (requested %d steps)" % (steps, args.steps)},
             "e2e": {"value": value, "unit": "fixpoints/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+class Prepared:
+    """The workload resident on the device, and how one step enforces it."""
+
+    def __init__(self, args, rac, torch, dev):
+        spec = WORKLOADS[args.workload]
+        self.spec = spec
+        if spec.get("batch"):
+            nets_np, items, offs, doms, flat = make_batch(args.seed, spec["networks"],
+                                                          spec["states_per_net"])
+            self.cfg = {"workload": args.workload, "networks": spec["networks"],
+                        "states_per_network": spec["states_per_net"],
+                        "n": "U{50..800}", "d": "U{8..32}", "density": "U[0.3,1.0]",
+                        "tightness": "U[0.2,0.4]", "constraints": int(sum(x.m for x in nets_np)),
+                        "state_kind": "assign", "seed_generated": True,
+                        "l2": "flushed between timed steps"}
+        else:
+            _, net_np, dm = make_inputs(args.workload, args.seed)
+            nets_np = [net_np]
+            B = dm.shape[0]
+            items = np.zeros(B, np.int32)
+            offs = np.arange(B, dtype=np.int64) * net_np.n
+            doms = list(dm)
+            flat = dm.reshape(-1)
+            self.cfg = config_of(args.workload, spec, net_np, True)
+        self.nets_np, self.items, self.offs, self.doms = nets_np, items, offs, doms
+        self.B = len(items)
+        self.nets = [rac.Network(x.n, x.d, x.scope, x.rel) for x in nets_np]
+        self.flat = flat
+        self.din = torch.from_numpy(np.ascontiguousarray(flat).view(np.int32)).to(dev)
+        self.dout = torch.empty_like(self.din)
+        self.it = torch.empty(self.B, dtype=torch.int32, device=dev)
+        self.st = torch.empty(self.B, dtype=torch.int32, device=dev)
+        self.plan = rac.Plan(self.nets, items, offs) if len(self.nets) > 1 else None
+        self.rac = rac
+        self.torch = torch
+        self.dev = dev
+
+    def step(self, flags, stream):
+        rac = self.rac
+        if self.plan is not None:
+            self.plan.enforce(self.din, self.dout, self.it, self.st, flags=flags, stream=stream)
+        elif self.B == 1:
+            rac.enforce(self.nets[0], self.din, self.dout, self.it, self.st, flags=flags,
+                        stream=stream)
+        else:
+            rac.enforce_batch(self.nets, self.items, self.offs, self.din, self.dout, self.it,
+                              self.st, flags=flags, stream=stream)
+
+    def plain_step(self, stream, ptr_in, ptr_out, it_ptr, st_ptr):
+        """Plain GPU RAC on the same items: one single-state launch per item."""
+        L = self.rac.lib()
+        sh = stream.cuda_stream
+        for j in range(self.B):
+            net = self.nets[int(self.items[j])]
+            o = int(self.offs[j]) * 4
+            rc = L.rac_enforce(net.handle, ptr_in + o, ptr_out + o, it_ptr + 4 * j, st_ptr + 4 * j,
+                               0, 0, sh)
+            if rc != 0:
+                raise self.rac.RacError(rc, self.rac.last_error())
+
+    def alg_bytes(self, its):
+        """m d^2 / 8 bytes per network per sweep that any of its states ran:
+        a launch reads each relation once per sweep for all of its states."""
+        per_net = {}
+        for j in range(self.B):
+            k = int(self.items[j])
+            per_net[k] = max(per_net.get(k, 0), int(its[j]))
+        return float(sum(self.nets_np[k].m * self.nets_np[k].d ** 2 / 8.0 * sw
+                         for k, sw in per_net.items()))
+
+    def plain_bits(self, its):
+        """Relation bits of the plain recurrence: m d^2 per state per sweep."""
+        return float(sum(self.nets_np[int(self.items[j])].m * self.nets_np[int(self.items[j])].d ** 2
+                         * int(its[j]) for j in range(self.B)))
 
 
 def run_ours(args):
@@ -297,32 +415,17 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
 
-    spec, net_np, doms = make_inputs(args.workload, args.seed)
-    n, d, B = spec["n"], spec["d"], spec["n_states"]
-    net = rac.Network(n, d, net_np.scope, net_np.rel)
+    W = Prepared(args, rac, torch, dev)
+    B = W.B
     stream = torch.cuda.current_stream()
-    din = torch.from_numpy(doms.reshape(-1).view(np.int32)).to(dev)
-    dout = torch.empty_like(din)
-    it = torch.empty(B, dtype=torch.int32, device=dev)
-    st = torch.empty(B, dtype=torch.int32, device=dev)
-    offs = np.arange(B, dtype=np.int64) * n
-    items = np.zeros(B, np.int32)
-
-    def step():
-        if B == 1:
-            rac.enforce(net, din, dout, it, st, flags=args.flags, stream=stream)
-        else:
-            rac.enforce_batch([net], items, offs, din, dout, it, st, flags=args.flags,
-                              stream=stream)
-
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
     for _ in range(max(3, args.warmup)):
-        step()
+        W.step(args.flags, stream)
         flush.zero_()
     torch.cuda.synchronize()
-    sweeps = int(it.max().item())
-    total_sweeps = int(it.sum().item())
-    statuses = st.cpu().numpy()
+    its = W.it.cpu().numpy()
+    statuses = W.st.cpu().numpy()
+    total_sweeps = int(its.sum())
 
     K = args.steps
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
@@ -334,7 +437,7 @@ def run_ours(args):
         w0 = time.perf_counter()
         for i in range(K):
             starts[i].record(stream)
-            step()
+            W.step(args.flags, stream)
             ends[i].record(stream)
             flush.zero_()
         torch.cuda.synchronize()
@@ -343,19 +446,43 @@ def run_ours(args):
         pg.barrier()
     dev_ms = max_over_ranks(float(sum(s.elapsed_time(e) for s, e in zip(starts, ends))))
     per_step_s = dev_ms / 1000.0 / K
-    fix_per_s = world * B / per_step_s
-    bits_per_fix = float(net_np.m) * d * d * total_sweeps / B  # m d^2 bits per plain sweep
-    value = fix_per_s
+    value = world * B / per_step_s
+
+    # plain GPU RAC on the same items (only where the step is a batch)
+    plain = None
+    if B > 1:
+        pin, pout = W.din.data_ptr(), W.dout.data_ptr()
+        pit = torch.empty(B, dtype=torch.int32, device=dev)
+        pst = torch.empty(B, dtype=torch.int32, device=dev)
+        W.plain_step(stream, pin, pout, pit.data_ptr(), pst.data_ptr())
+        torch.cuda.synchronize()
+        if not (np.array_equal(pit.cpu().numpy(), its) and np.array_equal(pst.cpu().numpy(), statuses)):
+            raise SystemExit("plain per-item launches disagree with the batched launch")
+        ps = max(1, min(3, K))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_plain = 0.0
+        for _ in range(ps):
+            flush.zero_()
+            e0.record(stream)
+            W.plain_step(stream, pin, pout, pit.data_ptr(), pst.data_ptr())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_plain += e0.elapsed_time(e1) / 1000.0
+        t_plain = max_over_ranks(t_plain) / ps
+        plain = {"value": world * B / t_plain, "unit": "fixpoints/s", "steps": ps,
+                 "how": "one single-state rac_enforce launch per item (kernel (a)), same items",
+                 "speedup_of_this_form": (world * B / per_step_s) / (world * B / t_plain)}
 
     # end to end through the host entry point (copies inside the timed region)
     e2e = None
-    if not args.no_e2e:
-        host_in = torch.from_numpy(doms.reshape(-1).view(np.int32).copy()).pin_memory()
+    if not args.no_e2e and len(W.nets) == 1:
+        host_in = torch.from_numpy(np.ascontiguousarray(W.flat).view(np.int32).copy()).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
         hit = torch.empty(B, dtype=torch.int32).pin_memory()
         hst = torch.empty(B, dtype=torch.int32).pin_memory()
         L = rac.lib()
         sh = stream.cuda_stream
+        net = W.nets[0]
 
         def host_step():
             rc = L.rac_enforce_host(net.handle, B, host_in.data_ptr(), host_out.data_ptr(),
@@ -372,43 +499,65 @@ def run_ours(args):
         for _ in range(Ke):
             host_step()
         el = max_over_ranks(time.perf_counter() - t0)
-        if not np.array_equal(host_out.numpy().view(np.uint32), dout.cpu().numpy().view(np.uint32)):
+        if not np.array_equal(host_out.numpy().view(np.uint32), W.dout.cpu().numpy().view(np.uint32)):
             raise SystemExit("host entry point disagrees with the device entry point")
         e2e = {"value": world * B * Ke / el, "unit": "fixpoints/s",
-               "h2d_bytes_per_step": int(B * n * 4), "d2h_bytes_per_step": int(B * n * 4 + B * 8),
+               "h2d_bytes_per_step": int(W.flat.size * 4), "d2h_bytes_per_step": int(W.flat.size * 4 + B * 8),
+               "steps": Ke}
+    elif not args.no_e2e:
+        # batches: pinned host states copied in, the plan launch, results copied out
+        host_in = torch.from_numpy(np.ascontiguousarray(W.flat).view(np.int32).copy()).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        hit = torch.empty(B, dtype=torch.int32).pin_memory()
+        Ke = max(3, min(K, 20))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            W.din.copy_(host_in, non_blocking=True)
+            W.step(args.flags, stream)
+            host_out.copy_(W.dout, non_blocking=True)
+            hit.copy_(W.it, non_blocking=True)
+            torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * B * Ke / el, "unit": "fixpoints/s",
+               "h2d_bytes_per_step": int(W.flat.size * 4), "d2h_bytes_per_step": int(W.flat.size * 4 + B * 4),
                "steps": Ke}
 
     peaks = measured_peaks()
     hbm_peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6400.0
-    # a launch reads each relation once per sweep, for all its states at once
-    alg_bytes_per_launch = float(net_np.m) * d * d / 8.0 * sweeps
+    alg_bytes_per_launch = W.alg_bytes(its)
     achieved = alg_bytes_per_launch / per_step_s / 1e9
     traffic = traffic_from_profiles(args.workload)
     clocks = clk.summary()
+    kernel = "rac_batch_kernel" if W.plan is not None else "rac_bits_kernel"
 
     line = {"metric": METRIC, "value": value, "unit": "fixpoints/s", "n_gpus": world,
             "steps": K, "warmup": max(3, args.warmup), "ms_per_step": per_step_s * 1000.0,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic (seeded random binary CSP, generated in-process)",
-            "config": config_of(args.workload, spec, net_np, True),
-            "relation_bits_per_s": world * bits_per_fix * B / per_step_s,
+            "config": W.cfg,
+            "relation_bits_per_s": world * W.plain_bits(its) / per_step_s,
             "sweeps_per_fixpoint": total_sweeps / B,
             "status_counts": {str(k): int(v) for k, v in zip(*np.unique(statuses, return_counts=True))},
             "wall_s_timed_region": wall,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": traffic,
                          "peak_source": "measured" if peaks else "fallback",
-                         "kernel": "rac_bits_kernel",
-                         "alg_bytes_per_launch": alg_bytes_per_launch},
+                         "kernel": kernel, "alg_bytes_per_launch": alg_bytes_per_launch},
             "clocks": clocks,
             "gpu_launches": K,
             "e2e": e2e}
+    if plain is not None:
+        line["plain_gpu_rac"] = plain
     if rank == 0 and not args.no_cpu_baseline:
-        cb, _ = cpu_baseline(spec, net_np, doms)
+        cb, _ = cpu_baseline(W)
         line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
-    net.close()
+    if W.plan is not None:
+        W.plan.close()
+    for n in W.nets:
+        n.close()
     if pg:
         pg.destroy_process_group()
 
