@@ -82,6 +82,10 @@ typedef int32_t rac_status;
                                     domain changed in sweep k-1.  The result,
                                     every sweep's removals and the sweep count
                                     are identical to the plain recurrence. */
+#define RAC_VERIFY_FULL 0x4u      /* rac_enforce_learned only: the verification sweep
+                                    after a gated sweep that removed nothing
+                                    evaluates EVERY slab, instead of the slabs
+                                    left pending (see rac_enforce_learned). */
 #define RAC_KERNEL_TENSOR 0x10u  /* evaluate the support counts with the tensor-core
                                     kernel (tcgen05 FP8 GEMMs, FP32 accumulation in
                                     tensor memory) instead of the bit-packed kernel:
@@ -264,6 +268,139 @@ RAC_API rac_status rac_enforce_host(const rac_network *net, int32_t n_states, co
 RAC_API rac_status rac_enforce_noalloc(const rac_network *net, const uint32_t *dom_in,
                                        uint32_t *dom_out, int32_t *iterations, int32_t *status,
                                        int32_t max_sweeps, uint32_t flags, rac_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned active-block gating.
+ *
+ * The paper gates sweeps exactly with Proposition 2 (Sec. 3): sweep k >= 2
+ * only needs the constraints touching a variable whose domain changed in
+ * sweep k-1.  On dense networks that set is nearly every relation slab, yet
+ * most of those evaluations remove nothing.  A small learned predictor
+ * scores each (slab, state) candidate before it is evaluated and skips the
+ * unpromising ones; a skipped pair stays PENDING until a sweep evaluates it.
+ * Exactness is kept by the recurrence itself:
+ *  - every removal is made from a superset of D_ac, hence sound (Lemma 1);
+ *  - a gated sweep that removes nothing is followed by a verification sweep
+ *    that evaluates, without the predictor, every pending pair and every
+ *    Proposition-2 candidate.  A pair that is neither has been evaluated
+ *    since the last change of any of its variables and removed nothing
+ *    then, so it would remove nothing now (Proposition 2's argument): a
+ *    sweep that removes nothing and leaves no pair pending is equivalent to
+ *    a full sweep that removes nothing.  Only such a sweep ends a state; its
+ *    domain is arc consistent and contains D_ac, i.e. it is D_ac.
+ *  - with RAC_VERIFY_FULL the verification sweep evaluates every slab
+ *    literally, and only a full sweep that removes nothing ends a state.
+ * So the result and status are those of rac_enforce; the sweep count is the
+ * number of sweeps this gated recurrence executed (it may differ).
+ *
+ * The predictor is an MLP 8 -> 64 -> 64 -> 1 (ReLU hidden layers, a logit
+ * out) with BF16 weights and FP32 accumulation.  Its 8 features of a (slab,
+ * state) pair before sweep k, all in [0, 1]:
+ *   f0 min(k, 16) / 16; f1 slab rows (variables x) changed in sweep k-1 /
+ *   slab rows; f2 column-block variables y changed in sweep k-1 / 32; f3 the
+ *   slab's disallowed fraction of relation bits (tightness); f4 constraints
+ *   in the slab / (slab rows * 32); f5 min over the column variables of
+ *   |D_{k-1}(y)| / d; f6 mean of the same; f7 min over the slab's row
+ *   variables of |D_{k-1}(x)| / d.
+ * Parameters (RAC_PREDICTOR_PARAMS floats, in this order): W1[64][8], b1[64],
+ * W2[64][64], b2[64], w3[64], b3.  Forward: x~ = bf16(x), h1 = bf16(relu(W1
+ * x~ + b1)), h2 = relu(W2 h1 + b2), z = w3 . h2 + b3.
+ * ------------------------------------------------------------------------- */
+typedef struct rac_predictor rac_predictor;
+#define RAC_PREDICTOR_FEATURES 8
+#define RAC_PREDICTOR_PARAMS 4801
+
+/* rac_predictor_num_params -- RAC_PREDICTOR_PARAMS. */
+RAC_API int32_t rac_predictor_num_params(void);
+
+/* rac_predictor_create -- a predictor on the current device, He-initialised
+ * from `seed` (biases zero).  Synchronises with the device.
+ * Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA. */
+RAC_API rac_status rac_predictor_create(uint64_t seed, rac_predictor **out);
+
+/* rac_predictor_destroy -- NULL-safe; no launch using it may still run. */
+RAC_API void rac_predictor_destroy(rac_predictor *p);
+
+/* rac_predictor_set_weights / rac_predictor_get_weights -- HOST arrays of
+ * RAC_PREDICTOR_PARAMS floats.  set: replaces the FP32 master weights (and
+ * their BF16 copy), resets the optimiser state.  get: the FP32 master
+ * weights, or with bf16 != 0 the BF16 copy that inference uses, widened.
+ * Both synchronise with the device.  Errors: RAC_EINVAL, RAC_ECUDA. */
+RAC_API rac_status rac_predictor_set_weights(rac_predictor *p, const float *params);
+RAC_API rac_status rac_predictor_get_weights(const rac_predictor *p, float *params, int32_t bf16);
+
+/* rac_predictor_gradient -- mean loss and its gradient over n samples.
+ *  x      DEVICE, n x 8 floats (features); y DEVICE, n floats (labels 0/1).
+ *  Loss per sample: w(y) (softplus(z) - y z), w(1) = pos_weight, w(0) = 1.
+ *  The gradient is taken at the BF16 weights, with the BF16 rounding of x and
+ *  h1 passed straight through.
+ *  grad   HOST, RAC_PREDICTOR_PARAMS floats (may be NULL); loss HOST (may be
+ *  NULL).  Synchronises.  Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA. */
+RAC_API rac_status rac_predictor_gradient(rac_predictor *p, const float *x, const float *y,
+                                          int64_t n, float pos_weight, float *grad, float *loss);
+
+/* rac_predictor_train -- `steps` Adam steps (beta1 0.9, beta2 0.999, eps
+ * 1e-8, learning rate lr) on minibatches of `batch` samples drawn uniformly
+ * with replacement from the n samples (x, y as above, DEVICE), the draws
+ * fixed by `seed`.  loss (HOST, may be NULL) receives the last minibatch's
+ * loss.  Synchronises.  Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA. */
+RAC_API rac_status rac_predictor_train(rac_predictor *p, const float *x, const float *y, int64_t n,
+                                       int32_t steps, int32_t batch, float lr, float pos_weight,
+                                       uint64_t seed, float *loss);
+
+/* rac_predictor_predict -- logits of n samples (x DEVICE n x 8, logits
+ * DEVICE n).  tensor_cores != 0 runs the warp-wide tensor-core routine the
+ * sweep kernel uses, 0 a scalar one.  Synchronises.
+ * Errors: RAC_EINVAL, RAC_ECUDA. */
+RAC_API rac_status rac_predictor_predict(const rac_predictor *p, const float *x, int64_t n,
+                                         float *logits, int32_t tensor_cores);
+
+/* Optional record of the gating decisions of rac_enforce_learned: one record
+ * per Proposition-2 candidate (slab, state) of every sweep k >= 2 (with a
+ * predictor, candidates of verification sweeps too; pending pairs that are
+ * no candidate get no record).  Records are appended in no particular
+ * order. */
+typedef struct rac_trace {
+  float *features;   /* DEVICE, capacity x 8: the features above */
+  float *label;      /* DEVICE, capacity: 1 the evaluation removed a value,
+                        0 it did not, -1 the pair was skipped */
+  float *logit;      /* DEVICE, capacity (may be NULL): the predictor's logit,
+                        NaN without a predictor */
+  int32_t *where;    /* DEVICE, capacity x 4: sweep k (| 1 << 30 if the state
+                        was in its gated phase), state index, tile I | J << 16
+                        (rows of variables 32 I.., columns 32 J..), rows
+                        row0 | nrows << 8 (slab rows inside the tile) */
+  int64_t capacity;  /* records that fit (0: count only) */
+  unsigned long long *count;      /* DEVICE (may be NULL): records offered, may
+                                     exceed capacity; set to 0 by the call */
+  unsigned long long *evaluated;  /* DEVICE (may be NULL): (slab, state)
+                                     evaluations executed in all sweeps; set to
+                                     0 by the call */
+} rac_trace;
+
+/*
+ * rac_enforce_learned -- rac_enforce for n_states states (state s at word
+ * s * n_vars of dom_in / dom_out, DEVICE), with learned gating.
+ *
+ *  pred       the predictor, or NULL: then every sweep k >= 2 evaluates
+ *             exactly the Proposition-2 candidates (as RAC_INCREMENTAL), the
+ *             mode used to record training traces.
+ *  threshold  a candidate of a gated sweep is evaluated iff its logit >
+ *             threshold.
+ *  sweeps     DEVICE, n_states int32: sweeps executed.
+ *  status     DEVICE, n_states int32: as rac_enforce (identical values).
+ *  max_sweeps, stream: as rac_enforce.  flags: RAC_STOP_ON_WIPEOUT (the
+ *             returned domain is then the state at the first sweep that
+ *             emptied a domain -- a sound superset of D_ac, not unique),
+ *             RAC_VERIFY_FULL (see above).
+ *  trace      optional (NULL: none).
+ * Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA.
+ */
+RAC_API rac_status rac_enforce_learned(const rac_network *net, int32_t n_states,
+                                       const uint32_t *dom_in, uint32_t *dom_out, int32_t *sweeps,
+                                       int32_t *status, int32_t max_sweeps, uint32_t flags,
+                                       const rac_predictor *pred, float threshold,
+                                       const rac_trace *trace, rac_stream_t stream);
 
 /*
  * rac_network_info -- describe a network: writes up to n_info int64 values

@@ -23,6 +23,7 @@ EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBARRIER, ENOTSUP = -1, -2, -3, -4, -5, -6
 LAYOUT_BITS = 0x1
 STOP_ON_WIPEOUT = 0x1
 INCREMENTAL = 0x2
+VERIFY_FULL = 0x4  # rac_enforce_learned: literal full verification sweep (see include/rac.h)
 KERNEL_TENSOR = 0x10  # tcgen05 tensor-core kernel (see include/rac.h)
 TEST_WITHHOLD_ARRIVAL = 0x80000000  # failure-detection test hook (see include/rac.h)
 
@@ -31,8 +32,22 @@ STATUS_NAMES = {OK: "ok", WIPEOUT: "wipeout", EINVAL: "einval", ENOMEM: "enomem"
 
 ABI_FUNCTIONS = ("rac_create_network", "rac_destroy", "rac_enforce", "rac_enforce_batch",
                  "rac_enforce_host", "rac_enforce_noalloc", "rac_network_info", "rac_last_error",
-                 "rac_plan_create", "rac_plan_enforce", "rac_plan_destroy", "rac_assign_enforce")
+                 "rac_plan_create", "rac_plan_enforce", "rac_plan_destroy", "rac_assign_enforce",
+                 "rac_predictor_num_params", "rac_predictor_create", "rac_predictor_destroy",
+                 "rac_predictor_set_weights", "rac_predictor_get_weights",
+                 "rac_predictor_gradient", "rac_predictor_train", "rac_predictor_predict",
+                 "rac_enforce_learned")
 NOALLOC_MAX_VARS = 65536
+PREDICTOR_FEATURES = 8
+PREDICTOR_PARAMS = 4801
+
+
+class RacTrace(ctypes.Structure):
+    """struct rac_trace of include/rac.h (device pointers)."""
+    _fields_ = [("features", ctypes.c_void_p), ("label", ctypes.c_void_p),
+                ("logit", ctypes.c_void_p), ("where", ctypes.c_void_p),
+                ("capacity", ctypes.c_int64), ("count", ctypes.c_void_p),
+                ("evaluated", ctypes.c_void_p)]
 
 
 class RacError(RuntimeError):
@@ -76,6 +91,26 @@ def lib():
         L.rac_network_info.argtypes = [vp, ctypes.POINTER(i64), i32]
         L.rac_last_error.restype = ctypes.c_char_p
         L.rac_last_error.argtypes = []
+        f32, u64 = ctypes.c_float, ctypes.c_uint64
+        L.rac_predictor_num_params.restype = i32
+        L.rac_predictor_num_params.argtypes = []
+        L.rac_predictor_create.restype = i32
+        L.rac_predictor_create.argtypes = [u64, ctypes.POINTER(vp)]
+        L.rac_predictor_destroy.restype = None
+        L.rac_predictor_destroy.argtypes = [vp]
+        L.rac_predictor_set_weights.restype = i32
+        L.rac_predictor_set_weights.argtypes = [vp, vp]
+        L.rac_predictor_get_weights.restype = i32
+        L.rac_predictor_get_weights.argtypes = [vp, vp, i32]
+        L.rac_predictor_gradient.restype = i32
+        L.rac_predictor_gradient.argtypes = [vp, vp, vp, i64, f32, vp, vp]
+        L.rac_predictor_train.restype = i32
+        L.rac_predictor_train.argtypes = [vp, vp, vp, i64, i32, i32, f32, f32, u64, vp]
+        L.rac_predictor_predict.restype = i32
+        L.rac_predictor_predict.argtypes = [vp, vp, i64, vp, i32]
+        L.rac_enforce_learned.restype = i32
+        L.rac_enforce_learned.argtypes = [vp, i32, vp, vp, vp, vp, i32, u32, vp, f32,
+                                          ctypes.POINTER(RacTrace), vp]
         _lib = L
     return _lib
 
@@ -259,3 +294,117 @@ def enforce_host(net, dom_in, max_sweeps=0, flags=0, stream=None):
     if single:
         return out[0], int(it[0]), int(st[0])
     return out, it, st
+
+
+class Predictor:
+    """The active-block predictor (rac_predictor_*): an MLP 8 -> 64 -> 64 -> 1
+    with BF16 weights, trained and evaluated by the library's kernels."""
+
+    def __init__(self, seed=0):
+        h = ctypes.c_void_p()
+        _check(lib().rac_predictor_create(int(seed), ctypes.byref(h)), "rac_predictor_create")
+        self.handle = h.value
+
+    @staticmethod
+    def num_params():
+        return int(lib().rac_predictor_num_params())
+
+    def set_weights(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        if params.shape[0] != PREDICTOR_PARAMS:
+            raise RacError(EINVAL, "expected %d parameters" % PREDICTOR_PARAMS)
+        _check(lib().rac_predictor_set_weights(self.handle, params.ctypes.data),
+               "rac_predictor_set_weights")
+
+    def get_weights(self, bf16=False):
+        out = np.empty(PREDICTOR_PARAMS, dtype=np.float32)
+        _check(lib().rac_predictor_get_weights(self.handle, out.ctypes.data, int(bool(bf16))),
+               "rac_predictor_get_weights")
+        return out
+
+    def gradient(self, x, y, pos_weight=1.0):
+        """Mean loss and gradient over the samples (x: (N, 8) float32 CUDA
+        tensor, y: (N,) float32 CUDA tensor).  Returns (grad, loss)."""
+        grad = np.empty(PREDICTOR_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(lib().rac_predictor_gradient(self.handle, _ptr(x), _ptr(y), int(y.numel()),
+                                            float(pos_weight), grad.ctypes.data,
+                                            ctypes.addressof(loss)),
+               "rac_predictor_gradient")
+        return grad, float(loss.value)
+
+    def train(self, x, y, steps, batch=4096, lr=1e-3, pos_weight=1.0, seed=0):
+        """Adam steps on minibatches drawn from (x, y); returns the last
+        minibatch loss."""
+        loss = ctypes.c_float()
+        _check(lib().rac_predictor_train(self.handle, _ptr(x), _ptr(y), int(y.numel()), int(steps),
+                                         int(batch), float(lr), float(pos_weight), int(seed),
+                                         ctypes.addressof(loss)),
+               "rac_predictor_train")
+        return float(loss.value)
+
+    def predict(self, x, logits, tensor_cores=True):
+        _check(lib().rac_predictor_predict(self.handle, _ptr(x), int(x.shape[0]), _ptr(logits),
+                                           int(bool(tensor_cores))),
+               "rac_predictor_predict")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rac_predictor_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Trace:
+    """Device buffers for the records of rac_enforce_learned (struct
+    rac_trace), held as torch tensors on the current device."""
+
+    def __init__(self, capacity):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.capacity = int(capacity)
+        c = max(1, self.capacity)
+        self.features = torch.zeros((c, PREDICTOR_FEATURES), dtype=torch.float32, device=dev)
+        self.label = torch.zeros(c, dtype=torch.float32, device=dev)
+        self.logit = torch.zeros(c, dtype=torch.float32, device=dev)
+        self.where = torch.zeros((c, 4), dtype=torch.int32, device=dev)
+        self.counters = torch.zeros(2, dtype=torch.int64, device=dev)  # count, evaluated
+
+    def struct(self):
+        return RacTrace(self.features.data_ptr(), self.label.data_ptr(), self.logit.data_ptr(),
+                        self.where.data_ptr(), self.capacity, self.counters.data_ptr(),
+                        self.counters.data_ptr() + 8)
+
+    def count(self):
+        return int(self.counters[0].item())
+
+    def evaluated(self):
+        return int(self.counters[1].item())
+
+    def records(self):
+        """Host copies of the stored records: dict of numpy arrays."""
+        k = min(self.count(), self.capacity)
+        return {"features": self.features[:k].cpu().numpy(), "label": self.label[:k].cpu().numpy(),
+                "logit": self.logit[:k].cpu().numpy(), "where": self.where[:k].cpu().numpy()}
+
+
+def enforce_learned(net, dom_in, dom_out, sweeps, status, predictor=None, threshold=0.0,
+                    trace=None, max_sweeps=0, flags=0, n_states=None, stream=None):
+    """rac_enforce_learned: states s at word s * n of dom_in / dom_out, with
+    learned gating (predictor) or, with predictor=None, Proposition-2 sweeps
+    (the mode that records training traces).  Asynchronous on `stream`."""
+    if n_states is None:
+        n_states = dom_in.numel() // net.n
+    tr = trace.struct() if trace is not None else None
+    _check(lib().rac_enforce_learned(net.handle, int(n_states), _ptr(dom_in), _ptr(dom_out),
+                                     _ptr(sweeps), _ptr(status), int(max_sweeps), int(flags),
+                                     predictor.handle if predictor is not None else None,
+                                     float(threshold),
+                                     ctypes.byref(tr) if tr is not None else None,
+                                     _stream(stream)),
+           "rac_enforce_learned")

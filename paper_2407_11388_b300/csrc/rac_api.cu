@@ -34,6 +34,7 @@ NetDev net_dev(const rac_network *net) {
   N.n_slabs = int32_t(net->n_slabs);
   N.rel = static_cast<const uint4 *>(net->d_rel);
   N.slabs = net->d_slabs;
+  N.slab_feat = net->d_slab_feat;
   return N;
 }
 
@@ -46,6 +47,9 @@ void free_workspace(Workspace *w) {
   cudaFree(w->res_idx);
   cudaFree(w->host_dom);
   cudaFree(w->host_res);
+  cudaFree(w->pend);
+  cudaFree(w->pend_slab);
+  cudaFree(w->pcount);
   delete w;
 }
 
@@ -235,6 +239,7 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
 
   // slabs: (I, J, i / rows), each a header followed by its relations
   std::vector<SlabDesc> slabs;
+  std::vector<float2> slab_feat;  // tightness, density
   std::vector<uint32_t> relw;
   const size_t hdr = size_t(2) * rows;  // pm[rows] + roff[rows], a multiple of 4 words
   try {
@@ -286,6 +291,16 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
           row_base[(size_t(a / 4) * cnt + rank) * 4 + (a % 4)] = w;
         }
       }
+      // the slab's tightness (disallowed fraction of its d x d relation bits)
+      // and density (constraints / (rows x 32))
+      uint64_t allowed = 0;
+      for (size_t t = i; t < j; ++t) {
+        const int64_t c = order[t].second;
+        for (int a = 0; a < d; ++a) allowed += uint64_t(__builtin_popcount(rel_bits[c * d + a]));
+      }
+      slab_feat.push_back(make_float2(
+          float(1.0 - double(allowed) / (double(count) * double(d) * double(d))),
+          float(double(count) / (double(rows) * 32.0))));
       SlabDesc sd;
       sd.rel_off16 = uint32_t(base / 4);
       sd.nbytes = uint32_t((hdr + count * size_t(dp)) * 4);
@@ -337,6 +352,9 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
   if ((e = upload(reinterpret_cast<void **>(&net->d_slabs), slabs.data(),
                   slabs.size() * sizeof(SlabDesc))) != cudaSuccess)
     return fail(e, "upload of the slab table");
+  if ((e = upload(reinterpret_cast<void **>(&net->d_slab_feat), slab_feat.data(),
+                  slab_feat.size() * sizeof(float2))) != cudaSuccess)
+    return fail(e, "upload of the slab features");
   *out = net;
   return RAC_OK;
 }
@@ -347,6 +365,7 @@ void rac_destroy(rac_network *net) {
   net->ws.clear();
   cudaFree(net->d_rel);
   cudaFree(net->d_slabs);
+  cudaFree(net->d_slab_feat);
   delete net;
 }
 
@@ -572,6 +591,94 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess && rc == RAC_OK) rc = cuda_fail(e, "cudaStreamSynchronize");
   return rc;
+}
+
+rac_status rac_enforce_learned(const rac_network *net, int32_t n_states, const uint32_t *dom_in,
+                               uint32_t *dom_out, int32_t *sweeps, int32_t *status,
+                               int32_t max_sweeps, uint32_t flags, const rac_predictor *pred,
+                               float threshold, const rac_trace *trace, rac_stream_t stream) {
+  set_error("");
+  if (!net || n_states < 0) {
+    set_error("NULL network or negative state count");
+    return RAC_EINVAL;
+  }
+  if (n_states > 0 && (!dom_in || !dom_out || !sweeps || !status)) {
+    set_error("NULL argument");
+    return RAC_EINVAL;
+  }
+  if (flags & ~(RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL | RAC_VERIFY_FULL |
+                RAC_TEST_WITHHOLD_ARRIVAL)) {
+    set_error("unknown flag (rac_enforce_learned takes RAC_STOP_ON_WIPEOUT, RAC_VERIFY_FULL)");
+    return RAC_EINVAL;
+  }
+  if (trace && (trace->capacity < 0 ||
+                (trace->capacity > 0 && (!trace->features || !trace->label || !trace->where ||
+                                         !trace->count)))) {
+    set_error("trace: negative capacity, or records without features / label / where / count");
+    return RAC_EINVAL;
+  }
+  if (!check_device(net)) return RAC_EINVAL;
+  if (pred && predictor_device(pred) != net->device) {
+    set_error("the predictor lives on another device than the network");
+    return RAC_EINVAL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (trace) {
+    cudaError_t e = cudaSuccess;
+    if (trace->count) e = cudaMemsetAsync(trace->count, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess && trace->evaluated)
+      e = cudaMemsetAsync(trace->evaluated, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the trace counters");
+  }
+  for (int32_t base = 0; base < n_states; base += kMaxStatesPerLaunch) {
+    const int cnt = std::min<int32_t>(kMaxStatesPerLaunch, n_states - base);
+    rac_status rc = RAC_OK;
+    Workspace *w = get_workspace(net, s, cnt, 0, &rc);
+    if (!w) return rc;
+    if (pred && !(flags & RAC_VERIFY_FULL) && !w->pend) {
+      // the launch clears them in its first sweep: no initialisation needed
+      const size_t slabs = size_t(std::max<int64_t>(net->n_slabs, 1));
+      if (cudaMalloc(&w->pend, slabs * size_t(w->cap_states)) != cudaSuccess ||
+          cudaMalloc(&w->pend_slab, slabs * sizeof(int32_t)) != cudaSuccess ||
+          cudaMalloc(&w->pcount, size_t(w->cap_states) * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation of the pending-pair arrays failed");
+        return RAC_ENOMEM;
+      }
+    }
+    // Proposition-2 bookkeeping (changed-variable union) is what both the
+    // gated sweeps and the trace mode start from
+    LaunchParams P = base_params(net, w, cnt, max_sweeps, flags | RAC_INCREMENTAL);
+    // a gated sweep that removes nothing is followed by a full sweep, so at
+    // most twice the |D| + 1 sweeps of Proposition 1 (plus one)
+    const int64_t bound = 2 * (int64_t(net->n) * net->d + 2);
+    P.sweep_bound = int32_t(std::min<int64_t>(bound, 0xFFFFF0));
+    P.contiguous = 1;
+    P.dom_in = dom_in + size_t(base) * net->n;
+    P.dom_out = dom_out + size_t(base) * net->n;
+    P.iterations = sweeps + base;
+    P.status = status + base;
+    P.mlp = pred ? predictor_weights(pred) : nullptr;
+    P.mlp_thr = threshold;
+    if (pred && !(flags & RAC_VERIFY_FULL)) {
+      P.pend = w->pend;
+      P.pend_slab = w->pend_slab;
+      P.pcount = w->pcount;
+    }
+    if (trace) {
+      P.tr_x = trace->features;
+      P.tr_y = trace->label;
+      P.tr_z = trace->logit;
+      P.tr_w = trace->where;
+      P.tr_cap = trace->capacity;
+      P.tr_count = trace->count;
+      P.tr_evals = trace->evaluated;
+      P.tr_state_base = base;
+    }
+    rc = launch_bits(P, s);
+    if (rc != RAC_OK) return rc;
+  }
+  return RAC_OK;
 }
 
 }  // extern "C"

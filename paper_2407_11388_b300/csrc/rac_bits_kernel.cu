@@ -32,6 +32,7 @@
 
 #include "rac_device.cuh"
 #include "rac_internal.h"
+#include "rac_mlp.cuh"
 
 namespace rac {
 namespace {
@@ -58,7 +59,9 @@ struct Smem {
   uint32_t failed;      // a wait of this CTA gave up, or another CTA reported one
   uint32_t cta_any;
   uint32_t cta_wipe;
+  uint32_t load_all;    // learned gating: some running state is in its full phase
   uint32_t red[2][kConsumerWarps][32];
+  uint32_t remw[2][kConsumerWarps];  // per-warp "removed a value" of a state group
   uint32_t st_info[kMaxStatesPerLaunch];  // see kInfo* below
   uint8_t any_loc[kMaxStatesPerLaunch];
   uint8_t wipe_loc[kMaxStatesPerLaunch];
@@ -70,10 +73,11 @@ static_assert(size_t(kStages) * kStageBytes + sizeof(Smem) <= 232448,
               "shared memory of the bit-packed kernel exceeds 227 KB");
 // st_info: bits 0..23 sweep at which the state finished (0 = running),
 // bit 24 result in buffer B, bit 25 some domain emptied so far,
-// bits 27..31 status code + 8.
+// bit 26 gated phase (learned gating), bits 27..31 status code + 8.
 constexpr uint32_t kInfoSweepMask = 0xFFFFFFu;
 constexpr uint32_t kInfoResB = 1u << 24;
 constexpr uint32_t kInfoWiped = 1u << 25;
+constexpr uint32_t kInfoGated = 1u << 26;  // learned gating: the state is in its gated phase
 __device__ __forceinline__ uint32_t info_status_bits(int st) { return uint32_t(st + 8) << 27; }
 __device__ __forceinline__ int info_status(uint32_t v) { return int((v >> 27) & 31u) - 8; }
 
@@ -180,7 +184,204 @@ __device__ void grid_barrier(Smem &S, const LaunchParams &P, int slot) {
   __syncthreads();
 }
 
+// Evaluate one state on one slab: the support step of Eq. 1 restricted to the
+// slab's constraints, with its removals applied to D_k.  With kLabel, the
+// state group's first warp (sub == 0) gets back whether the evaluation
+// removed a value.
+template <int Q, bool kLabel>
+__device__ __forceinline__ bool eval_state(Smem &S, const LaunchParams &P, int s, int k,
+                                           int slot_w, const uint32_t *hdr, const uint4 *rel,
+                                           uint32_t I, uint32_t row0, uint32_t nrows, int y,
+                                           bool y_ok, bool cached, int warp, int lane, int cg,
+                                           int g, int sub, int wps, uint32_t &red_iter) {
+  const NetDev &N = P.net;
+  const int n = N.n;
+  const uint32_t dfull = N.d >= 32 ? kFull : ((1u << N.d) - 1u);
+  const StateView V = state_view(P, s, k);
+  const uint32_t *Dc = cached ? S.dom + s * n : V.C;
+  uint32_t Dy = y_ok ? (cached ? Dc[y] : ld_dom(Dc + y)) : 0u;
+  if (k == 1 && !cached) Dy = input_word(P, y, Dy);
+  uint32_t racc = kFull;
+  bool rem = false;
+  for (int r = sub; r < int(nrows); r += wps) {
+    const uint32_t pm = hdr[r];
+    if (pm == 0u) continue;
+    const int x = int(I) * 32 + int(row0) + r;
+    uint32_t Dx = cached ? Dc[x] : ld_dom(Dc + x);
+    if (k == 1 && !cached) Dx = input_word(P, x, Dx);
+    uint32_t fwd = kFull, rev = kFull;
+    if ((pm >> lane) & 1u) {
+      // this lane's relation: rank t in the row, chunk c at c * cnt + t
+      const uint32_t t = __popc(pm & lanemask_lt());
+      const uint4 *mine = rel + hdr[nrows + r] * Q + t;
+      if (Dx == dfull)
+        support_relation<Q, true>(mine, __popc(pm), Dx, Dy, fwd, rev);
+      else
+        support_relation<Q, false>(mine, __popc(pm), Dx, Dy, fwd, rev);
+    }
+    const uint32_t keep_x = __reduce_and_sync(kFull, fwd) & Dx;  // warp-uniform
+    if (keep_x != Dx) {
+      if (lane == 0) remove_values(S, P, s, slot_w, V.T, uint32_t(x), keep_x);
+      rem = true;
+    }
+    racc &= rev;
+  }
+  if (wps > 1) {
+    const int buf = red_iter & 1;
+    S.red[buf][warp][lane] = racc;
+    if (kLabel && lane == 0) S.remw[buf][warp] = rem ? 1u : 0u;
+    named_bar(state_group_bar(cg, g), wps * 32);
+    if (sub == 0) {
+      for (int j = 1; j < wps; ++j) {
+        racc &= S.red[buf][warp + j][lane];
+        if (kLabel) rem = rem || S.remw[buf][warp + j] != 0u;
+      }
+    }
+    ++red_iter;
+  }
+  bool rem_y = false;
+  if (sub == 0 && y_ok) {
+    const uint32_t keep_y = racc & Dy;
+    if (keep_y != Dy) {
+      remove_values(S, P, s, slot_w, V.T, uint32_t(y), keep_y);
+      rem_y = true;
+    }
+  }
+  if (kLabel) rem = rem || __any_sync(kFull, rem_y);
+  return rem;
+}
+
+// Sweep k >= 2 of rac_enforce_learned: the states of this warp's state group
+// are taken 32 at a time (lane i <-> state c0 + groups * i).  Per chunk:
+// the Proposition-2 test (a variable of the slab's rows or columns changed in
+// sweep k-1), the predictor's features and -- for states in the gated phase
+// -- its logit (one warp-wide tensor-core MLP for the 32 states), then the
+// evaluations the decision keeps, with optional trace records.
 template <int Q>
+__device__ void consume_slab_gated(Smem &S, const LaunchParams &P, const uint32_t *hdr,
+                                   const uint4 *rel, const StageInfo &si, int k, int slot_r,
+                                   int slot_w, int warp, int lane, int cg, int g, int sub,
+                                   int wps, int groups, uint32_t &red_iter) {
+  const NetDev &N = P.net;
+  const int n = N.n, B = P.n_states;
+  const uint32_t I = si.ij & 0xFFFFu, J = si.ij >> 16;
+  const uint32_t row0 = si.rows & 0xFFu, nrows = si.rows >> 8;
+  const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
+  const int y = int(J) * 32 + lane;
+  const bool y_ok = y < n;
+  const int x_l = int(I) * 32 + int(row0) + lane;
+  const bool x_ok = lane < int(nrows) && x_l < n;
+  const bool cached = S.dom_cached != 0;
+  const float2 sf = N.slab_feat[si.sl];
+  const float inv_d = 1.0f / float(N.d);
+  const float inv_cols = 1.0f / float(min(32, n - int(J) * 32) * N.d);
+  const bool learned = P.mlp != nullptr;
+  const bool recording = P.tr_count != nullptr;
+  for (int c0 = g; c0 < B; c0 += 32 * groups) {
+    const int s_l = c0 + groups * lane;
+    const uint32_t info = s_l < B ? S.st_info[s_l] : 1u;  // lanes past the end look finished
+    const bool valid = (info & kInfoSweepMask) == 0u;
+    const bool gated = learned && (info & kInfoGated);
+    uint32_t cI = 0u, cJ = 0u;
+    if (valid) {
+      const uint32_t *ch = P.chg + (int64_t(slot_r) * P.flag_stride + s_l) * N.nb;
+      cJ = ld_dom(ch + J);
+      cI = ld_dom(ch + I) & rowmask;
+    }
+    const bool p2 = (cI | cJ) != 0u;
+    const bool need = valid && p2 && (gated || recording);
+    const uint32_t need_mask = __ballot_sync(kFull, need);
+    float f[kMlpIn];
+    f[0] = float(min(k, 16)) * (1.0f / 16.0f);
+    f[1] = float(__popc(cI)) / float(nrows);
+    f[2] = float(__popc(cJ)) * (1.0f / 32.0f);
+    f[3] = sf.x;
+    f[4] = sf.y;
+    f[5] = f[6] = f[7] = 0.0f;
+    // domain sizes of D_{k-1}: the warp reads one state's column words
+    // (lane = column) and row words (lane = row) at a time
+    for (uint32_t m = need_mask; m; m &= m - 1u) {
+      const int i = __ffs(m) - 1;
+      const int s = c0 + groups * i;
+      const uint32_t *Dc = cached ? S.dom + s * n : state_view(P, s, k).C;
+      const uint32_t dy = y_ok ? uint32_t(__popc(cached ? Dc[y] : ld_dom(Dc + y))) : uint32_t(N.d);
+      const uint32_t dx = x_ok ? uint32_t(__popc(cached ? Dc[x_l] : ld_dom(Dc + x_l))) : uint32_t(N.d);
+      const uint32_t cmin = __reduce_min_sync(kFull, dy);
+      const uint32_t csum = __reduce_add_sync(kFull, y_ok ? dy : 0u);
+      const uint32_t rmin = __reduce_min_sync(kFull, dx);
+      if (lane == i) {
+        f[5] = float(cmin) * inv_d;
+        f[6] = float(csum) * inv_cols;
+        f[7] = float(rmin) * inv_d;
+      }
+    }
+    float z = __int_as_float(0x7FC00000);  // NaN: not scored
+    if (learned && need_mask != 0u) z = mlp_warp_logits(P.mlp, f);
+    // pending pairs (learned gating without RAC_VERIFY_FULL)
+    const bool pending_on = P.pend != nullptr;
+    uint8_t *pd_ptr = pending_on ? P.pend + int64_t(si.sl) * P.flag_stride + s_l : nullptr;
+    const bool pd = pending_on && valid && *pd_ptr != 0;
+    bool ev;
+    if (!valid)
+      ev = false;
+    else if (!learned)
+      ev = p2;                        // Proposition 2
+    else if (gated)
+      ev = p2 && z > P.mlp_thr;       // the predictor's choice among the candidates
+    else if (pending_on)
+      ev = p2 || pd;                  // verification: candidates and pending pairs
+    else
+      ev = true;                      // RAC_VERIFY_FULL: every slab
+    const uint32_t ev_mask = __ballot_sync(kFull, ev);
+    if (pending_on) {
+      // a skipped candidate becomes pending; an evaluated pair is no longer
+      const bool npd = !ev && (pd || (gated && p2));
+      // every warp of the state group has read the flags before they change
+      if (wps > 1) named_bar(state_group_bar(cg, g), wps * 32);
+      if (sub == 0 && valid && npd != pd) {
+        *pd_ptr = npd ? 1 : 0;
+        const int delta = npd ? 1 : -1;
+        atomicAdd(P.pend_slab + si.sl, delta);
+        atomicAdd(P.pcount + s_l, delta);
+      }
+    }
+    int64_t rec = -1;
+    if (recording && sub == 0) {
+      unsigned long long base = 0ull;
+      if (lane == 0 && need_mask != 0u) base = atomicAdd(P.tr_count, (unsigned long long)__popc(need_mask));
+      base = __shfl_sync(kFull, base, 0);
+      if (need) {
+        const int64_t r = int64_t(base) + __popc(need_mask & lanemask_lt());
+        if (r < P.tr_cap) {
+          rec = r;
+#pragma unroll
+          for (int j = 0; j < kMlpIn; ++j) P.tr_x[r * kMlpIn + j] = f[j];
+          P.tr_y[r] = ev ? 0.0f : -1.0f;  // an evaluated record gets its label below
+          if (P.tr_z) P.tr_z[r] = z;
+          int32_t *w = P.tr_w + r * 4;
+          w[0] = k | (gated ? (1 << 30) : 0);
+          w[1] = P.tr_state_base + s_l;
+          w[2] = int32_t(si.ij);
+          w[3] = int32_t(si.rows);
+        }
+      }
+    }
+    if (P.tr_evals && sub == 0 && lane == 0 && ev_mask != 0u)
+      atomicAdd(P.tr_evals, (unsigned long long)__popc(ev_mask));
+    for (uint32_t m = ev_mask; m; m &= m - 1u) {
+      const int i = __ffs(m) - 1;
+      const int s = c0 + groups * i;
+      const bool removed = eval_state<Q, true>(S, P, s, k, slot_w, hdr, rel, I, row0, nrows, y,
+                                               y_ok, cached, warp, lane, cg, g, sub, wps, red_iter);
+      if (recording && sub == 0) {
+        const int64_t r = __shfl_sync(kFull, rec, i);
+        if (lane == 0 && r >= 0) P.tr_y[r] = removed ? 1.0f : 0.0f;
+      }
+    }
+  }
+}
+
+template <int Q, bool kGate>
 __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char *stage,
                              const StageInfo &si, int k, int slot_r, int slot_w, int warp,
                              int lane, uint32_t &red_iter) {
@@ -198,59 +399,31 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
   const int wps = P.n_states >= 4 ? 1 : (P.n_states >= 2 ? 2 : 4);
   const int groups = kGroupWarps / wps;
   const int g = lw / wps, sub = lw % wps;
-  const uint32_t dfull = N.d >= 32 ? kFull : ((1u << N.d) - 1u);
   const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
   const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
   const bool cached = S.dom_cached != 0;
   if (k == 1 && P.seed_var >= 0 && !slab_touches_seed(P, I, J, row0, nrows)) return;
+  if constexpr (kGate) {
+    if (k >= 2) {
+      consume_slab_gated<Q>(S, P, hdr, rel, si, k, slot_r, slot_w, warp, lane, cg, g, sub, wps,
+                            groups, red_iter);
+      return;
+    }
+  }
   for (int s = g; s < P.n_states; s += groups) {
     if (S.st_info[s] & kInfoSweepMask) continue;  // finished state
     if (incr) {
       const uint32_t *ch = P.chg + (int64_t(slot_r) * P.flag_stride + s) * N.nb;
       if (ld_dom(ch + J) == 0u && (ld_dom(ch + I) & rowmask) == 0u) continue;
     }
-    const StateView V = state_view(P, s, k);
-    const uint32_t *Dc = cached ? S.dom + s * n : V.C;
-    uint32_t Dy = y_ok ? (cached ? Dc[y] : ld_dom(Dc + y)) : 0u;
-    if (k == 1 && !cached) Dy = input_word(P, y, Dy);
-    uint32_t racc = kFull;
-    for (int r = sub; r < int(nrows); r += wps) {
-      const uint32_t pm = hdr[r];
-      if (pm == 0u) continue;
-      const int x = int(I) * 32 + int(row0) + r;
-      uint32_t Dx = cached ? Dc[x] : ld_dom(Dc + x);
-      if (k == 1 && !cached) Dx = input_word(P, x, Dx);
-      uint32_t fwd = kFull, rev = kFull;
-      if ((pm >> lane) & 1u) {
-        // this lane's relation: rank t in the row, chunk c at c * cnt + t
-        const uint32_t t = __popc(pm & lanemask_lt());
-        const uint4 *mine = rel + hdr[nrows + r] * Q + t;
-        if (Dx == dfull)
-          support_relation<Q, true>(mine, __popc(pm), Dx, Dy, fwd, rev);
-        else
-          support_relation<Q, false>(mine, __popc(pm), Dx, Dy, fwd, rev);
-      }
-      const uint32_t keep_x = __reduce_and_sync(kFull, fwd) & Dx;
-      if (keep_x != Dx && lane == 0) remove_values(S, P, s, slot_w, V.T, uint32_t(x), keep_x);
-      racc &= rev;
-    }
-    if (wps > 1) {
-      const int buf = red_iter & 1;
-      S.red[buf][warp][lane] = racc;
-      named_bar(state_group_bar(cg, g), wps * 32);
-      if (sub == 0) {
-        for (int j = 1; j < wps; ++j) racc &= S.red[buf][warp + j][lane];
-      }
-      ++red_iter;
-    }
-    if (sub == 0 && y_ok) {
-      const uint32_t keep_y = racc & Dy;
-      if (keep_y != Dy) remove_values(S, P, s, slot_w, V.T, uint32_t(y), keep_y);
-    }
+    eval_state<Q, false>(S, P, s, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, cached, warp,
+                         lane, cg, g, sub, wps, red_iter);
   }
 }
 
-template <int Q>
+// kGate: the variant of rac_enforce_learned (learned gating and/or trace
+// records); the plain variant carries none of that code.
+template <int Q, bool kGate>
 __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParams P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *ring = smem_raw;
@@ -276,6 +449,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
     }
     fence_mbar_init();
     S.all_done = 0;
+    S.load_all = 1;
     S.abort = 0;
     S.failed = 0;
     S.dom_cached = int64_t(B) * n <= kDomWords ? 1u : 0u;
@@ -327,7 +501,8 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
         // producer: stream this CTA's active slabs through the ring
         if (lane == 0) {
           if (cta == 0) P.sync->bar[slot_c] = 0ull;  // last used two sweeps (or a launch) ago
-          const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
+          // (learned gating: every slab while some state is in its full phase)
+          const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2 && !(P.mlp && S.load_all);
           const uint32_t *cu = P.chgU + int64_t(slot_r) * N.nb;
           bool ok = true;
           // in sweep 1 the first slab may already be on its way
@@ -338,7 +513,9 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
               const uint32_t I = sd.ij & 0xFFFFu, J = sd.ij >> 16;
               const uint32_t row0 = sd.rows & 0xFFu, nrows = sd.rows >> 8;
               const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
-              if (ld_dom(cu + J) == 0u && (ld_dom(cu + I) & rowmask) == 0u) continue;
+              if (ld_dom(cu + J) == 0u && (ld_dom(cu + I) & rowmask) == 0u &&
+                  !(P.pend_slab && ld_dom(reinterpret_cast<const uint32_t *>(P.pend_slab) + sl) != 0u))
+                continue;
             } else if (k == 1 && P.seed_var >= 0 &&
                        !slab_touches_seed(P, sd.ij & 0xFFFFu, sd.ij >> 16, sd.rows & 0xFFu,
                                           sd.rows >> 8)) {
@@ -392,6 +569,19 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
           P.chg[slot_c * stride * N.nb + i] = 0u;
         for (int64_t i = cgtid; i < N.nb; i += cgstride) P.chgU[int64_t(slot_c) * N.nb + i] = 0u;
         named_bar(kAllConsumersBar, kConsumerWarps * 32);
+        // sweep 1 evaluates every slab for every state
+        if (k == 1 && P.tr_evals && cta == 0 && ctid == 0)
+          atomicAdd(P.tr_evals, (unsigned long long)N.n_slabs * (unsigned long long)B);
+        if (k == 1 && P.pend) {
+          // no pair is pending before sweep 2 (this CTA's slabs; CTA 0 the counts)
+          for (int64_t i = ctid; i < int64_t(my_slabs) * B; i += kConsumerWarps * 32) {
+            const int sl = cta + int(i / B) * G;
+            P.pend[int64_t(sl) * P.flag_stride + (i % B)] = 0;
+          }
+          for (int j = ctid; j < my_slabs; j += kConsumerWarps * 32) P.pend_slab[cta + j * G] = 0;
+          if (cta == 0)
+            for (int s = ctid; s < B; s += kConsumerWarps * 32) P.pcount[s] = 0;
+        }
         if (k == 1) {
           // A := dom_in; B (all ones between launches) &= dom_in -- an AND,
           // so it needs no ordering against this sweep's removals; note
@@ -440,7 +630,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
           __syncwarp();
           const StageInfo si = S.stage[stg];
           if (si.sl >= 0)
-            consume_slab<Q>(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_r, slot_w, warp,
+            consume_slab<Q, kGate>(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_r, slot_w, warp,
                             lane, red_iter);
           __syncwarp();
           if (lane == 0) mbar_arrive(&S.empty[stg]);
@@ -486,20 +676,38 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
         if (wp) info |= kInfoWiped;
         const uint32_t t_is_b = (k & 1) ? kInfoResB : 0u;               // T of sweep k
         const uint32_t c_is_b = (k >= 2 && !(k & 1)) ? kInfoResB : 0u;  // C of sweep k
+        const bool gated = (info & kInfoGated) != 0u;
+        // a sweep that removed nothing ends the state if it proves the
+        // fixpoint: any sweep of the plain and Proposition-2 recurrences; with
+        // pending pairs, one that left no pair pending; with RAC_VERIFY_FULL,
+        // a full sweep
+        const bool proves = !P.mlp ? true
+                            : P.pend ? ld_dom(reinterpret_cast<const uint32_t *>(P.pcount) + s) == 0u
+                                     : !gated;
         if (stop && wp) {
           info |= uint32_t(k) | t_is_b | info_status_bits(RAC_WIPEOUT);
-        } else if (!any) {
+        } else if (!any && proves) {
           info |= uint32_t(k) | c_is_b |
                   info_status_bits((info & kInfoWiped) ? RAC_WIPEOUT : RAC_OK);
         } else if ((P.max_sweeps > 0 && k >= P.max_sweeps) || k >= P.sweep_bound) {
           info |= uint32_t(k) | t_is_b | info_status_bits(RAC_ETIMEOUT);
+        } else if (P.mlp) {
+          info = any ? (info | kInfoGated) : (info & ~kInfoGated);
         }
         S.st_info[s] = info;
       }
-      if (tid == 0) S.all_done = 1;
+      if (tid == 0) {
+        S.all_done = 1;
+        S.load_all = 0;
+      }
       __syncthreads();
-      for (int s = tid; s < B; s += blockDim.x)
-        if (!(S.st_info[s] & kInfoSweepMask)) S.all_done = 0;
+      for (int s = tid; s < B; s += blockDim.x) {
+        const uint32_t info = S.st_info[s];
+        if (!(info & kInfoSweepMask)) {
+          S.all_done = 0;
+          if (!(info & kInfoGated) && (P.flags & RAC_VERIFY_FULL)) S.load_all = 1;
+        }
+      }
       __syncthreads();
       if (S.all_done) break;
     }
@@ -538,7 +746,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
   }
 }
 
-template <int Q>
+template <int Q, bool kGate>
 rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
   static int grid = 0;
   static int dev_cached = -1;
@@ -547,11 +755,11 @@ rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (grid == 0 || dev_cached != dev) {
-    e = cudaFuncSetAttribute(rac_bits_kernel<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(rac_bits_kernel<Q, kGate>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(smem));
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rac_bits_kernel<Q>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rac_bits_kernel<Q, kGate>, kThreads, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
@@ -572,25 +780,31 @@ rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, rac_bits_kernel<Q>, P);
+  e = cudaLaunchKernelEx(&cfg, rac_bits_kernel<Q, kGate>, P);
   if (e != cudaSuccess) return cuda_fail(e, "launch of the bit-packed kernel");
   return RAC_OK;
+}
+
+template <bool kGate>
+rac_status launch_width(const LaunchParams &P, cudaStream_t stream) {
+  switch (P.net.q) {
+    case 1: return launch_q<1, kGate>(P, stream);
+    case 2: return launch_q<2, kGate>(P, stream);
+    case 3: return launch_q<3, kGate>(P, stream);
+    case 4: return launch_q<4, kGate>(P, stream);
+    case 5: return launch_q<5, kGate>(P, stream);
+    case 6: return launch_q<6, kGate>(P, stream);
+    case 7: return launch_q<7, kGate>(P, stream);
+    case 8: return launch_q<8, kGate>(P, stream);
+    default: set_error("unsupported relation width"); return RAC_EINVAL;
+  }
 }
 
 }  // namespace
 
 rac_status launch_bits(const LaunchParams &P, cudaStream_t stream) {
-  switch (P.net.q) {
-    case 1: return launch_q<1>(P, stream);
-    case 2: return launch_q<2>(P, stream);
-    case 3: return launch_q<3>(P, stream);
-    case 4: return launch_q<4>(P, stream);
-    case 5: return launch_q<5>(P, stream);
-    case 6: return launch_q<6>(P, stream);
-    case 7: return launch_q<7>(P, stream);
-    case 8: return launch_q<8>(P, stream);
-    default: set_error("unsupported relation width"); return RAC_EINVAL;
-  }
+  const bool gate = P.mlp != nullptr || P.tr_count != nullptr || P.tr_evals != nullptr;
+  return gate ? launch_width<true>(P, stream) : launch_width<false>(P, stream);
 }
 
 }  // namespace rac

@@ -1,6 +1,7 @@
 // Internal types shared by the host side of librac and its kernels.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -60,6 +61,7 @@ struct NetDev {
   int32_t n, d, dp, q, nb, rows_per_slab, n_slabs;
   const uint4 *rel;
   const SlabDesc *slabs;
+  const float2 *slab_feat;  // per slab: (tightness, density), the predictor's f3 and f4
 };
 
 // Launch-to-launch state of a workspace.  Between launches the scratch
@@ -81,12 +83,12 @@ constexpr int kBarCountBits = 16;  // grids of at most 65535 CTAs
 constexpr uint32_t kErrGridWait = 1u;
 constexpr uint32_t kErrCopyWait = 2u;
 
-constexpr int kMaxFirst = 160;
+constexpr int kMaxFirst = 160;  // per-CTA first slab descriptors passed with the launch
 constexpr uint64_t kWaitLimitNs = 2000000000ull;      // 2 s
 constexpr uint64_t kTestWaitLimitNs = 50000000ull;    // 50 ms under RAC_TEST_WITHHOLD_ARRIVAL
 inline uint64_t wait_limit_for(uint32_t flags) {
   return (flags & RAC_TEST_WITHHOLD_ARRIVAL) ? kTestWaitLimitNs : kWaitLimitNs;
-}  // per-CTA first slab descriptors passed with the launch
+}
 
 struct LaunchParams {
   NetDev net;
@@ -112,6 +114,30 @@ struct LaunchParams {
   int32_t seed_var;          // >= 0: the search's assignment (one state only): the
   uint32_t seed_keep;        //   input domain of seed_var is ANDed with seed_keep, and
                              //   sweep 1 examines only the constraints on seed_var
+  // learned gating (rac_enforce_learned): with mlp set, sweep k >= 2 of a
+  // state in the gated phase evaluates a Proposition-2 candidate slab only if
+  // the predictor's logit exceeds mlp_thr; a gated sweep that removes nothing
+  // is followed by a full sweep, and only a full sweep that removes nothing
+  // ends the state
+  const __nv_bfloat16 *mlp;
+  float mlp_thr;
+  // pending (slab, state) pairs: candidates a gated sweep skipped and no
+  // sweep has evaluated since (RAC_VERIFY_FULL off).  pend[sl * flag_stride
+  // + s] is owned by the CTA that owns slab sl; pend_slab[sl] counts the
+  // slab's pending states, pcount[s] the state's pending slabs.
+  uint8_t *pend;
+  int32_t *pend_slab;
+  int32_t *pcount;
+  // trace records (tr_count set): one per Proposition-2 candidate of sweep
+  // k >= 2 -- features [8], label (1 removed / 0 not / -1 skipped), logit,
+  // where [4] = k (| 1 << 30 in the gated phase), state, tile I | J << 16,
+  // rows row0 | nrows << 8
+  float *tr_x, *tr_y, *tr_z;
+  int32_t *tr_w;
+  int64_t tr_cap;
+  unsigned long long *tr_count;  // records offered (may exceed tr_cap)
+  unsigned long long *tr_evals;  // (slab, state) evaluations executed
+  int32_t tr_state_base;         // added to the state index of a record
   int32_t n_first;           // CTAs whose first slab descriptor is in `first`
   SlabDesc first[kMaxFirst];
 };
@@ -182,6 +208,10 @@ struct Workspace {
   int32_t *host_res = nullptr;
   size_t host_cap = 0;
   size_t host_res_cap = 0;
+  // learned gating: pending pairs (allocated on the first learned call)
+  uint8_t *pend = nullptr;       // [n_slabs][cap_states]
+  int32_t *pend_slab = nullptr;  // [n_slabs]
+  int32_t *pcount = nullptr;     // [cap_states]
 };
 
 }  // namespace rac
@@ -194,6 +224,7 @@ struct rac_network {
   int device = 0;
   void *d_rel = nullptr;
   rac::SlabDesc *d_slabs = nullptr;
+  float2 *d_slab_feat = nullptr;      // per slab: tightness, density
   std::vector<rac::SlabDesc> first;  // host copy of the first kMaxFirst descriptors
   std::mutex mu;
   std::unordered_map<cudaStream_t, rac::Workspace *> ws;
@@ -208,6 +239,8 @@ rac_status launch_bits(const LaunchParams &P, cudaStream_t stream);
 // Launch the tensor-core kernel for P (at most 128 states).
 rac_status launch_tc(const LaunchParams &P, cudaStream_t stream);
 constexpr int kTensorMaxStates = 128;
+const __nv_bfloat16 *predictor_weights(const rac_predictor *p);
+int predictor_device(const rac_predictor *p);
 Workspace *get_workspace(const rac_network *net, cudaStream_t stream, int n_states, int n_items,
                          rac_status *rc);
 void free_workspace(Workspace *w);

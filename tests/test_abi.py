@@ -88,3 +88,28 @@ def test_python_binding_wraps_errors(L):
     with pytest.raises(rac.RacError) as e:
         rac.Network(3, 40, np.zeros((0, 2), np.int32), np.zeros((0, 40), np.uint32))
     assert e.value.code == rac.EINVAL
+
+
+def test_predictor_entry_points_check_arguments(L):
+    assert L.rac_predictor_num_params() == rac.PREDICTOR_PARAMS
+    assert L.rac_predictor_create(0, None) == rac.EINVAL
+    L.rac_predictor_destroy(None)  # NULL-safe
+    assert L.rac_predictor_set_weights(None, None) == rac.EINVAL
+    assert L.rac_predictor_get_weights(None, None, 0) == rac.EINVAL
+    assert L.rac_predictor_gradient(None, None, None, 0, 1.0, None, None) == rac.EINVAL
+    assert L.rac_predictor_train(None, None, None, 0, 1, 1, 1e-3, 1.0, 0, None) == rac.EINVAL
+    assert L.rac_predictor_predict(None, None, 1, None, 1) == rac.EINVAL
+    assert L.rac_enforce_learned(None, 1, None, None, None, None, 0, 0, None, 0.0, None,
+                                 None) == rac.EINVAL
+    assert L.rac_last_error().decode() != ""
+
+
+def test_trace_struct_matches_header():
+    """struct rac_trace: four pointers, an int64, two pointers (no padding
+    on LP64)."""
+    assert ctypes.sizeof(rac.RacTrace) == 7 * 8
+    src = open(os.path.join(ROOT, "include", "rac.h")).read()
+    body = src[src.index("typedef struct rac_trace {"):src.index("} rac_trace;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\*?\s*(\w+);", body)
+    assert fields == [f[0] for f in rac.RacTrace._fields_]
