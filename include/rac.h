@@ -293,6 +293,11 @@ RAC_API rac_status rac_enforce_noalloc(const rac_network *net, const uint32_t *d
  * So the result and status are those of rac_enforce; the sweep count is the
  * number of sweeps this gated recurrence executed (it may differ).
  *
+ * Every sweep is gated, the first one included: before sweep 1 a variable
+ * counts as changed when its input domain is not full (so on states that
+ * assign a few variables of full domains the predictor can learn the seeded
+ * first sweep of Algorithm 2; nothing relies on it).
+ *
  * The predictor is an MLP 8 -> 64 -> 64 -> 1 (ReLU hidden layers, a logit
  * out) with BF16 weights and FP32 accumulation.  Its 8 features of a (slab,
  * state) pair before sweep k, all in [0, 1]:
@@ -356,10 +361,10 @@ RAC_API rac_status rac_predictor_predict(const rac_predictor *p, const float *x,
                                          float *logits, int32_t tensor_cores);
 
 /* Optional record of the gating decisions of rac_enforce_learned: one record
- * per Proposition-2 candidate (slab, state) of every sweep k >= 2 (with a
- * predictor, candidates of verification sweeps too; pending pairs that are
- * no candidate get no record).  Records are appended in no particular
- * order. */
+ * per Proposition-2 candidate (slab, state) of every sweep (sweep 1: every
+ * pair; with a predictor, candidates of verification sweeps too; pending
+ * pairs that are no candidate get no record).  Records are appended in no
+ * particular order. */
 typedef struct rac_trace {
   float *features;   /* DEVICE, capacity x 8: the features above */
   float *label;      /* DEVICE, capacity: 1 the evaluation removed a value,

@@ -10,7 +10,9 @@ gated enforcement must contain:
                           (lo % 32) // rows == row0 // rows (lo < hi the
                           constraint's variables);
   candidate(...)          Proposition 2: some variable of the slab's rows or of
-                          its column block changed in sweep k-1;
+                          its column block changed in sweep k-1 (before sweep
+                          1 every pair is a candidate, and a variable counts
+                          as changed when its input domain is not full);
   label(...)              the evaluation of the slab's constraints on D_{k-1}
                           removes a value: some (x, a) with a in D_{k-1}(x) has
                           no b in D_{k-1}(y) with R_xy[a][b] on one of them

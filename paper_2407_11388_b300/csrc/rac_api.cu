@@ -658,12 +658,14 @@ rac_status rac_enforce_learned(const rac_network *net, int32_t n_states, const u
     P.dom_out = dom_out + size_t(base) * net->n;
     P.iterations = sweeps + base;
     P.status = status + base;
-    P.mlp = pred ? predictor_weights(pred) : nullptr;
+    P.mlp = pred ? predictor_pack(pred) : nullptr;
     P.mlp_thr = threshold;
     if (pred && !(flags & RAC_VERIFY_FULL)) {
       P.pend = w->pend;
       P.pend_slab = w->pend_slab;
       P.pcount = w->pcount;
+      cudaError_t e = cudaMemsetAsync(w->pcount, 0, size_t(cnt) * sizeof(int32_t), s);
+      if (e != cudaSuccess) return cuda_fail(e, "clearing the pending counts");
     }
     if (trace) {
       P.tr_x = trace->features;

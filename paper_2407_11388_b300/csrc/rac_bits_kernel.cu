@@ -66,8 +66,19 @@ struct Smem {
   uint8_t any_loc[kMaxStatesPerLaunch];
   uint8_t wipe_loc[kMaxStatesPerLaunch];
   SlabDesc desc[kDescCache];
-  uint32_t dom[kDomWords];  // D_{k-1} of every running state, when it fits
+  // D_{k-1} of every running state, when it fits; the gated variant keeps the
+  // predictor's packed weights in the last kMlpSmemWords words instead
+  alignas(16) uint32_t dom[kDomWords];
 };
+constexpr int kMlpSmemWords = kPackVec4 * 4;
+static_assert(kMlpSmemWords < kDomWords && (kDomWords - kMlpSmemWords) % 4 == 0,
+              "the packed weights fit at the 16-byte aligned end of the domain cache");
+__device__ __forceinline__ const uint4 *smem_mlp(const Smem &S) {
+  return reinterpret_cast<const uint4 *>(S.dom + (kDomWords - kMlpSmemWords));
+}
+// domain words the cache holds in the given variant
+template <int kGate>
+constexpr int dom_cache_words() { return kGate > 0 ? kDomWords - kMlpSmemWords : kDomWords; }
 static_assert(kStages % kGroups == 0, "each ring stage belongs to one consumer group");
 static_assert(size_t(kStages) * kStageBytes + sizeof(Smem) <= 232448,
               "shared memory of the bit-packed kernel exceeds 227 KB");
@@ -251,13 +262,15 @@ __device__ __forceinline__ bool eval_state(Smem &S, const LaunchParams &P, int s
   return rem;
 }
 
-// Sweep k >= 2 of rac_enforce_learned: the states of this warp's state group
-// are taken 32 at a time (lane i <-> state c0 + groups * i).  Per chunk:
-// the Proposition-2 test (a variable of the slab's rows or columns changed in
-// sweep k-1), the predictor's features and -- for states in the gated phase
-// -- its logit (one warp-wide tensor-core MLP for the 32 states), then the
-// evaluations the decision keeps, with optional trace records.
-template <int Q>
+// The sweeps of rac_enforce_learned (every sweep; the first one counts a
+// variable as changed when its input domain is not full).  The states of this
+// warp's state group are taken 32 at a time (lane i <-> state c0 + groups *
+// i).  Per chunk: the Proposition-2 test (a variable of the slab's rows or
+// columns changed in sweep k-1), the predictor's features and -- for states
+// in their gated phase -- its logit (one warp-wide tensor-core MLP for the
+// chunk), then the evaluations the decision keeps, the pending flags and the
+// optional trace records.
+template <int Q, int kMT>
 __device__ void consume_slab_gated(Smem &S, const LaunchParams &P, const uint32_t *hdr,
                                    const uint4 *rel, const StageInfo &si, int k, int slot_r,
                                    int slot_w, int warp, int lane, int cg, int g, int sub,
@@ -267,6 +280,7 @@ __device__ void consume_slab_gated(Smem &S, const LaunchParams &P, const uint32_
   const uint32_t I = si.ij & 0xFFFFu, J = si.ij >> 16;
   const uint32_t row0 = si.rows & 0xFFu, nrows = si.rows >> 8;
   const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
+  const uint32_t dfull = N.d >= 32 ? kFull : ((1u << N.d) - 1u);
   const int y = int(J) * 32 + lane;
   const bool y_ok = y < n;
   const int x_l = int(I) * 32 + int(row0) + lane;
@@ -274,58 +288,104 @@ __device__ void consume_slab_gated(Smem &S, const LaunchParams &P, const uint32_
   const bool cached = S.dom_cached != 0;
   const float2 sf = N.slab_feat[si.sl];
   const float inv_d = 1.0f / float(N.d);
+  const float inv_rows = 1.0f / float(nrows);
   const float inv_cols = 1.0f / float(min(32, n - int(J) * 32) * N.d);
   const bool learned = P.mlp != nullptr;
   const bool recording = P.tr_count != nullptr;
+  const bool pending_on = P.pend != nullptr;
   for (int c0 = g; c0 < B; c0 += 32 * groups) {
     const int s_l = c0 + groups * lane;
     const uint32_t info = s_l < B ? S.st_info[s_l] : 1u;  // lanes past the end look finished
     const bool valid = (info & kInfoSweepMask) == 0u;
     const bool gated = learned && (info & kInfoGated);
     uint32_t cI = 0u, cJ = 0u;
-    if (valid) {
+    bool p2 = valid;  // sweep 1: every pair is a candidate
+    if (valid && k >= 2) {
       const uint32_t *ch = P.chg + (int64_t(slot_r) * P.flag_stride + s_l) * N.nb;
       cJ = ld_dom(ch + J);
       cI = ld_dom(ch + I) & rowmask;
+      p2 = (cI | cJ) != 0u;
     }
-    const bool p2 = (cI | cJ) != 0u;
     const bool need = valid && p2 && (gated || recording);
     const uint32_t need_mask = __ballot_sync(kFull, need);
     float f[kMlpIn];
     f[0] = float(min(k, 16)) * (1.0f / 16.0f);
-    f[1] = float(__popc(cI)) / float(nrows);
+    f[1] = float(__popc(cI)) * inv_rows;
     f[2] = float(__popc(cJ)) * (1.0f / 32.0f);
     f[3] = sf.x;
     f[4] = sf.y;
     f[5] = f[6] = f[7] = 0.0f;
-    // domain sizes of D_{k-1}: the warp reads one state's column words
-    // (lane = column) and row words (lane = row) at a time
-    for (uint32_t m = need_mask; m; m &= m - 1u) {
-      const int i = __ffs(m) - 1;
-      const int s = c0 + groups * i;
-      const uint32_t *Dc = cached ? S.dom + s * n : state_view(P, s, k).C;
-      const uint32_t dy = y_ok ? uint32_t(__popc(cached ? Dc[y] : ld_dom(Dc + y))) : uint32_t(N.d);
-      const uint32_t dx = x_ok ? uint32_t(__popc(cached ? Dc[x_l] : ld_dom(Dc + x_l))) : uint32_t(N.d);
-      const uint32_t cmin = __reduce_min_sync(kFull, dy);
-      const uint32_t csum = __reduce_add_sync(kFull, y_ok ? dy : 0u);
-      const uint32_t rmin = __reduce_min_sync(kFull, dx);
-      if (lane == i) {
-        f[5] = float(cmin) * inv_d;
-        f[6] = float(csum) * inv_cols;
-        f[7] = float(rmin) * inv_d;
+    // domain sizes of D_{k-1} (and, in sweep 1, the variables whose input
+    // domain is not full): the warp reads the column words (lane = column)
+    // and row words (lane = row) of up to four states at a time
+    for (uint32_t m = need_mask; m;) {
+      int ii[4];
+      uint32_t wy[4], wx[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ii[u] = m ? __ffs(m) - 1 : -1;
+        m &= m ? m - 1u : 0u;
+        wy[u] = wx[u] = dfull;
+        if (ii[u] >= 0) {
+          const int s = c0 + groups * ii[u];
+          const uint32_t *Dc = cached ? S.dom + s * n : state_view(P, s, k).C;
+          if (y_ok) wy[u] = cached ? Dc[y] : ld_dom(Dc + y);
+          if (x_ok) wx[u] = cached ? Dc[x_l] : ld_dom(Dc + x_l);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (ii[u] < 0) continue;
+        const uint32_t dy = uint32_t(__popc(wy[u])), dx = uint32_t(__popc(wx[u]));
+        const uint32_t cmin = __reduce_min_sync(kFull, dy);
+        const uint32_t csum = __reduce_add_sync(kFull, y_ok ? dy : 0u);
+        const uint32_t rmin = __reduce_min_sync(kFull, dx);
+        uint32_t nfc = 0u, nfr = 0u;
+        if (k == 1) {
+          nfc = __ballot_sync(kFull, wy[u] != dfull);
+          nfr = __ballot_sync(kFull, wx[u] != dfull);
+        }
+        if (lane == ii[u]) {
+          f[5] = float(cmin) * inv_d;
+          f[6] = float(csum) * inv_cols;
+          f[7] = float(rmin) * inv_d;
+          if (k == 1) {
+            f[1] = float(__popc(nfr)) * inv_rows;
+            f[2] = float(__popc(nfc)) * (1.0f / 32.0f);
+          }
+        }
+      }
+    }
+    // trace record: features and place now, decision, logit and label below
+    int64_t rec = -1;
+    if (recording && sub == 0) {
+      unsigned long long base = 0ull;
+      if (lane == 0 && need_mask != 0u) base = atomicAdd(P.tr_count, (unsigned long long)__popc(need_mask));
+      base = __shfl_sync(kFull, base, 0);
+      if (need) {
+        const int64_t r = int64_t(base) + __popc(need_mask & lanemask_lt());
+        if (r < P.tr_cap) {
+          rec = r;
+#pragma unroll
+          for (int j = 0; j < kMlpIn; ++j) P.tr_x[r * kMlpIn + j] = f[j];
+          int32_t *w = P.tr_w + r * 4;
+          w[0] = k | (gated ? (1 << 30) : 0);
+          w[1] = P.tr_state_base + s_l;
+          w[2] = int32_t(si.ij);
+          w[3] = int32_t(si.rows);
+        }
       }
     }
     float z = __int_as_float(0x7FC00000);  // NaN: not scored
-    if (learned && need_mask != 0u) z = mlp_warp_logits(P.mlp, f);
+    if (learned && need_mask != 0u) z = mlp_warp_logits_mt<kMT>(smem_mlp(S), f);
     // pending pairs (learned gating without RAC_VERIFY_FULL)
-    const bool pending_on = P.pend != nullptr;
     uint8_t *pd_ptr = pending_on ? P.pend + int64_t(si.sl) * P.flag_stride + s_l : nullptr;
     const bool pd = pending_on && valid && *pd_ptr != 0;
     bool ev;
     if (!valid)
       ev = false;
     else if (!learned)
-      ev = p2;                        // Proposition 2
+      ev = p2;                        // Proposition 2 (sweep 1: everything)
     else if (gated)
       ev = p2 && z > P.mlp_thr;       // the predictor's choice among the candidates
     else if (pending_on)
@@ -345,26 +405,9 @@ __device__ void consume_slab_gated(Smem &S, const LaunchParams &P, const uint32_
         atomicAdd(P.pcount + s_l, delta);
       }
     }
-    int64_t rec = -1;
-    if (recording && sub == 0) {
-      unsigned long long base = 0ull;
-      if (lane == 0 && need_mask != 0u) base = atomicAdd(P.tr_count, (unsigned long long)__popc(need_mask));
-      base = __shfl_sync(kFull, base, 0);
-      if (need) {
-        const int64_t r = int64_t(base) + __popc(need_mask & lanemask_lt());
-        if (r < P.tr_cap) {
-          rec = r;
-#pragma unroll
-          for (int j = 0; j < kMlpIn; ++j) P.tr_x[r * kMlpIn + j] = f[j];
-          P.tr_y[r] = ev ? 0.0f : -1.0f;  // an evaluated record gets its label below
-          if (P.tr_z) P.tr_z[r] = z;
-          int32_t *w = P.tr_w + r * 4;
-          w[0] = k | (gated ? (1 << 30) : 0);
-          w[1] = P.tr_state_base + s_l;
-          w[2] = int32_t(si.ij);
-          w[3] = int32_t(si.rows);
-        }
-      }
+    if (rec >= 0) {
+      P.tr_y[rec] = ev ? 0.0f : -1.0f;  // an evaluated record gets its label below
+      if (P.tr_z) P.tr_z[rec] = z;
     }
     if (P.tr_evals && sub == 0 && lane == 0 && ev_mask != 0u)
       atomicAdd(P.tr_evals, (unsigned long long)__popc(ev_mask));
@@ -381,7 +424,7 @@ __device__ void consume_slab_gated(Smem &S, const LaunchParams &P, const uint32_
   }
 }
 
-template <int Q, bool kGate>
+template <int Q, int kGate>
 __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char *stage,
                              const StageInfo &si, int k, int slot_r, int slot_w, int warp,
                              int lane, uint32_t &red_iter) {
@@ -403,12 +446,10 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
   const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
   const bool cached = S.dom_cached != 0;
   if (k == 1 && P.seed_var >= 0 && !slab_touches_seed(P, I, J, row0, nrows)) return;
-  if constexpr (kGate) {
-    if (k >= 2) {
-      consume_slab_gated<Q>(S, P, hdr, rel, si, k, slot_r, slot_w, warp, lane, cg, g, sub, wps,
-                            groups, red_iter);
-      return;
-    }
+  if constexpr (kGate > 0) {
+    consume_slab_gated<Q, kGate>(S, P, hdr, rel, si, k, slot_r, slot_w, warp, lane, cg, g, sub,
+                                 wps, groups, red_iter);
+    return;
   }
   for (int s = g; s < P.n_states; s += groups) {
     if (S.st_info[s] & kInfoSweepMask) continue;  // finished state
@@ -421,9 +462,10 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
   }
 }
 
-// kGate: the variant of rac_enforce_learned (learned gating and/or trace
-// records); the plain variant carries none of that code.
-template <int Q, bool kGate>
+// kGate: 0 the plain variant; 1 or 2 the variant of rac_enforce_learned
+// (learned gating and/or trace records) whose warp-wide MLP scores 16 or 32
+// states of a warp at a time (one or two MMA M tiles).
+template <int Q, int kGate>
 __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParams P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *ring = smem_raw;
@@ -452,10 +494,16 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
     S.load_all = 1;
     S.abort = 0;
     S.failed = 0;
-    S.dom_cached = int64_t(B) * n <= kDomWords ? 1u : 0u;
+    S.dom_cached = int64_t(B) * n <= dom_cache_words<kGate>() ? 1u : 0u;
+  }
+  if constexpr (kGate > 0) {
+    if (P.mlp) {
+      uint4 *dst = reinterpret_cast<uint4 *>(S.dom + (kDomWords - kMlpSmemWords));
+      for (int i = tid; i < kPackVec4; i += blockDim.x) dst[i] = P.mlp[i];
+    }
   }
   for (int s = tid; s < B; s += blockDim.x) {
-    S.st_info[s] = 0;
+    S.st_info[s] = P.mlp ? kInfoGated : 0u;  // learned gating starts with a gated sweep
     S.any_loc[s] = 0;
     S.wipe_loc[s] = 0;
   }
@@ -568,20 +616,16 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
         for (int64_t i = cgtid; i < stride * N.nb; i += cgstride)
           P.chg[slot_c * stride * N.nb + i] = 0u;
         for (int64_t i = cgtid; i < N.nb; i += cgstride) P.chgU[int64_t(slot_c) * N.nb + i] = 0u;
-        named_bar(kAllConsumersBar, kConsumerWarps * 32);
-        // sweep 1 evaluates every slab for every state
-        if (k == 1 && P.tr_evals && cta == 0 && ctid == 0)
-          atomicAdd(P.tr_evals, (unsigned long long)N.n_slabs * (unsigned long long)B);
         if (k == 1 && P.pend) {
-          // no pair is pending before sweep 2 (this CTA's slabs; CTA 0 the counts)
+          // no pair of this CTA's slabs is pending yet (the per-state counts
+          // were zeroed before the launch)
           for (int64_t i = ctid; i < int64_t(my_slabs) * B; i += kConsumerWarps * 32) {
             const int sl = cta + int(i / B) * G;
             P.pend[int64_t(sl) * P.flag_stride + (i % B)] = 0;
           }
           for (int j = ctid; j < my_slabs; j += kConsumerWarps * 32) P.pend_slab[cta + j * G] = 0;
-          if (cta == 0)
-            for (int s = ctid; s < B; s += kConsumerWarps * 32) P.pcount[s] = 0;
         }
+        named_bar(kAllConsumersBar, kConsumerWarps * 32);
         if (k == 1) {
           // A := dom_in; B (all ones between launches) &= dom_in -- an AND,
           // so it needs no ordering against this sweep's removals; note
@@ -746,7 +790,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
   }
 }
 
-template <int Q, bool kGate>
+template <int Q, int kGate>
 rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
   static int grid = 0;
   static int dev_cached = -1;
@@ -785,7 +829,7 @@ rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
   return RAC_OK;
 }
 
-template <bool kGate>
+template <int kGate>
 rac_status launch_width(const LaunchParams &P, cudaStream_t stream) {
   switch (P.net.q) {
     case 1: return launch_q<1, kGate>(P, stream);
@@ -804,7 +848,10 @@ rac_status launch_width(const LaunchParams &P, cudaStream_t stream) {
 
 rac_status launch_bits(const LaunchParams &P, cudaStream_t stream) {
   const bool gate = P.mlp != nullptr || P.tr_count != nullptr || P.tr_evals != nullptr;
-  return gate ? launch_width<true>(P, stream) : launch_width<false>(P, stream);
+  if (!gate) return launch_width<0>(P, stream);
+  // a warp scores the states g, g + 4, ... of a 32-lane chunk: at most 16 of
+  // them while there are at most 64 states
+  return P.n_states <= 64 ? launch_width<1>(P, stream) : launch_width<2>(P, stream);
 }
 
 }  // namespace rac

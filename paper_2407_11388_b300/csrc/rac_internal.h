@@ -119,7 +119,7 @@ struct LaunchParams {
   // the predictor's logit exceeds mlp_thr; a gated sweep that removes nothing
   // is followed by a full sweep, and only a full sweep that removes nothing
   // ends the state
-  const __nv_bfloat16 *mlp;
+  const uint4 *mlp;          // the predictor's fragment-packed weights
   float mlp_thr;
   // pending (slab, state) pairs: candidates a gated sweep skipped and no
   // sweep has evaluated since (RAC_VERIFY_FULL off).  pend[sl * flag_stride
@@ -239,7 +239,7 @@ rac_status launch_bits(const LaunchParams &P, cudaStream_t stream);
 // Launch the tensor-core kernel for P (at most 128 states).
 rac_status launch_tc(const LaunchParams &P, cudaStream_t stream);
 constexpr int kTensorMaxStates = 128;
-const __nv_bfloat16 *predictor_weights(const rac_predictor *p);
+const uint4 *predictor_pack(const rac_predictor *p);  // fragment-packed weights
 int predictor_device(const rac_predictor *p);
 Workspace *get_workspace(const rac_network *net, cudaStream_t stream, int n_states, int n_items,
                          rac_status *rc);

@@ -34,6 +34,7 @@ struct rac_predictor {
   float *m = nullptr, *v = nullptr;  // Adam moments
   float *grad = nullptr;
   float *loss = nullptr;
+  uint32_t *pack = nullptr;          // fragment-packed BF16 copy for the warp-wide routine
   int64_t step = 0;
   // per-batch scratch, feature-major [rows][cap]
   float *xr = nullptr, *h1 = nullptr, *d1 = nullptr, *h2 = nullptr, *d2 = nullptr, *dz = nullptr;
@@ -150,6 +151,21 @@ __global__ void mlp_to_bf16(const float *master, __nv_bfloat16 *w) {
   if (p < kMlpParams) w[p] = __float2bfloat16(master[p]);
 }
 
+// The fragment-packed copy (rac_mlp.cuh): thread (lane, j) writes word j of
+// the lane; one more thread writes b3.
+__global__ void mlp_pack(const __nv_bfloat16 *w, uint32_t *pack) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 32 * 96) {
+    const int lane = i / 96, j = i % 96;
+    int i0, i1;
+    mlp_pack_word(lane, j, i0, i1);
+    const uint32_t lo = __bfloat16_as_ushort(w[i0]), hi = __bfloat16_as_ushort(w[i1]);
+    pack[((j / 4) * 32 + lane) * 4 + (j % 4)] = lo | (hi << 16);
+  } else if (i == 32 * 96) {
+    reinterpret_cast<float *>(pack)[kPackChunks * 32 * 4] = __bfloat162float(w[kMlpB3]);
+  }
+}
+
 __global__ void mlp_predict_scalar(const __nv_bfloat16 *w, const float *X, int64_t N, float *Z) {
   const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (n >= N) return;
@@ -160,13 +176,19 @@ __global__ void mlp_predict_scalar(const __nv_bfloat16 *w, const float *X, int64
 
 // The sweep kernel's inference routine on a plain array: warp q scores
 // samples 32 q .. 32 q + 31 (missing samples get zero features).
-__global__ void mlp_predict_tc(const __nv_bfloat16 *w, const float *X, int64_t N, float *Z) {
+__global__ void mlp_predict_tc(const uint4 *pack, const float *X, int64_t N, float *Z) {
   const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   float f[kMlpIn];
 #pragma unroll
   for (int j = 0; j < kMlpIn; ++j) f[j] = n < N ? X[n * kMlpIn + j] : 0.0f;
-  const float z = mlp_warp_logits(w, f);
+  // the upper M tile only when one of this warp's samples 16..31 exists
+  const bool upper = __any_sync(0xFFFFFFFFu, n < N && (threadIdx.x & 31) >= 16);
+  const float z = mlp_warp_logits(pack, f, upper);
   if (n < N) Z[n] = z;
+}
+
+void repack(rac_predictor *p) {
+  mlp_pack<<<(32 * 96 + 1 + 127) / 128, 128>>>(p->w, p->pack);
 }
 
 void pred_free_scratch(rac_predictor *p) {
@@ -179,7 +201,7 @@ void pred_free_scratch(rac_predictor *p) {
 void pred_free(rac_predictor *p) {
   if (!p) return;
   pred_free_scratch(p);
-  void *ptrs[] = {p->master, p->w, p->m, p->v, p->grad, p->loss};
+  void *ptrs[] = {p->master, p->w, p->m, p->v, p->grad, p->loss, p->pack};
   for (void *q : ptrs) cudaFree(q);
   delete p;
 }
@@ -223,7 +245,9 @@ void batch_gradient(rac_predictor *p, const float *X, const float *Y, int64_t N,
 }  // namespace
 
 namespace rac {
-const __nv_bfloat16 *predictor_weights(const rac_predictor *p) { return p ? p->w : nullptr; }
+const uint4 *predictor_pack(const rac_predictor *p) {
+  return p ? reinterpret_cast<const uint4 *>(p->pack) : nullptr;
+}
 int predictor_device(const rac_predictor *p) { return p ? p->device : -1; }
 }  // namespace rac
 
@@ -260,7 +284,8 @@ rac_status rac_predictor_create(uint64_t seed, rac_predictor **out) {
   if (cudaMalloc(&p->master, pb) != cudaSuccess ||
       cudaMalloc(&p->w, kMlpParams * sizeof(__nv_bfloat16)) != cudaSuccess ||
       cudaMalloc(&p->m, pb) != cudaSuccess || cudaMalloc(&p->v, pb) != cudaSuccess ||
-      cudaMalloc(&p->grad, pb) != cudaSuccess || cudaMalloc(&p->loss, sizeof(float)) != cudaSuccess) {
+      cudaMalloc(&p->grad, pb) != cudaSuccess || cudaMalloc(&p->loss, sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&p->pack, kPackWords * sizeof(uint32_t)) != cudaSuccess) {
     cudaGetLastError();
     pred_free(p);
     set_error("device allocation of the predictor failed");
@@ -271,6 +296,7 @@ rac_status rac_predictor_create(uint64_t seed, rac_predictor **out) {
   if (e == cudaSuccess) e = cudaMemset(p->v, 0, pb);
   if (e == cudaSuccess) {
     mlp_to_bf16<<<(kMlpParams + 255) / 256, 256>>>(p->master, p->w);
+    repack(p);
     e = cudaDeviceSynchronize();
   }
   if (e != cudaSuccess) {
@@ -296,6 +322,7 @@ rac_status rac_predictor_set_weights(rac_predictor *p, const float *params) {
   if (e == cudaSuccess) {
     p->step = 0;
     mlp_to_bf16<<<(kMlpParams + 255) / 256, 256>>>(p->master, p->w);
+    repack(p);
     e = cudaDeviceSynchronize();
   }
   return e == cudaSuccess ? RAC_OK : cuda_fail(e, "rac_predictor_set_weights");
@@ -364,6 +391,7 @@ rac_status rac_predictor_train(rac_predictor *p, const float *X, const float *Y,
     mlp_adam<<<(kMlpParams + 127) / 128, 128>>>(p->master, p->w, p->m, p->v, p->grad, lr, b1, b2,
                                                 1e-8f, c1, c2);
   }
+  repack(p);
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "predictor training");
   if (loss_out) {
@@ -383,7 +411,8 @@ rac_status rac_predictor_predict(const rac_predictor *p, const float *X, int64_t
   if (!check_pred_device(p)) return RAC_EINVAL;
   if (N == 0) return RAC_OK;
   if (tensor_cores)
-    mlp_predict_tc<<<unsigned((N + 127) / 128), 128>>>(p->w, X, N, Z);
+    mlp_predict_tc<<<unsigned((N + 127) / 128), 128>>>(reinterpret_cast<const uint4 *>(p->pack), X,
+                                                       N, Z);
   else
     mlp_predict_scalar<<<unsigned((N + 127) / 128), 128>>>(p->w, X, N, Z);
   cudaError_t e = cudaDeviceSynchronize();

@@ -9,8 +9,8 @@
   RAC_VERIFY_FULL.  At threshold -inf nothing is skipped: the pending mode
   runs exactly the Proposition-2 sweeps (K sweeps, the same evaluations) and
   RAC_VERIFY_FULL adds one full sweep (K + 1); at +inf every gated sweep
-  skips all and the verification sweep after it repeats one plain sweep
-  (2K - 1 sweeps in both modes);
+  (the first one included) skips all and the verification sweep after it
+  repeats one plain sweep (2K sweeps in both modes);
 - the logits the sweep kernel computed and the decisions it took agree with
   the float64 MLP on the recorded features;
 - a predictor trained on traces of other networks (the n=500 d=20 and batch
@@ -160,10 +160,12 @@ def test_trace_matches_oracle(n, d, dens, c):
     for s in range(doms.shape[0]):
         _, it, _, tr, _ = oracle.rac(n, d, scope, rel, doms[s], trace=True)
         seq = [doms[s]] + list(tr)
-        for k in range(2, it + 1):
-            changed = seq[k - 2] != seq[k - 1]
+        for k in range(1, it + 1):
+            # sweep 1: every pair is a candidate, and a variable counts as
+            # changed when its input domain is not full
+            changed = (seq[0] != full_word(d)) if k == 1 else (seq[k - 2] != seq[k - 1])
             for key in idx.keys:
-                if gating.candidate(idx, key, changed):
+                if k == 1 or gating.candidate(idx, key, changed):
                     want[(k, s) + key] = (gating.label(idx, key, seq[k - 1]),
                                           gating.features(idx, key, k, changed, seq[k - 1]))
     assert trace.count() == len(want) and len(want) > 0
@@ -179,12 +181,9 @@ def test_trace_matches_oracle(n, d, dens, c):
         wl, wf = want[key]
         assert lab == (1.0 if wl else 0.0), key
         assert np.allclose(f, wf, rtol=0, atol=2e-7), (key, f, wf)
-    # every candidate was evaluated, plus sweep 1 over every slab
-    assert trace.evaluated() == len(want) + idx_slabs(idx) * doms.shape[0]
-
-
-def idx_slabs(idx):
-    return len(idx.keys)
+    # every candidate was evaluated (sweep 1: every slab)
+    assert trace.evaluated() == len(want)
+    assert sum(1 for key in want if key[0] == 1) == len(idx.keys) * doms.shape[0]
 
 
 # ---------------------------------------------------------------------------
@@ -210,11 +209,11 @@ def test_learned_exact_at_the_extremes(n, d, dens, c):
         assert tr.evaluated() == tr_p2.evaluated()
         out, sw, st, _ = _run_learned(net, doms, pred, thr=-np.inf, flags=rac.VERIFY_FULL)
         _assert_exact(out, st, ref, "threshold -inf, full verification")
-        assert np.array_equal(sw, np.where(K >= 2, K + 1, 1)), (sw, K)
+        assert np.array_equal(sw, K + 1), (sw, K)
         for flags in (0, rac.VERIFY_FULL):
             out, sw, st, _ = _run_learned(net, doms, pred, thr=np.inf, flags=flags)
             _assert_exact(out, st, ref, "threshold +inf, flags %d" % flags)
-            assert np.array_equal(sw, 2 * K - 1), (flags, sw, K)
+            assert np.array_equal(sw, 2 * K), (flags, sw, K)
 
 
 @pytest.mark.parametrize("n,d,dens,c", LEARNED_CASES)
@@ -277,11 +276,10 @@ def test_learned_sweep_cap_and_empty_batch():
         for flags in (0, rac.VERIFY_FULL):
             out, sw, st, _ = _run_learned(net, doms, rac.Predictor(seed=1), thr=np.inf,
                                           max_sweeps=2, flags=flags)
+            # sweep 1 skips everything, sweep 2 is plain sweep 1
             for s in range(doms.shape[0]):
-                if ref[1][s] == 1:
-                    assert st[s] == ref[2][s] and sw[s] == 1
-                else:
-                    assert st[s] == rac.ETIMEOUT and sw[s] == 2
+                assert sw[s] == 2
+                assert st[s] == (ref[2][s] if ref[1][s] == 1 else rac.ETIMEOUT)
         empty = T.empty(0, dtype=T.int32, device="cuda:0")
         rac.enforce_learned(net, empty, empty, empty, empty, predictor=None, n_states=0)
 
