@@ -70,6 +70,15 @@ typedef int32_t rac_status;
 
 /* layout_flags of rac_create_network */
 #define RAC_LAYOUT_BITS 0x1u /* bit-packed relation slabs (always built) */
+/* Rows of the relation tiles ("slabs": 32 column variables x `rows` row
+ * variables of one block pair, read as one unit): RAC_LAYOUT_ROWS(l) asks
+ * for 2^l rows, 1 <= l <= 5 (a tile's header of 2 x rows words keeps the
+ * relations and the tile 16-byte aligned only from 2 rows on); without it the
+ * largest power of two whose slab fits the kernels' 32 KiB staging buffer
+ * (rows x 32 x round_up(d, 4) x 4 bytes) is used.  The result and the sweep
+ * count do not depend on it. */
+#define RAC_LAYOUT_ROWS(l) ((uint32_t)((l) + 1) << 8)
+#define RAC_LAYOUT_ROWS_MASK 0xF00u
 
 /* flags of the enforce calls */
 #define RAC_STOP_ON_WIPEOUT 0x1u /* end after the first sweep that leaves a domain
@@ -119,7 +128,9 @@ typedef int32_t rac_status;
  *             transposed (one relation per scope, Sec. 2).  Bits >= d must be
  *             zero.  Variables with no constraint between them are
  *             unconstrained (only real constraints are in C_x).
- *  layout_flags  RAC_LAYOUT_BITS (0 means the same).
+ *  layout_flags  RAC_LAYOUT_BITS (0 means the same), optionally |
+ *             RAC_LAYOUT_ROWS(l); a tile too large for the staging buffer is
+ *             rejected with RAC_EINVAL.
  *  out        receives the network handle.
  *
  * The library keeps its own copy; the host arrays may be freed on return.

@@ -21,6 +21,11 @@ from .build import LIB as _LIB_PATH
 OK, WIPEOUT = 0, 1
 EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBARRIER, ENOTSUP = -1, -2, -3, -4, -5, -6
 LAYOUT_BITS = 0x1
+
+
+def LAYOUT_ROWS(log2_rows):
+    """layout flag: relation tiles of 2**log2_rows rows (RAC_LAYOUT_ROWS)."""
+    return (int(log2_rows) + 1) << 8
 STOP_ON_WIPEOUT = 0x1
 INCREMENTAL = 0x2
 VERIFY_FULL = 0x4  # rac_enforce_learned: literal full verification sweep (see include/rac.h)
@@ -155,11 +160,22 @@ class Network:
     scope: (m, 2) int32 host array; rel: (m, d) uint32 host array, bit b of
     rel[c, a] = R_xy[a][b] for (x, y) = scope[c]."""
 
-    def __init__(self, n, d, scope, rel, layout=LAYOUT_BITS):
+    def __init__(self, n, d, scope, rel, layout=LAYOUT_BITS, rows=None):
+        """rows: tile rows (a power of two); None takes the autotuned table's
+        choice for this (d, density) if one is installed (tile_table.json),
+        else the library default."""
         scope = np.ascontiguousarray(scope, dtype=np.int32).reshape(-1, 2)
         rel = np.ascontiguousarray(rel, dtype=np.uint32).reshape(-1, d)
         if rel.shape[0] != scope.shape[0]:
             raise RacError(EINVAL, "scope and rel disagree on the number of constraints")
+        if rows is None and not (int(layout) & 0xF00):
+            from .autotune import table_rows
+            rows = table_rows(int(d), scope.shape[0] / max(1.0, n * (n - 1) / 2.0))
+        if rows is not None:
+            rows = int(rows)
+            if rows < 2 or rows > 32 or rows & (rows - 1):
+                raise RacError(EINVAL, "tile rows must be a power of two in [2, 32]")
+            layout = int(layout) | LAYOUT_ROWS(rows.bit_length() - 1)
         h = ctypes.c_void_p()
         _check(lib().rac_create_network(int(n), int(d), scope.shape[0], scope.ctypes.data,
                                         rel.ctypes.data, int(layout), ctypes.byref(h)),

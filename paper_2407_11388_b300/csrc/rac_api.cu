@@ -194,7 +194,7 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
     set_error("n_cons < 0 or NULL scope / rel_bits");
     return RAC_EINVAL;
   }
-  if (layout_flags & ~RAC_LAYOUT_BITS) {
+  if (layout_flags & ~(RAC_LAYOUT_BITS | RAC_LAYOUT_ROWS_MASK)) {
     set_error("unknown layout flag");
     return RAC_EINVAL;
   }
@@ -202,7 +202,21 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
   const int nb = (n_vars + 31) / 32;
   const int dp = (d + 3) & ~3;
   const int q = dp / 4;
-  const int rows = rows_per_slab_for(dp);
+  int rows = rows_per_slab_for(dp);
+  if (const uint32_t code = (layout_flags & RAC_LAYOUT_ROWS_MASK) >> 8) {
+    if (code < 2 || code > 6) {
+      // l = 0 would give a 2-word tile header: relations and tile sizes that
+      // are not multiples of the 16 bytes a bulk copy moves
+      set_error("RAC_LAYOUT_ROWS(l) takes 1 <= l <= 5");
+      return RAC_EINVAL;
+    }
+    rows = 1 << (code - 1);
+    if (size_t(rows) * 32 * dp * 4 > size_t(kSlabRelBytes)) {
+      set_error("a tile of " + std::to_string(rows) + " rows of width " + std::to_string(d) +
+                " does not fit the 32 KiB staging buffer");
+      return RAC_EINVAL;
+    }
+  }
 
   // orient every constraint as (lo, hi) and sort by (I, J, i, j)
   std::vector<std::pair<uint64_t, int64_t>> order;
@@ -241,7 +255,7 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
   std::vector<SlabDesc> slabs;
   std::vector<float2> slab_feat;  // tightness, density
   std::vector<uint32_t> relw;
-  const size_t hdr = size_t(2) * rows;  // pm[rows] + roff[rows], a multiple of 4 words
+  const size_t hdr = size_t(2) * rows;  // pm[rows] + roff[rows], a multiple of 4 words (rows >= 2)
   try {
     size_t i = 0;
     while (i < order.size()) {

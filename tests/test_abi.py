@@ -45,7 +45,8 @@ def _create(L, n, d, scope, rel, flags=1):
 
 
 @pytest.mark.parametrize("case", ["d0", "d33", "n0", "self_loop", "out_of_range", "dup_pair",
-                                  "dup_pair_reversed", "bit_above_d", "bad_layout"])
+                                  "dup_pair_reversed", "bit_above_d", "bad_layout",
+                                  "bad_rows_code"])
 def test_create_rejects(L, case):
     n, d = 4, 3
     scope = np.array([[0, 1], [1, 2]], np.int32)
@@ -68,7 +69,9 @@ def test_create_rejects(L, case):
     elif case == "bit_above_d":
         rel[1, 2] = 8
     elif case == "bad_layout":
-        flags = 0x100
+        flags = 0x1000
+    elif case == "bad_rows_code":
+        flags = 1 | (7 << 8)  # RAC_LAYOUT_ROWS takes l <= 5
     rc, h = _create(L, n, d, scope, rel.reshape(2, -1) if d == 3 else np.zeros((2, max(d, 1)), np.uint32), flags)
     assert rc == rac.EINVAL
     assert h.value is None
@@ -113,3 +116,18 @@ def test_trace_struct_matches_header():
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = re.findall(r"\*?\s*(\w+);", body)
     assert fields == [f[0] for f in rac.RacTrace._fields_]
+
+
+def test_tile_rows_too_large_rejected(L):
+    # 16 rows x 32 columns x 32 words x 4 bytes = 64 KiB > the 32 KiB staging buffer
+    rc, h = _create(L, 4, 32, np.array([[0, 1]], np.int32), np.zeros((1, 32), np.uint32),
+                    flags=1 | (5 << 8))
+    assert rc == rac.EINVAL and h.value is None
+    assert "staging buffer" in L.rac_last_error().decode()
+    # one row would leave the tile header (2 x rows words) unaligned
+    rc, h = _create(L, 4, 8, np.array([[0, 1]], np.int32), np.zeros((1, 8), np.uint32),
+                    flags=1 | (1 << 8))
+    assert rc == rac.EINVAL and h.value is None
+    for rows in (1, 3, 64):
+        with pytest.raises(rac.RacError):
+            rac.Network(4, 8, np.array([[0, 1]], np.int32), np.zeros((1, 8), np.uint32), rows=rows)

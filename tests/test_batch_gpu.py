@@ -128,3 +128,32 @@ def test_plan_in_cuda_graph():
         T.cuda.synchronize()
         got = (from_dev(dout), it.cpu().numpy(), st.cpu().numpy())
     _check(nets_np, items, offs, doms, got, 0)
+
+
+@pytest.mark.parametrize("rows", [2, 4, 8, 16, 32])
+def test_tile_rows_do_not_change_results(rows):
+    """Every admissible tile row count (RAC_LAYOUT_ROWS) gives the oracle's
+    domains, sweep counts and statuses: single-network launches, the
+    Proposition-2 flag and the multi-network launch."""
+    from paper_2407_11388_b300.autotune import admissible_rows
+
+    def shape(i):
+        return (40 + 37 * i, [5, 8, 12, 16, 20, 24, 32][i % 7], 0.7, [0.25, 0.3, 0.35][i % 3])
+    nets_np, items, offs, doms, flat = _batch(13, 7, 4, shape=shape)
+    nets = [rac.Network(x.n, x.d, x.scope, x.rel,
+                        rows=rows if rows in admissible_rows(x.d) else None)
+            for x in nets_np]
+    for x, net in zip(nets_np, nets):
+        want = rows if rows in admissible_rows(x.d) else None
+        if want is not None:
+            assert net.info()["rows_per_slab"] == want
+    for flags in (0, rac.INCREMENTAL):
+        got = _run(nets, items, offs, flat, flags)
+        _check(nets_np, items, offs, doms, got, flags)
+        for i in range(len(nets)):  # one network per launch
+            sel = np.flatnonzero(items == i)
+            got1 = _run([nets[i]], np.zeros(sel.size, np.int32), offs[sel], flat, flags)
+            for a, j in enumerate(sel):
+                n = nets_np[i].n
+                assert np.array_equal(got1[0][offs[j]:offs[j] + n], got[0][offs[j]:offs[j] + n])
+                assert got1[1][a] == got[1][j] and got1[2][a] == got[2][j]
