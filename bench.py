@@ -44,6 +44,11 @@ WORKLOADS = {
                           n_states=64),
     "n1000_d24_b128": dict(n=1000, d=24, density=0.8, tightness=0.3, states="assign",
                            n_states=128),
+    # the same network and states with learned active-block gating: the
+    # predictor is trained first (GPU traces of the n=500/2000 dense and batch
+    # generators, other seeds), then the gated enforcement is timed
+    "learned_n1000_d24_b32": dict(n=1000, d=24, density=0.8, tightness=0.3, states="assign",
+                                  n_states=32, learned=True),
     # 256 networks, n ~ U{50..800}, d ~ U{8..32}, density ~ U[0.3,1],
     # tightness ~ U[0.2,0.4], 64 assignment states each: one launch per step
     "batch256_x64": dict(batch=True, networks=256, states_per_net=64),
@@ -323,6 +328,37 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def train_predictor(rac, torch, seed, recall=0.995, log=None):
+    """The active-block predictor trained on the GPU from Proposition-2 traces
+    of other networks: the n=500 d=20 and n=2000 d=32 dense generators and the
+    batch generator (assignment states, seeds disjoint from the workload's).
+    Returns (predictor, logit threshold, training summary)."""
+    import racgen
+    from paper_2407_11388_b300 import learned
+    t0 = time.perf_counter()
+    specs = [(seed + 1000, 0, 500, 20, 1.0, 0.35, 32), (seed + 1000, 1, 500, 20, 1.0, 0.35, 32),
+             (seed + 1000, 0, 2000, 32, 0.9, 0.3, 16)]
+    specs += [(seed + 1000, i) + tuple(racgen.batch_params(seed + 1000, i)) + (16,)
+              for i in range(12)]
+    items, keep = [], []
+    for sd, inst, n, d, p, t, B in specs:
+        x = racgen.random_network(sd, inst, n, d, p, t)
+        doms = np.array([racgen.assignment_state(sd, inst, s, n, d) for s in range(B)], np.uint32)
+        net = rac.Network(x.n, x.d, x.scope, x.rel)
+        keep.append(net)
+        items.append((net, torch.from_numpy(doms.view(np.int32)).cuda()))
+    x, y, _ = learned.collect_traces(items)
+    for net in keep:
+        net.close()
+    pred = learned.train(x, y, steps=4000, batch=4096, lr=2e-3, pos_weight=4.0, seed=seed + 1)
+    thr = learned.choose_threshold(pred, x, y, recall=recall)
+    info = {"records": int(x.shape[0]), "positive_rate": float(y.mean()), "recall_target": recall,
+            "threshold_logit": thr, "train_s": time.perf_counter() - t0,
+            "traces": "Proposition-2 sweeps of n=500 d=20 (2x32 states), n=2000 d=32 (16), "
+                      "12 batch-generator networks (16 each), seed %d" % (seed + 1000)}
+    return pred, thr, info
+
+
 class Prepared:
     """The workload resident on the device, and how one step enforces it."""
 
@@ -359,10 +395,18 @@ class Prepared:
         self.rac = rac
         self.torch = torch
         self.dev = dev
+        self.pred = None
+        if spec.get("learned"):
+            self.pred, self.thr, self.train_info = train_predictor(rac, torch, args.seed)
+            self.cfg["gating"] = "learned (rac_enforce_learned, pending-pair verification)"
 
     def step(self, flags, stream):
         rac = self.rac
-        if self.plan is not None:
+        if self.pred is not None:
+            rac.enforce_learned(self.nets[0], self.din, self.dout, self.it, self.st,
+                                predictor=self.pred, threshold=self.thr, flags=flags,
+                                stream=stream)
+        elif self.plan is not None:
             self.plan.enforce(self.din, self.dout, self.it, self.st, flags=flags, stream=stream)
         elif self.B == 1:
             rac.enforce(self.nets[0], self.din, self.dout, self.it, self.st, flags=flags,
@@ -397,6 +441,65 @@ class Prepared:
         """Relation bits of the plain recurrence: m d^2 per state per sweep."""
         return float(sum(self.nets_np[int(self.items[j])].m * self.nets_np[int(self.items[j])].d ** 2
                          * int(its[j]) for j in range(self.B)))
+
+
+def compare_learned(W, args, stream, flush, per_step_s, world):
+    """Learned gating against plain and Proposition-2 RAC on the same states:
+    the same batch through rac_enforce_batch (flags 0 and RAC_INCREMENTAL),
+    CUDA-event timed like the main loop; (slab, state) evaluations from the
+    trace counters; the learned result checked against the plain one."""
+    torch, rac = W.torch, W.rac
+    B = W.B
+    net = W.nets[0]
+    out_p = torch.empty_like(W.din)
+    it_p = torch.empty(B, dtype=torch.int32, device=W.dev)
+    st_p = torch.empty_like(it_p)
+
+    def timed(fn, reps):
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b) / 1000.0
+        return tot / reps
+
+    reps = max(3, min(20, args.steps))
+    res = {}
+    for name, fl in (("plain", 0), ("proposition2", rac.INCREMENTAL)):
+        def run(fl=fl):
+            rac.enforce_batch([net], W.items, W.offs, W.din, out_p, it_p, st_p, flags=fl,
+                              stream=stream)
+        run()
+        t = timed(run, reps)
+        res[name] = {"value": world * B / t, "unit": "fixpoints/s", "ms_per_step": t * 1000.0}
+    torch.cuda.synchronize()
+    plain_its = it_p.cpu().numpy()
+    if not (torch.equal(out_p, W.dout) and np.array_equal(st_p.cpu().numpy(), W.st.cpu().numpy())):
+        raise SystemExit("learned gating disagrees with plain RAC")
+    tr = rac.Trace(0)
+    rac.enforce_learned(net, W.din, out_p, it_p, st_p, predictor=W.pred, threshold=W.thr,
+                        trace=tr, stream=stream)
+    torch.cuda.synchronize()
+    learned_evals = tr.evaluated()
+    learned_sweeps = it_p.cpu().numpy()
+    rac.enforce_learned(net, W.din, out_p, it_p, st_p, predictor=None, trace=tr, stream=stream)
+    torch.cuda.synchronize()
+    p2_evals = tr.evaluated()
+    slabs = net.info()["n_slabs"]
+    res.update({
+        "evaluations": {"plain": int(plain_its.sum()) * slabs, "proposition2": p2_evals,
+                        "learned": learned_evals, "unit": "(slab, state) evaluations per step"},
+        "sweeps_per_fixpoint_plain": float(plain_its.mean()),
+        "sweeps_per_fixpoint_learned": float(learned_sweeps.mean()),
+        "max_sweeps": {"plain": int(plain_its.max()), "learned": int(learned_sweeps.max())},
+        "speedup_vs_plain": res["plain"]["ms_per_step"] / (per_step_s * 1000.0),
+        "speedup_vs_proposition2": res["proposition2"]["ms_per_step"] / (per_step_s * 1000.0),
+        "_plain_iterations": plain_its})
+    return res
 
 
 def run_ours(args):
@@ -448,9 +551,13 @@ def run_ours(args):
     per_step_s = dev_ms / 1000.0 / K
     value = world * B / per_step_s
 
+    learned_cmp = None
+    if W.pred is not None:
+        learned_cmp = compare_learned(W, args, stream, flush, per_step_s, world)
+        its = learned_cmp.pop("_plain_iterations")
     # plain GPU RAC on the same items (only where the step is a batch)
     plain = None
-    if B > 1:
+    if B > 1 and W.pred is None:
         pin, pout = W.din.data_ptr(), W.dout.data_ptr()
         pit = torch.empty(B, dtype=torch.int32, device=dev)
         pst = torch.empty(B, dtype=torch.int32, device=dev)
@@ -475,7 +582,7 @@ def run_ours(args):
 
     # end to end through the host entry point (copies inside the timed region)
     e2e = None
-    if not args.no_e2e and len(W.nets) == 1:
+    if not args.no_e2e and len(W.nets) == 1 and W.pred is None:
         host_in = torch.from_numpy(np.ascontiguousarray(W.flat).view(np.int32).copy()).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
         hit = torch.empty(B, dtype=torch.int32).pin_memory()
@@ -505,7 +612,8 @@ def run_ours(args):
                "h2d_bytes_per_step": int(W.flat.size * 4), "d2h_bytes_per_step": int(W.flat.size * 4 + B * 8),
                "steps": Ke}
     elif not args.no_e2e:
-        # batches: pinned host states copied in, the plan launch, results copied out
+        # batches and learned gating: pinned host states copied in, the step's
+        # launch, results copied out
         host_in = torch.from_numpy(np.ascontiguousarray(W.flat).view(np.int32).copy()).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
         hit = torch.empty(B, dtype=torch.int32).pin_memory()
@@ -549,6 +657,10 @@ def run_ours(args):
             "e2e": e2e}
     if plain is not None:
         line["plain_gpu_rac"] = plain
+    if learned_cmp is not None:
+        line["learned"] = learned_cmp
+        line["learned"]["training"] = W.train_info
+        line["sweeps_per_fixpoint"] = learned_cmp["sweeps_per_fixpoint_learned"]
     if rank == 0 and not args.no_cpu_baseline:
         cb, _ = cpu_baseline(W)
         line["cpu_baseline"] = cb
