@@ -8,10 +8,11 @@
 //
 // Work: global slab g of job (network) j; CTA c streams slabs c, c+G, ...
 // through a 6-stage bulk-copy ring (one producer thread).  Three groups of
-// four consumer warps take alternate stages; a group stages the domain words
-// its slab needs (32 column variables + the slab's rows) for 32 states at a
-// time in shared memory and gives each warp one state at a time.  The
-// relation width is dispatched at run time.
+// four consumer warps take alternate stages; the warps of a group own every
+// fourth state of the slab's job and evaluate them independently, loading a
+// state's column and row words straight into registers (the next state's
+// while the current one is evaluated).  The relation width is dispatched
+// once per slab.
 //
 // Per sweep: one barrier after the removals (its word counts the CTAs that
 // removed values), then the owners of the states (state t belongs to CTA
@@ -47,10 +48,6 @@ struct BSmem {
   uint32_t base, poisoned, abort, failed;
   uint32_t any_total, wipe_total, running_total;
   uint32_t cta_any, cta_wipe, cta_running;
-  uint32_t dom[kBGroups][kBatchChunk][kBatchStageWords];  // [0,32): columns, [32,64): rows
-  uint32_t info[kBGroups][kBatchChunk];
-  uint32_t chgJ[kBGroups][kBatchChunk], chgI[kBGroups][kBatchChunk];
-  int64_t chgoff[kBGroups][kBatchChunk];
 };
 static_assert(size_t(kBStages) * kStageBytes + sizeof(BSmem) <= 232448,
               "shared memory of the batched kernel exceeds 227 KB");
@@ -89,24 +86,26 @@ __device__ __forceinline__ BView bview(const BatchParams &P, int t, int k) {
 __device__ void batch_barrier(const BatchParams &P, unsigned long long *w,
                               unsigned long long mine, unsigned long long target_mask,
                               uint32_t G, unsigned long long &out, uint32_t &failed) {
-  // thread 0 only
-  __threadfence();
-  unsigned long long v = atomicAdd(w, mine) + mine;
+  // thread 0 only: the arrival releases this CTA's writes (the last arrival
+  // acquires everyone's); poll the barrier word alone and look at the error
+  // word and the time limit every 64 polls
+  unsigned long long v = atom_add_acq_rel_u64(w, mine) + mine;
   const uint64_t t0 = global_timer();
+  uint32_t spins = 0;
   while ((v & target_mask) < G) {
-    if (ld_acquire(&P.sync->err) != 0u) {
-      failed = 1;
-      break;
+    if ((++spins & 63u) == 0u) {
+      if (ld_acquire(&P.sync->err) != 0u) {
+        failed = 1;
+        break;
+      }
+      if (global_timer() - t0 > P.wait_limit_ns) {
+        atomicOr(&P.sync->err, kErrGridWait);
+        failed = 1;
+        break;
+      }
     }
-    if (global_timer() - t0 > P.wait_limit_ns) {
-      atomicOr(&P.sync->err, kErrGridWait);
-      failed = 1;
-      break;
-    }
-    __nanosleep(20);
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(w) : "memory");
+    v = ld_acquire_u64(w);
   }
-  __threadfence();
   out = v;
 }
 
@@ -118,21 +117,6 @@ __device__ __forceinline__ void support_dispatch_q(const uint4 *mine, uint32_t s
     support_relation<Q, true>(mine, stride, Dx, Dy, fwd, rev);
   else
     support_relation<Q, false>(mine, stride, Dx, Dy, fwd, rev);
-}
-
-__device__ __forceinline__ void support_any_q(int q, const uint4 *mine, uint32_t stride,
-                                              uint32_t Dx, uint32_t Dy, uint32_t dfull,
-                                              uint32_t &fwd, uint32_t &rev) {
-  switch (q) {
-    case 1: support_dispatch_q<1>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
-    case 2: support_dispatch_q<2>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
-    case 3: support_dispatch_q<3>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
-    case 4: support_dispatch_q<4>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
-    case 5: support_dispatch_q<5>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
-    case 6: support_dispatch_q<6>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
-    case 7: support_dispatch_q<7>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
-    default: support_dispatch_q<8>(mine, stride, Dx, Dy, dfull, fwd, rev); break;
-  }
 }
 
 __device__ __forceinline__ void batch_remove(BSmem &S, const BatchParams &P, const BatchJob &J,
@@ -151,11 +135,17 @@ __device__ __forceinline__ void batch_remove(BSmem &S, const BatchParams &P, con
     atomicOr(P.chgU + int64_t(slot_w) * P.u_slot_words + J.u_off + (v >> 5), bit);
 }
 
-// One slab of job J for every running state of J, by one consumer group.
-__device__ void batch_consume(BSmem &S, const BatchParams &P, const unsigned char *stage,
-                              const BStage &si, int k, int slot_r, int slot_w, int cg, int lw,
-                              int lane) {
-  const BatchJob J = P.jobs[si.job];
+// One slab of job J for every running state of J, by one consumer group: the
+// group's warps own the job's states s = 4 i + lw.  A warp takes its states
+// 32 at a time (lane i checks state base + 4 i: running, and with
+// RAC_INCREMENTAL a Proposition-2 candidate) and evaluates the ones that
+// need it, one after the other: each state's column words (lane = column)
+// and row words (lane = row) come in two coalesced loads, issued for the
+// next state while the current one is evaluated.
+template <int Q>
+__device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &J,
+                                const unsigned char *stage, const BStage &si, int k, int slot_r,
+                                int slot_w, int lw, int lane) {
   const int n = J.n;
   const uint32_t I = si.ij & 0xFFFFu, Jb = si.ij >> 16;
   const uint32_t row0 = si.rows & 0xFFu, nrows = si.rows >> 8;
@@ -163,70 +153,95 @@ __device__ void batch_consume(BSmem &S, const BatchParams &P, const unsigned cha
   const uint4 *rel = reinterpret_cast<const uint4 *>(stage) + (2 * nrows) / 4;
   const int y = int(Jb) * 32 + lane;
   const bool y_ok = y < n;
+  const int x_l = int(I) * 32 + int(row0) + lane;
+  const bool x_ok = lane < int(nrows) && x_l < n;
   const uint32_t dfull = J.d >= 32 ? kFull : ((1u << J.d) - 1u);
   const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
   const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
-  const int gl = lw * 32 + lane;  // thread index inside the group
-  for (int c0 = 0; c0 < J.n_states; c0 += kBatchChunk) {
-    const int cnt = min(kBatchChunk, J.n_states - c0);
-    // stage the chunk's domain words, decisions and change words
-    for (int i = gl; i < cnt * kBatchStageWords; i += kBGroupWarps * 32) {
-      const int q = i / kBatchStageWords, w = i % kBatchStageWords;
-      const int t = J.state_base + c0 + q;
-      const BView V = bview(P, t, k);
-      uint32_t val = 0u;
-      if (w < 32) {
-        const int yy = int(Jb) * 32 + w;
-        if (yy < n) val = ld_dom(V.C + yy);
-      } else if (uint32_t(w - 32) < nrows) {
-        const int xx = int(I) * 32 + int(row0) + (w - 32);
-        if (xx < n) val = ld_dom(V.C + xx);
+  for (int base = lw; base < J.n_states; base += 32 * kBGroupWarps) {
+    // lane i: state t = state_base + base + 4 i
+    const int q = base + kBGroupWarps * lane;
+    const int t = J.state_base + q;
+    bool act = false;
+    int64_t c_off = 0, t_off = 0, chgoff = 0;
+    if (q < J.n_states) {
+      act = (ld_dom(P.st_info + t) & kInfoSweepMask) == 0u;
+      chgoff = P.chg_off[t];
+      if (act && incr) {
+        const uint32_t *ch = P.chg + int64_t(slot_r) * P.chg_slot_words + chgoff;
+        act = ld_dom(ch + Jb) != 0u || (ld_dom(ch + I) & rowmask) != 0u;
       }
-      S.dom[cg][q][w] = val;
-    }
-    for (int q = gl; q < cnt; q += kBGroupWarps * 32) {
-      const int t = J.state_base + c0 + q;
-      S.info[cg][q] = ld_dom(P.st_info + t);
-      const int64_t co = P.chg_off[t];
-      S.chgoff[cg][q] = co;
-      if (incr) {
-        const uint32_t *ch = P.chg + int64_t(slot_r) * P.chg_slot_words + co;
-        S.chgJ[cg][q] = ld_dom(ch + Jb);
-        S.chgI[cg][q] = ld_dom(ch + I);
+      if (act) {
+        // the buffers of sweep k (as bview): C = D_{k-1}, T receives D_k
+        const int64_t a = P.state_off[t], b = P.scratch_off[t];
+        c_off = k == 1 ? a : ((k & 1) ? a : b);
+        t_off = (k == 1 || (k & 1)) ? b : a;
       }
     }
-    named_bar(group_bar(cg), kBGroupWarps * 32);
-    for (int q = lw; q < cnt; q += kBGroupWarps) {
-      if (S.info[cg][q] & kInfoSweepMask) continue;  // finished state
-      if (incr && S.chgJ[cg][q] == 0u && (S.chgI[cg][q] & rowmask) == 0u) continue;
-      const int t = J.state_base + c0 + q;
-      const uint32_t *Dq = S.dom[cg][q];
-      const uint32_t Dy = Dq[lane];
-      uint32_t *T = bview(P, t, k).T;
+    uint32_t am = __ballot_sync(kFull, act);
+    if (am == 0u) continue;
+    // words of the first state
+    int i = __ffs(am) - 1;
+    am &= am - 1u;
+    auto fetch = [&](int ii, uint32_t &dy, uint32_t &dx) {
+      const int64_t co = __shfl_sync(kFull, c_off, ii);
+      const uint32_t *C = (k == 1 ? P.dom_in : ((k & 1) ? P.dom_out : P.bufB)) + co;
+      dy = y_ok ? ld_dom(C + y) : 0u;
+      dx = x_ok ? ld_dom(C + x_l) : 0u;
+    };
+    uint32_t Dy, Dxl;
+    fetch(i, Dy, Dxl);
+    for (;;) {
+      const int inext = am ? __ffs(am) - 1 : -1;
+      if (inext >= 0) am &= am - 1u;
+      uint32_t Dy_n = 0u, Dx_n = 0u;
+      if (inext >= 0) fetch(inext, Dy_n, Dx_n);  // in flight during this evaluation
+      const int ts = __shfl_sync(kFull, t, i);
+      const int64_t to = __shfl_sync(kFull, t_off, i);
+      const int64_t co = __shfl_sync(kFull, chgoff, i);
+      uint32_t *T = ((k == 1 || (k & 1)) ? P.bufB : P.dom_out) + to;
       uint32_t racc = kFull;
       for (int r = 0; r < int(nrows); ++r) {
         const uint32_t pm = hdr[r];
         if (pm == 0u) continue;
-        const uint32_t Dx = Dq[32 + r];
+        const uint32_t Dx = __shfl_sync(kFull, Dxl, r);
         uint32_t fwd = kFull, rev = kFull;
         if ((pm >> lane) & 1u) {
           const uint32_t tt = __popc(pm & lanemask_lt());
-          support_any_q(J.q, rel + hdr[nrows + r] * uint32_t(J.q) + tt, __popc(pm), Dx, Dy,
-                        dfull, fwd, rev);
+          support_dispatch_q<Q>(rel + hdr[nrows + r] * uint32_t(Q) + tt, __popc(pm), Dx, Dy,
+                                dfull, fwd, rev);
         }
         const uint32_t keep_x = __reduce_and_sync(kFull, fwd) & Dx;
         if (keep_x != Dx && lane == 0) {
           const int x = int(I) * 32 + int(row0) + r;
-          batch_remove(S, P, J, t, S.chgoff[cg][q], slot_w, T, uint32_t(x), keep_x);
+          batch_remove(S, P, J, ts, co, slot_w, T, uint32_t(x), keep_x);
         }
         racc &= rev;
       }
       if (y_ok) {
         const uint32_t keep_y = racc & Dy;
-        if (keep_y != Dy) batch_remove(S, P, J, t, S.chgoff[cg][q], slot_w, T, uint32_t(y), keep_y);
+        if (keep_y != Dy) batch_remove(S, P, J, ts, co, slot_w, T, uint32_t(y), keep_y);
       }
+      if (inext < 0) break;
+      i = inext;
+      Dy = Dy_n;
+      Dxl = Dx_n;
     }
-    named_bar(group_bar(cg), kBGroupWarps * 32);
+  }
+}
+
+__device__ void batch_consume(BSmem &S, const BatchParams &P, const unsigned char *stage,
+                              const BStage &si, int k, int slot_r, int slot_w, int lw, int lane) {
+  const BatchJob J = P.jobs[si.job];
+  switch (J.q) {
+    case 1: batch_consume_q<1>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
+    case 2: batch_consume_q<2>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
+    case 3: batch_consume_q<3>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
+    case 4: batch_consume_q<4>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
+    case 5: batch_consume_q<5>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
+    case 6: batch_consume_q<6>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
+    case 7: batch_consume_q<7>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
+    default: batch_consume_q<8>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
   }
 }
 
@@ -383,7 +398,7 @@ __global__ void __launch_bounds__(kBThreads, 1) rac_batch_kernel(const BatchPara
           __syncwarp();
           const BStage si = S.stage[stg];
           if (si.job >= 0)
-            batch_consume(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_r, slot_w, cg, lw,
+            batch_consume(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_r, slot_w, lw,
                           lane);
           __syncwarp();
           if (lane == 0) mbar_arrive(&S.empty[stg]);

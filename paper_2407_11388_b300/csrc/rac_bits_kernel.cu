@@ -89,6 +89,9 @@ constexpr uint32_t kInfoSweepMask = 0xFFFFFFu;
 constexpr uint32_t kInfoResB = 1u << 24;
 constexpr uint32_t kInfoWiped = 1u << 25;
 constexpr uint32_t kInfoGated = 1u << 26;  // learned gating: the state is in its gated phase
+
+// kernel variants (see rac_bits_kernel)
+constexpr int kVarFew = 0, kVarMany = 1, kVarGated1 = 2, kVarGated2 = 3;
 __device__ __forceinline__ uint32_t info_status_bits(int st) { return uint32_t(st + 8) << 27; }
 __device__ __forceinline__ int info_status(uint32_t v) { return int((v >> 27) & 31u) - 8; }
 
@@ -169,25 +172,28 @@ __device__ void grid_barrier(Smem &S, const LaunchParams &P, int slot) {
                                     (uint64_t(S.cta_any ? 1u : 0u) << kBarCountBits) |
                                     (uint64_t(S.cta_wipe ? 1u : 0u) << (2 * kBarCountBits)) |
                                     (uint64_t(S.failed ? 1u : 0u) << (3 * kBarCountBits));
-    __threadfence();
     // test hook: CTA 0 withholds its first arrival, so every wait runs out
     const bool withhold = (P.flags & RAC_TEST_WITHHOLD_ARRIVAL) && blockIdx.x == 0;
-    unsigned long long v = withhold ? 0ull : atomicAdd(w, mine) + mine;
+    // the arrival releases this CTA's removals; the last arrival acquires all
+    unsigned long long v = withhold ? 0ull : atom_add_acq_rel_u64(w, mine) + mine;
     const uint64_t t0 = global_timer();
+    uint32_t spins = 0;
+    // poll the barrier word alone; the error word and the time limit are
+    // looked at every 64 polls (one L2 round trip each)
     while ((v & kMask) < gridDim.x) {
-      if (ld_acquire(&P.sync->err) != 0u) {
-        S.failed = 1;
-        break;
+      if ((++spins & 63u) == 0u) {
+        if (ld_acquire(&P.sync->err) != 0u) {
+          S.failed = 1;
+          break;
+        }
+        if (global_timer() - t0 > P.wait_limit_ns) {
+          atomicOr(&P.sync->err, kErrGridWait);
+          S.failed = 1;
+          break;
+        }
       }
-      if (global_timer() - t0 > P.wait_limit_ns) {
-        atomicOr(&P.sync->err, kErrGridWait);
-        S.failed = 1;
-        break;
-      }
-      __nanosleep(20);
-      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(w) : "memory");
+      v = ld_acquire_u64(w);
     }
-    __threadfence();
     S.any_total = uint32_t((v >> kBarCountBits) & kMask);
     S.wipe_total = uint32_t((v >> (2 * kBarCountBits)) & kMask);
     if ((v >> (3 * kBarCountBits)) & kMask) S.failed = 1;
@@ -195,31 +201,58 @@ __device__ void grid_barrier(Smem &S, const LaunchParams &P, int slot) {
   __syncthreads();
 }
 
+// D_{k-1} words of state s a slab's evaluation needs: the column word of
+// this lane (Dy) and the row word of this lane (Dxl, lane < slab rows), read
+// in two coalesced loads (sweep 1: the input domains, with a search
+// assignment applied).
+__device__ __forceinline__ void load_words(const Smem &S, const LaunchParams &P, int s, int k,
+                                           bool cached, int y, bool y_ok, int x_l, bool x_ok,
+                                           uint32_t &Dy, uint32_t &Dxl) {
+  const int n = P.net.n;
+  const uint32_t *Dc = cached ? S.dom + s * n : state_view(P, s, k).C;
+  Dy = y_ok ? (cached ? Dc[y] : ld_dom(Dc + y)) : 0u;
+  Dxl = x_ok ? (cached ? Dc[x_l] : ld_dom(Dc + x_l)) : 0u;
+  if (k == 1 && !cached) {  // the cached copy has the assignment applied already
+    Dy = input_word(P, y, Dy);
+    Dxl = input_word(P, x_l, Dxl);
+  }
+}
+
 // Evaluate one state on one slab: the support step of Eq. 1 restricted to the
-// slab's constraints, with its removals applied to D_k.  With kLabel, the
-// state group's first warp (sub == 0) gets back whether the evaluation
-// removed a value.
-template <int Q, bool kLabel>
+// slab's constraints, with its removals applied to D_k.  With kPre, Dy / Dxl
+// are the state's words from load_words and a row's word is taken from lane
+// r; without, every row reads its word when it gets to it (the shorter path
+// when a state's rows are split over several warps).  With kLabel, the state
+// group's first warp (sub == 0) gets back whether the evaluation removed a
+// value.
+template <int Q, bool kLabel, bool kPre>
 __device__ __forceinline__ bool eval_state(Smem &S, const LaunchParams &P, int s, int k,
                                            int slot_w, const uint32_t *hdr, const uint4 *rel,
                                            uint32_t I, uint32_t row0, uint32_t nrows, int y,
-                                           bool y_ok, bool cached, int warp, int lane, int cg,
-                                           int g, int sub, int wps, uint32_t &red_iter) {
+                                           bool y_ok, bool cached, uint32_t Dy, uint32_t Dxl,
+                                           int warp, int lane, int cg, int g, int sub, int wps,
+                                           uint32_t &red_iter) {
   const NetDev &N = P.net;
-  const int n = N.n;
   const uint32_t dfull = N.d >= 32 ? kFull : ((1u << N.d) - 1u);
   const StateView V = state_view(P, s, k);
-  const uint32_t *Dc = cached ? S.dom + s * n : V.C;
-  uint32_t Dy = y_ok ? (cached ? Dc[y] : ld_dom(Dc + y)) : 0u;
-  if (k == 1 && !cached) Dy = input_word(P, y, Dy);
+  const uint32_t *Dc = cached ? S.dom + s * N.n : V.C;
+  if (!kPre) {
+    Dy = y_ok ? (cached ? Dc[y] : ld_dom(Dc + y)) : 0u;
+    if (k == 1 && !cached) Dy = input_word(P, y, Dy);
+  }
   uint32_t racc = kFull;
   bool rem = false;
   for (int r = sub; r < int(nrows); r += wps) {
     const uint32_t pm = hdr[r];
     if (pm == 0u) continue;
     const int x = int(I) * 32 + int(row0) + r;
-    uint32_t Dx = cached ? Dc[x] : ld_dom(Dc + x);
-    if (k == 1 && !cached) Dx = input_word(P, x, Dx);
+    uint32_t Dx;
+    if (kPre) {
+      Dx = __shfl_sync(kFull, Dxl, r);
+    } else {
+      Dx = cached ? Dc[x] : ld_dom(Dc + x);
+      if (k == 1 && !cached) Dx = input_word(P, x, Dx);
+    }
     uint32_t fwd = kFull, rev = kFull;
     if ((pm >> lane) & 1u) {
       // this lane's relation: rank t in the row, chunk c at c * cnt + t
@@ -414,8 +447,11 @@ __device__ void consume_slab_gated(Smem &S, const LaunchParams &P, const uint32_
     for (uint32_t m = ev_mask; m; m &= m - 1u) {
       const int i = __ffs(m) - 1;
       const int s = c0 + groups * i;
-      const bool removed = eval_state<Q, true>(S, P, s, k, slot_w, hdr, rel, I, row0, nrows, y,
-                                               y_ok, cached, warp, lane, cg, g, sub, wps, red_iter);
+      uint32_t Dy, Dxl;
+      load_words(S, P, s, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
+      const bool removed = eval_state<Q, true, true>(S, P, s, k, slot_w, hdr, rel, I, row0,
+                                                     nrows, y, y_ok, cached, Dy, Dxl, warp, lane,
+                                                     cg, g, sub, wps, red_iter);
       if (recording && sub == 0) {
         const int64_t r = __shfl_sync(kFull, rec, i);
         if (lane == 0 && r >= 0) P.tr_y[r] = removed ? 1.0f : 0.0f;
@@ -424,7 +460,7 @@ __device__ void consume_slab_gated(Smem &S, const LaunchParams &P, const uint32_
   }
 }
 
-template <int Q, int kGate>
+template <int Q, int kVar>
 __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char *stage,
                              const StageInfo &si, int k, int slot_r, int slot_w, int warp,
                              int lane, uint32_t &red_iter) {
@@ -446,27 +482,67 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
   const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
   const bool cached = S.dom_cached != 0;
   if (k == 1 && P.seed_var >= 0 && !slab_touches_seed(P, I, J, row0, nrows)) return;
-  if constexpr (kGate > 0) {
-    consume_slab_gated<Q, kGate>(S, P, hdr, rel, si, k, slot_r, slot_w, warp, lane, cg, g, sub,
-                                 wps, groups, red_iter);
-    return;
-  }
-  for (int s = g; s < P.n_states; s += groups) {
-    if (S.st_info[s] & kInfoSweepMask) continue;  // finished state
-    if (incr) {
-      const uint32_t *ch = P.chg + (int64_t(slot_r) * P.flag_stride + s) * N.nb;
-      if (ld_dom(ch + J) == 0u && (ld_dom(ch + I) & rowmask) == 0u) continue;
+  if constexpr (kVar >= kVarGated1) {
+    consume_slab_gated<Q, kVar - kVarGated1 + 1>(S, P, hdr, rel, si, k, slot_r, slot_w, warp,
+                                                 lane, cg, g, sub, wps, groups, red_iter);
+  } else if constexpr (kVar == kVarFew) {
+    // one to three states, each split over several warps: a short loop
+    for (int s = g; s < P.n_states; s += groups) {
+      if (S.st_info[s] & kInfoSweepMask) continue;  // finished state
+      if (incr) {
+        const uint32_t *ch = P.chg + (int64_t(slot_r) * P.flag_stride + s) * N.nb;
+        if (ld_dom(ch + J) == 0u && (ld_dom(ch + I) & rowmask) == 0u) continue;
+      }
+      eval_state<Q, false, false>(S, P, s, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, cached,
+                                  0u, 0u, warp, lane, cg, g, sub, wps, red_iter);
     }
-    eval_state<Q, false>(S, P, s, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, cached, warp,
-                         lane, cg, g, sub, wps, red_iter);
+  } else {
+    const int x_l = int(I) * 32 + int(row0) + lane;
+    const bool x_ok = lane < int(nrows) && x_l < n;
+    // one warp per state (four or more states): the warp's states, 32 at a
+    // time (lane i checks state c0 + groups * i: running, and with
+    // RAC_INCREMENTAL a Proposition-2 candidate); the words of the next
+    // state are loaded while the current one is evaluated
+    for (int c0 = g; c0 < P.n_states; c0 += 32 * groups) {
+      const int s_l = c0 + groups * lane;
+      bool act = s_l < P.n_states && !(S.st_info[s_l] & kInfoSweepMask);
+      if (act && incr) {
+        const uint32_t *ch = P.chg + (int64_t(slot_r) * P.flag_stride + s_l) * N.nb;
+        act = ld_dom(ch + J) != 0u || (ld_dom(ch + I) & rowmask) != 0u;
+      }
+      uint32_t am = __ballot_sync(kFull, act);
+      if (am == 0u) continue;
+      int i = __ffs(am) - 1;
+      am &= am - 1u;
+      uint32_t Dy, Dxl;
+      load_words(S, P, c0 + groups * i, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
+      for (;;) {
+        const int inext = am ? __ffs(am) - 1 : -1;
+        if (inext >= 0) am &= am - 1u;
+        uint32_t Dy_n = 0u, Dx_n = 0u;
+        if (inext >= 0)
+          load_words(S, P, c0 + groups * inext, k, cached, y, y_ok, x_l, x_ok, Dy_n, Dx_n);
+        eval_state<Q, false, true>(S, P, c0 + groups * i, k, slot_w, hdr, rel, I, row0, nrows, y,
+                                   y_ok, cached, Dy, Dxl, warp, lane, cg, g, sub, wps, red_iter);
+        if (inext < 0) break;
+        i = inext;
+        Dy = Dy_n;
+        Dxl = Dx_n;
+      }
+    }
   }
 }
 
-// kGate: 0 the plain variant; 1 or 2 the variant of rac_enforce_learned
-// (learned gating and/or trace records) whose warp-wide MLP scores 16 or 32
-// states of a warp at a time (one or two MMA M tiles).
-template <int Q, int kGate>
+// kVar: the plain variants for one to three states (kVarFew: a state's rows
+// split over several warps) and for four or more (kVarMany: a warp per
+// state, words prefetched), and the variants of rac_enforce_learned (learned
+// gating and/or trace records) whose warp-wide MLP scores 16 or 32 states of
+// a warp at a time (one or two MMA M tiles).  Separate kernels keep each
+// one's instruction footprint small: a launch after an L2 flush fetches its
+// code from HBM.
+template <int Q, int kVar>
 __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParams P) {
+  constexpr int kGate = kVar >= kVarGated1 ? 1 : 0;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *ring = smem_raw;
   Smem &S = *reinterpret_cast<Smem *>(smem_raw + size_t(kStages) * kStageBytes);
@@ -674,7 +750,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
           __syncwarp();
           const StageInfo si = S.stage[stg];
           if (si.sl >= 0)
-            consume_slab<Q, kGate>(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_r, slot_w, warp,
+            consume_slab<Q, kVar>(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_r, slot_w, warp,
                             lane, red_iter);
           __syncwarp();
           if (lane == 0) mbar_arrive(&S.empty[stg]);
@@ -790,7 +866,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
   }
 }
 
-template <int Q, int kGate>
+template <int Q, int kVar>
 rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
   static int grid = 0;
   static int dev_cached = -1;
@@ -799,11 +875,11 @@ rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (grid == 0 || dev_cached != dev) {
-    e = cudaFuncSetAttribute(rac_bits_kernel<Q, kGate>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(rac_bits_kernel<Q, kVar>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(smem));
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rac_bits_kernel<Q, kGate>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rac_bits_kernel<Q, kVar>, kThreads, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
@@ -824,22 +900,22 @@ rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, rac_bits_kernel<Q, kGate>, P);
+  e = cudaLaunchKernelEx(&cfg, rac_bits_kernel<Q, kVar>, P);
   if (e != cudaSuccess) return cuda_fail(e, "launch of the bit-packed kernel");
   return RAC_OK;
 }
 
-template <int kGate>
+template <int kVar>
 rac_status launch_width(const LaunchParams &P, cudaStream_t stream) {
   switch (P.net.q) {
-    case 1: return launch_q<1, kGate>(P, stream);
-    case 2: return launch_q<2, kGate>(P, stream);
-    case 3: return launch_q<3, kGate>(P, stream);
-    case 4: return launch_q<4, kGate>(P, stream);
-    case 5: return launch_q<5, kGate>(P, stream);
-    case 6: return launch_q<6, kGate>(P, stream);
-    case 7: return launch_q<7, kGate>(P, stream);
-    case 8: return launch_q<8, kGate>(P, stream);
+    case 1: return launch_q<1, kVar>(P, stream);
+    case 2: return launch_q<2, kVar>(P, stream);
+    case 3: return launch_q<3, kVar>(P, stream);
+    case 4: return launch_q<4, kVar>(P, stream);
+    case 5: return launch_q<5, kVar>(P, stream);
+    case 6: return launch_q<6, kVar>(P, stream);
+    case 7: return launch_q<7, kVar>(P, stream);
+    case 8: return launch_q<8, kVar>(P, stream);
     default: set_error("unsupported relation width"); return RAC_EINVAL;
   }
 }
@@ -848,10 +924,12 @@ rac_status launch_width(const LaunchParams &P, cudaStream_t stream) {
 
 rac_status launch_bits(const LaunchParams &P, cudaStream_t stream) {
   const bool gate = P.mlp != nullptr || P.tr_count != nullptr || P.tr_evals != nullptr;
-  if (!gate) return launch_width<0>(P, stream);
+  if (!gate) return P.n_states < 4 ? launch_width<kVarFew>(P, stream)
+                                   : launch_width<kVarMany>(P, stream);
   // a warp scores the states g, g + 4, ... of a 32-lane chunk: at most 16 of
   // them while there are at most 64 states
-  return P.n_states <= 64 ? launch_width<1>(P, stream) : launch_width<2>(P, stream);
+  return P.n_states <= 64 ? launch_width<kVarGated1>(P, stream)
+                          : launch_width<kVarGated2>(P, stream);
 }
 
 }  // namespace rac

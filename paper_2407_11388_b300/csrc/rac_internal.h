@@ -165,8 +165,6 @@ struct BatchSync {
   uint32_t err;
 };
 
-constexpr int kBatchChunk = 32;      // states staged together per slab
-constexpr int kBatchStageWords = 64; // domain words staged per state (<= 32 rows + 32 columns)
 
 struct BatchParams {
   const BatchJob *jobs;
