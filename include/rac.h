@@ -403,6 +403,11 @@ typedef struct rac_trace {
  *             mode used to record training traces.
  *  threshold  a candidate of a gated sweep is evaluated iff its logit >
  *             threshold.
+ *  min_scored the states are scored 32 at a time per slab; a 32-state group
+ *             with fewer than min_scored gated candidates on a slab is not
+ *             scored and all its candidates are evaluated (the predictor's
+ *             cost per slab would exceed what it can save).  <= 1: always
+ *             score.
  *  sweeps     DEVICE, n_states int32: sweeps executed.
  *  status     DEVICE, n_states int32: as rac_enforce (identical values).
  *  max_sweeps, stream: as rac_enforce.  flags: RAC_STOP_ON_WIPEOUT (the
@@ -416,7 +421,8 @@ RAC_API rac_status rac_enforce_learned(const rac_network *net, int32_t n_states,
                                        const uint32_t *dom_in, uint32_t *dom_out, int32_t *sweeps,
                                        int32_t *status, int32_t max_sweeps, uint32_t flags,
                                        const rac_predictor *pred, float threshold,
-                                       const rac_trace *trace, rac_stream_t stream);
+                                       int32_t min_scored, const rac_trace *trace,
+                                       rac_stream_t stream);
 
 /*
  * rac_network_info -- describe a network: writes up to n_info int64 values

@@ -114,7 +114,7 @@ def lib():
         L.rac_predictor_predict.restype = i32
         L.rac_predictor_predict.argtypes = [vp, vp, i64, vp, i32]
         L.rac_enforce_learned.restype = i32
-        L.rac_enforce_learned.argtypes = [vp, i32, vp, vp, vp, vp, i32, u32, vp, f32,
+        L.rac_enforce_learned.argtypes = [vp, i32, vp, vp, vp, vp, i32, u32, vp, f32, i32,
                                           ctypes.POINTER(RacTrace), vp]
         _lib = L
     return _lib
@@ -410,17 +410,20 @@ class Trace:
 
 
 def enforce_learned(net, dom_in, dom_out, sweeps, status, predictor=None, threshold=0.0,
-                    trace=None, max_sweeps=0, flags=0, n_states=None, stream=None):
+                    trace=None, max_sweeps=0, flags=0, n_states=None, stream=None,
+                    min_scored=0):
     """rac_enforce_learned: states s at word s * n of dom_in / dom_out, with
     learned gating (predictor) or, with predictor=None, Proposition-2 sweeps
-    (the mode that records training traces).  Asynchronous on `stream`."""
+    (the mode that records training traces).  min_scored: a 32-state group
+    of a slab with fewer gated candidates is evaluated unscored.
+    Asynchronous on `stream`."""
     if n_states is None:
         n_states = dom_in.numel() // net.n
     tr = trace.struct() if trace is not None else None
     _check(lib().rac_enforce_learned(net.handle, int(n_states), _ptr(dom_in), _ptr(dom_out),
                                      _ptr(sweeps), _ptr(status), int(max_sweeps), int(flags),
                                      predictor.handle if predictor is not None else None,
-                                     float(threshold),
+                                     float(threshold), int(min_scored),
                                      ctypes.byref(tr) if tr is not None else None,
                                      _stream(stream)),
            "rac_enforce_learned")

@@ -610,7 +610,8 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
 rac_status rac_enforce_learned(const rac_network *net, int32_t n_states, const uint32_t *dom_in,
                                uint32_t *dom_out, int32_t *sweeps, int32_t *status,
                                int32_t max_sweeps, uint32_t flags, const rac_predictor *pred,
-                               float threshold, const rac_trace *trace, rac_stream_t stream) {
+                               float threshold, int32_t min_scored, const rac_trace *trace,
+                               rac_stream_t stream) {
   set_error("");
   if (!net || n_states < 0) {
     set_error("NULL network or negative state count");
@@ -674,6 +675,7 @@ rac_status rac_enforce_learned(const rac_network *net, int32_t n_states, const u
     P.status = status + base;
     P.mlp = pred ? predictor_pack(pred) : nullptr;
     P.mlp_thr = threshold;
+    P.mlp_min_scored = min_scored;
     if (pred && !(flags & RAC_VERIFY_FULL)) {
       P.pend = w->pend;
       P.pend_slab = w->pend_slab;

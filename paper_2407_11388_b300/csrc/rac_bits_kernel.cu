@@ -47,6 +47,7 @@ struct StageInfo {
 struct Smem {
   uint64_t full[kStages];
   uint64_t empty[kStages];
+  uint64_t issued[kStages];  // gated variants: the stage's slab is known (scorer may start)
   StageInfo stage[kStages];
   uint32_t stage_ok[kStages];
   uint32_t base;        // barrier k uses slot (base + k) % 3
@@ -71,14 +72,23 @@ struct Smem {
   alignas(16) uint32_t dom[kDomWords];
 };
 constexpr int kMlpSmemWords = kPackVec4 * 4;
-static_assert(kMlpSmemWords < kDomWords && (kDomWords - kMlpSmemWords) % 4 == 0,
-              "the packed weights fit at the 16-byte aligned end of the domain cache");
+// gated variants: per ring stage, the producer's decisions for the slab in it
+// -- ev[32] (states to evaluate), need[32] (states with a trace record),
+// rec_lo[32], rec_hi[32] (first record index of each 32-state chunk)
+constexpr int kDecWords = 128;
+constexpr int kDecBase = kDomWords - kMlpSmemWords - kStages * kDecWords;
+static_assert(kDecBase > 0 && kDecBase % 4 == 0 && (kDomWords - kMlpSmemWords) % 4 == 0,
+              "weights and stage decisions fit 16-byte aligned at the end of the domain cache");
+static_assert(kMaxStatesPerLaunch <= 32 * 32, "one decision word per 32 states");
 __device__ __forceinline__ const uint4 *smem_mlp(const Smem &S) {
   return reinterpret_cast<const uint4 *>(S.dom + (kDomWords - kMlpSmemWords));
 }
+__device__ __forceinline__ uint32_t *stage_dec(Smem &S, int stg) {
+  return S.dom + kDecBase + stg * kDecWords;
+}
 // domain words the cache holds in the given variant
 template <int kGate>
-constexpr int dom_cache_words() { return kGate > 0 ? kDomWords - kMlpSmemWords : kDomWords; }
+constexpr int dom_cache_words() { return kGate > 0 ? kDecBase : kDomWords; }
 static_assert(kStages % kGroups == 0, "each ring stage belongs to one consumer group");
 static_assert(size_t(kStages) * kStageBytes + sizeof(Smem) <= 232448,
               "shared memory of the bit-packed kernel exceeds 227 KB");
@@ -92,6 +102,12 @@ constexpr uint32_t kInfoGated = 1u << 26;  // learned gating: the state is in it
 
 // kernel variants (see rac_bits_kernel)
 constexpr int kVarFew = 0, kVarMany = 1, kVarGated1 = 2, kVarGated2 = 3;
+// the gated variants add one scorer warp per consumer group (16 warps: at most
+// 4 per SM sub-partition, so the 128 registers per thread still fit)
+constexpr int kScorerWarps = kGroups;
+constexpr int threads_for(int var) {
+  return var >= kVarGated1 ? kThreads + kScorerWarps * 32 : kThreads;
+}
 __device__ __forceinline__ uint32_t info_status_bits(int st) { return uint32_t(st + 8) << 27; }
 __device__ __forceinline__ int info_status(uint32_t v) { return int((v >> 27) & 31u) - 8; }
 
@@ -295,39 +311,34 @@ __device__ __forceinline__ bool eval_state(Smem &S, const LaunchParams &P, int s
   return rem;
 }
 
-// The sweeps of rac_enforce_learned (every sweep; the first one counts a
-// variable as changed when its input domain is not full).  The states of this
-// warp's state group are taken 32 at a time (lane i <-> state c0 + groups *
-// i).  Per chunk: the Proposition-2 test (a variable of the slab's rows or
-// columns changed in sweep k-1), the predictor's features and -- for states
-// in their gated phase -- its logit (one warp-wide tensor-core MLP for the
-// chunk), then the evaluations the decision keeps, the pending flags and the
-// optional trace records.
-template <int Q, int kMT>
-__device__ void consume_slab_gated(Smem &S, const LaunchParams &P, const uint32_t *hdr,
-                                   const uint4 *rel, const StageInfo &si, int k, int slot_r,
-                                   int slot_w, int warp, int lane, int cg, int g, int sub,
-                                   int wps, int groups, uint32_t &red_iter) {
+// The decisions of rac_enforce_learned for the slab in ring stage `stg`,
+// taken by the producer warp right after it issued the slab's copy, so that
+// they run ahead of the consumers (every sweep; the first one counts a
+// variable as changed when its input domain is not full).  Lane i stands for
+// state c0 + i of each 32-state chunk: the Proposition-2 test (a variable of
+// the slab's rows or columns changed in sweep k-1), the predictor's features
+// (D_{k-1} read from global memory: the shared-memory copy of the consumers
+// is still being filled), for states in their gated phase the logit (one
+// tensor-core MLP pass per chunk), the decision, the pending flag and the
+// optional trace record.  The decision words land in stage_dec(S, stg).
+template <int kMT>
+__device__ void score_stage(Smem &S, const LaunchParams &P, int stg, int sl, uint32_t ij,
+                            uint32_t rows, int k, int slot_r, int lane) {
   const NetDev &N = P.net;
   const int n = N.n, B = P.n_states;
-  const uint32_t I = si.ij & 0xFFFFu, J = si.ij >> 16;
-  const uint32_t row0 = si.rows & 0xFFu, nrows = si.rows >> 8;
+  const uint32_t I = ij & 0xFFFFu, J = ij >> 16;
+  const uint32_t row0 = rows & 0xFFu, nrows = rows >> 8;
   const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
   const uint32_t dfull = N.d >= 32 ? kFull : ((1u << N.d) - 1u);
-  const int y = int(J) * 32 + lane;
-  const bool y_ok = y < n;
-  const int x_l = int(I) * 32 + int(row0) + lane;
-  const bool x_ok = lane < int(nrows) && x_l < n;
-  const bool cached = S.dom_cached != 0;
-  const float2 sf = N.slab_feat[si.sl];
-  const float inv_d = 1.0f / float(N.d);
-  const float inv_rows = 1.0f / float(nrows);
-  const float inv_cols = 1.0f / float(min(32, n - int(J) * 32) * N.d);
+  const int ncols = min(32, n - int(J) * 32);
+  const int xrows = min(int(nrows), n - int(I) * 32 - int(row0));
+  const float2 sf = N.slab_feat[sl];
   const bool learned = P.mlp != nullptr;
   const bool recording = P.tr_count != nullptr;
   const bool pending_on = P.pend != nullptr;
-  for (int c0 = g; c0 < B; c0 += 32 * groups) {
-    const int s_l = c0 + groups * lane;
+  uint32_t *dec = stage_dec(S, stg);
+  for (int c0 = 0; c0 < B; c0 += 32) {
+    const int s_l = c0 + lane;
     const uint32_t info = s_l < B ? S.st_info[s_l] : 1u;  // lanes past the end look finished
     const bool valid = (info & kInfoSweepMask) == 0u;
     const bool gated = learned && (info & kInfoGated);
@@ -339,131 +350,263 @@ __device__ void consume_slab_gated(Smem &S, const LaunchParams &P, const uint32_
       cI = ld_dom(ch + I) & rowmask;
       p2 = (cI | cJ) != 0u;
     }
-    const bool need = valid && p2 && (gated || recording);
+    // a chunk with fewer than min_scored gated candidates is evaluated
+    // without scoring: the predictor's fixed cost per slab would exceed the
+    // few evaluations it could save
+    const bool scored = learned &&
+                        __popc(__ballot_sync(kFull, valid && p2 && gated)) >= P.mlp_min_scored;
+    const bool need = valid && p2 && ((gated && scored) || recording);
     const uint32_t need_mask = __ballot_sync(kFull, need);
     float f[kMlpIn];
     f[0] = float(min(k, 16)) * (1.0f / 16.0f);
-    f[1] = float(__popc(cI)) * inv_rows;
-    f[2] = float(__popc(cJ)) * (1.0f / 32.0f);
     f[3] = sf.x;
     f[4] = sf.y;
-    f[5] = f[6] = f[7] = 0.0f;
-    // domain sizes of D_{k-1} (and, in sweep 1, the variables whose input
-    // domain is not full): the warp reads the column words (lane = column)
-    // and row words (lane = row) of up to four states at a time
-    for (uint32_t m = need_mask; m;) {
-      int ii[4];
-      uint32_t wy[4], wx[4];
+    if (need) {
+      // this lane's state: its column and row words, 16 loads in flight at a time
+      const uint32_t *C = state_view(P, s_l, k).C;
+      const uint32_t *Cy = C + int(J) * 32;
+      const uint32_t *Cx = C + int(I) * 32 + int(row0);
+      uint32_t cmin = 32u, csum = 0u, rmin = 32u, nfc = 0u, nfr = 0u;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        ii[u] = m ? __ffs(m) - 1 : -1;
-        m &= m ? m - 1u : 0u;
-        wy[u] = wx[u] = dfull;
-        if (ii[u] >= 0) {
-          const int s = c0 + groups * ii[u];
-          const uint32_t *Dc = cached ? S.dom + s * n : state_view(P, s, k).C;
-          if (y_ok) wy[u] = cached ? Dc[y] : ld_dom(Dc + y);
-          if (x_ok) wx[u] = cached ? Dc[x_l] : ld_dom(Dc + x_l);
-        }
-      }
+      for (int h = 0; h < 32; h += 16) {
+        uint32_t w[16];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (ii[u] < 0) continue;
-        const uint32_t dy = uint32_t(__popc(wy[u])), dx = uint32_t(__popc(wx[u]));
-        const uint32_t cmin = __reduce_min_sync(kFull, dy);
-        const uint32_t csum = __reduce_add_sync(kFull, y_ok ? dy : 0u);
-        const uint32_t rmin = __reduce_min_sync(kFull, dx);
-        uint32_t nfc = 0u, nfr = 0u;
-        if (k == 1) {
-          nfc = __ballot_sync(kFull, wy[u] != dfull);
-          nfr = __ballot_sync(kFull, wx[u] != dfull);
-        }
-        if (lane == ii[u]) {
-          f[5] = float(cmin) * inv_d;
-          f[6] = float(csum) * inv_cols;
-          f[7] = float(rmin) * inv_d;
-          if (k == 1) {
-            f[1] = float(__popc(nfr)) * inv_rows;
-            f[2] = float(__popc(nfc)) * (1.0f / 32.0f);
+        for (int j = 0; j < 16; ++j) w[j] = h + j < ncols ? ld_dom(Cy + h + j) : dfull;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if (h + j < ncols) {
+            const uint32_t c = uint32_t(__popc(w[j]));
+            cmin = min(cmin, c);
+            csum += c;
+            nfc += w[j] != dfull ? 1u : 0u;
           }
         }
       }
-    }
-    // trace record: features and place now, decision, logit and label below
-    int64_t rec = -1;
-    if (recording && sub == 0) {
-      unsigned long long base = 0ull;
-      if (lane == 0 && need_mask != 0u) base = atomicAdd(P.tr_count, (unsigned long long)__popc(need_mask));
-      base = __shfl_sync(kFull, base, 0);
-      if (need) {
-        const int64_t r = int64_t(base) + __popc(need_mask & lanemask_lt());
-        if (r < P.tr_cap) {
-          rec = r;
 #pragma unroll
-          for (int j = 0; j < kMlpIn; ++j) P.tr_x[r * kMlpIn + j] = f[j];
-          int32_t *w = P.tr_w + r * 4;
-          w[0] = k | (gated ? (1 << 30) : 0);
-          w[1] = P.tr_state_base + s_l;
-          w[2] = int32_t(si.ij);
-          w[3] = int32_t(si.rows);
+      for (int h = 0; h < 32; h += 16) {
+        if (h >= xrows) break;
+        uint32_t w[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) w[j] = h + j < xrows ? ld_dom(Cx + h + j) : dfull;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if (h + j < xrows) {
+            rmin = min(rmin, uint32_t(__popc(w[j])));
+            nfr += w[j] != dfull ? 1u : 0u;
+          }
         }
       }
+      // sweep 1: a variable counts as changed when its input domain is not full
+      f[1] = float(k == 1 ? nfr : uint32_t(__popc(cI))) / float(nrows);
+      f[2] = float(k == 1 ? nfc : uint32_t(__popc(cJ))) * (1.0f / 32.0f);
+      f[5] = float(cmin) / float(N.d);
+      f[6] = float(csum) / float(ncols * N.d);
+      f[7] = float(rmin) / float(N.d);
+    } else {
+      f[1] = f[2] = f[5] = f[6] = f[7] = 0.0f;
     }
     float z = __int_as_float(0x7FC00000);  // NaN: not scored
-    if (learned && need_mask != 0u) z = mlp_warp_logits_mt<kMT>(smem_mlp(S), f);
-    // pending pairs (learned gating without RAC_VERIFY_FULL)
-    uint8_t *pd_ptr = pending_on ? P.pend + int64_t(si.sl) * P.flag_stride + s_l : nullptr;
+    if (scored && need_mask != 0u) z = mlp_warp_logits_mt<kMT>(smem_mlp(S), f);
+    uint8_t *pd_ptr = pending_on ? P.pend + int64_t(sl) * P.flag_stride + s_l : nullptr;
     const bool pd = pending_on && valid && *pd_ptr != 0;
     bool ev;
     if (!valid)
       ev = false;
     else if (!learned)
-      ev = p2;                        // Proposition 2 (sweep 1: everything)
+      ev = p2;                   // Proposition 2 (sweep 1: everything)
+    else if (gated && !scored)
+      ev = p2;                   // too few candidates to score: evaluate them all
     else if (gated)
-      ev = p2 && z > P.mlp_thr;       // the predictor's choice among the candidates
+      ev = p2 && z > P.mlp_thr;  // the predictor's choice among the candidates
     else if (pending_on)
-      ev = p2 || pd;                  // verification: candidates and pending pairs
+      ev = p2 || pd;             // verification: candidates and pending pairs
     else
-      ev = true;                      // RAC_VERIFY_FULL: every slab
+      ev = true;                 // RAC_VERIFY_FULL: every slab
     const uint32_t ev_mask = __ballot_sync(kFull, ev);
-    if (pending_on) {
+    if (pending_on && valid) {
       // a skipped candidate becomes pending; an evaluated pair is no longer
       const bool npd = !ev && (pd || (gated && p2));
-      // every warp of the state group has read the flags before they change
-      if (wps > 1) named_bar(state_group_bar(cg, g), wps * 32);
-      if (sub == 0 && valid && npd != pd) {
+      if (npd != pd) {
         *pd_ptr = npd ? 1 : 0;
         const int delta = npd ? 1 : -1;
-        atomicAdd(P.pend_slab + si.sl, delta);
+        atomicAdd(P.pend_slab + sl, delta);
         atomicAdd(P.pcount + s_l, delta);
       }
     }
-    if (rec >= 0) {
-      P.tr_y[rec] = ev ? 0.0f : -1.0f;  // an evaluated record gets its label below
-      if (P.tr_z) P.tr_z[rec] = z;
-    }
-    if (P.tr_evals && sub == 0 && lane == 0 && ev_mask != 0u)
-      atomicAdd(P.tr_evals, (unsigned long long)__popc(ev_mask));
-    for (uint32_t m = ev_mask; m; m &= m - 1u) {
-      const int i = __ffs(m) - 1;
-      const int s = c0 + groups * i;
-      uint32_t Dy, Dxl;
-      load_words(S, P, s, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
-      const bool removed = eval_state<Q, true, true>(S, P, s, k, slot_w, hdr, rel, I, row0,
-                                                     nrows, y, y_ok, cached, Dy, Dxl, warp, lane,
-                                                     cg, g, sub, wps, red_iter);
-      if (recording && sub == 0) {
-        const int64_t r = __shfl_sync(kFull, rec, i);
-        if (lane == 0 && r >= 0) P.tr_y[r] = removed ? 1.0f : 0.0f;
+    unsigned long long base = 0ull;
+    if (recording) {
+      if (lane == 0 && need_mask != 0u) base = atomicAdd(P.tr_count, (unsigned long long)__popc(need_mask));
+      base = __shfl_sync(kFull, base, 0);
+      const int64_t r = int64_t(base) + __popc(need_mask & lanemask_lt());
+      if (need && r < P.tr_cap) {
+#pragma unroll
+        for (int j = 0; j < kMlpIn; ++j) P.tr_x[r * kMlpIn + j] = f[j];
+        P.tr_y[r] = ev ? 0.0f : -1.0f;  // an evaluated record gets its label from the consumer
+        if (P.tr_z) P.tr_z[r] = z;
+        int32_t *w = P.tr_w + r * 4;
+        w[0] = k | (gated ? (1 << 30) : 0);
+        w[1] = P.tr_state_base + s_l;
+        w[2] = int32_t(ij);
+        w[3] = int32_t(rows);
       }
     }
+    if (lane == 0) {
+      if (P.tr_evals && ev_mask != 0u) atomicAdd(P.tr_evals, (unsigned long long)__popc(ev_mask));
+      const int ch = c0 >> 5;
+      dec[ch] = ev_mask;
+      dec[32 + ch] = need_mask;
+      dec[64 + ch] = uint32_t(base);
+      dec[96 + ch] = uint32_t(base >> 32);
+    }
+  }
+  __syncwarp();
+}
+
+// The consumers' side of rac_enforce_learned: the states the producer decided
+// to evaluate (stage_dec), each warp its own states as in the plain kernel,
+// the next state's words loaded during the current evaluation; evaluated
+// records get their label.
+template <int Q>
+__device__ void consume_slab_scored(Smem &S, const LaunchParams &P, const uint32_t *hdr,
+                                    const uint4 *rel, const StageInfo &si, int stg, int k,
+                                    int slot_w, int warp, int lane, int cg, int g, int sub,
+                                    int wps, int groups, uint32_t &red_iter) {
+  const NetDev &N = P.net;
+  const int n = N.n, B = P.n_states;
+  const uint32_t I = si.ij & 0xFFFFu, J = si.ij >> 16;
+  const uint32_t row0 = si.rows & 0xFFu, nrows = si.rows >> 8;
+  const int y = int(J) * 32 + lane;
+  const bool y_ok = y < n;
+  const int x_l = int(I) * 32 + int(row0) + lane;
+  const bool x_ok = lane < int(nrows) && x_l < n;
+  const bool cached = S.dom_cached != 0;
+  const bool recording = P.tr_count != nullptr;
+  const uint32_t *dec = stage_dec(S, stg);
+  for (int c0 = g; c0 < B; c0 += 32 * groups) {
+    const int s_l = c0 + groups * lane;
+    const bool ev = s_l < B && ((dec[s_l >> 5] >> (s_l & 31)) & 1u);
+    uint32_t m = __ballot_sync(kFull, ev);
+    if (m == 0u) continue;
+    int i = __ffs(m) - 1;
+    m &= m - 1u;
+    uint32_t Dy, Dxl;
+    load_words(S, P, c0 + groups * i, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
+    for (;;) {
+      const int inext = m ? __ffs(m) - 1 : -1;
+      if (inext >= 0) m &= m - 1u;
+      uint32_t Dy_n = 0u, Dx_n = 0u;
+      if (inext >= 0)
+        load_words(S, P, c0 + groups * inext, k, cached, y, y_ok, x_l, x_ok, Dy_n, Dx_n);
+      const int s = c0 + groups * i;
+      const bool removed = eval_state<Q, true, true>(S, P, s, k, slot_w, hdr, rel, I, row0, nrows,
+                                                     y, y_ok, cached, Dy, Dxl, warp, lane, cg, g,
+                                                     sub, wps, red_iter);
+      if (recording && sub == 0 && lane == 0) {
+        const uint32_t need = dec[32 + (s >> 5)];
+        if ((need >> (s & 31)) & 1u) {
+          const int64_t r = int64_t(dec[64 + (s >> 5)] | (uint64_t(dec[96 + (s >> 5)]) << 32)) +
+                            __popc(need & ((1u << (s & 31)) - 1u));
+          if (r < P.tr_cap) P.tr_y[r] = removed ? 1.0f : 0.0f;
+        }
+      }
+      if (inext < 0) break;
+      i = inext;
+      Dy = Dy_n;
+      Dxl = Dx_n;
+    }
+  }
+}
+
+// The producer warp of rac_enforce_learned: the plain producer's slab stream
+// (lane 0 issues the copies), and after each stage's slab is set an arrival
+// on the stage's `issued` barrier, so that the stage's scorer warp can take
+// the decisions while the copy is in flight.  A stage's full barrier
+// completes with the copy and the scorer's arrival.
+__device__ void produce_gated(Smem &S, const LaunchParams &P, unsigned char *ring, int k,
+                              int slot_r, int slot_c, int cta, int G, int my_slabs,
+                              uint32_t &prod_it, int lane) {
+  if (lane != 0) return;
+  const NetDev &N = P.net;
+  if (cta == 0) P.sync->bar[slot_c] = 0ull;  // last used two sweeps (or a launch) ago
+  // every slab while some state is in its full phase (RAC_VERIFY_FULL)
+  const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2 && !(P.mlp && S.load_all);
+  const uint32_t *cu = P.chgU + int64_t(slot_r) * N.nb;
+  bool ok = true;
+  // in sweep 1 the first slab may already be on its way
+  for (int j = (k == 1 && prod_it == 1) ? 1 : 0; j < my_slabs; ++j) {
+    const int sl = cta + j * G;
+    const SlabDesc sd = j < kDescCache ? S.desc[j] : N.slabs[sl];
+    if (incr) {
+      const uint32_t I = sd.ij & 0xFFFFu, J = sd.ij >> 16;
+      const uint32_t row0 = sd.rows & 0xFFu, nrows = sd.rows >> 8;
+      const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
+      if (ld_dom(cu + J) == 0u && (ld_dom(cu + I) & rowmask) == 0u &&
+          !(P.pend_slab && ld_dom(reinterpret_cast<const uint32_t *>(P.pend_slab) + sl) != 0u))
+        continue;
+    }
+    const int stg = prod_it % kStages;
+    const uint32_t par = (prod_it / kStages) & 1u;
+    if (!mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err, P.wait_limit_ns)) {
+      ok = false;
+      break;
+    }
+    S.stage[stg].sl = sl;
+    S.stage[stg].ij = sd.ij;
+    S.stage[stg].rows = sd.rows;
+    mbar_arrive(&S.issued[stg]);
+    mbar_arrive_expect_tx(&S.full[stg], sd.nbytes);
+    bulk_copy_g2s(ring + size_t(stg) * kStageBytes, N.rel + size_t(sd.rel_off16), sd.nbytes,
+                  &S.full[stg]);
+    ++prod_it;
+  }
+  // end of this sweep's slabs: one marker for each consumer group (its
+  // scorer gives the second arrival)
+  for (int e = 0; e < kGroups && ok; ++e) {
+    const int stg = prod_it % kStages;
+    const uint32_t par = (prod_it / kStages) & 1u;
+    if (!mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err, P.wait_limit_ns)) {
+      ok = false;
+      break;
+    }
+    S.stage[stg].sl = -1;
+    mbar_arrive(&S.issued[stg]);
+    mbar_arrive(&S.full[stg]);
+    ++prod_it;
+  }
+  if (!ok) S.abort = 1;
+}
+
+// Scorer warp sc of rac_enforce_learned: the stages of consumer group sc
+// (ring positions sc, sc + 3, ...), in order; for each, waits until the
+// producer has set the slab, takes the decisions (score_stage) and gives the
+// stage's second full-barrier arrival.  Ends the sweep at the group's marker.
+template <int kMT>
+__device__ void score_sweep(Smem &S, const LaunchParams &P, int k, int slot_r, int sc,
+                            uint32_t &sc_it, int lane) {
+  for (;;) {
+    const uint32_t pos = sc_it * kGroups + sc;
+    const int stg = pos % kStages;
+    const uint32_t par = (pos / kStages) & 1u;
+    uint32_t ok = 1u;
+    if (lane == 0) ok = mbar_wait(&S.issued[stg], par, &P.sync->err, P.wait_limit_ns) ? 1u : 0u;
+    ok = __shfl_sync(kFull, ok, 0);
+    if (!ok) {
+      if (lane == 0) S.abort = 1;
+      return;
+    }
+    const StageInfo si = S.stage[stg];
+    if (si.sl >= 0) score_stage<kMT>(S, P, stg, si.sl, si.ij, si.rows, k, slot_r, lane);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.full[stg]);
+    ++sc_it;
+    if (si.sl < 0) return;
   }
 }
 
 template <int Q, int kVar>
 __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char *stage,
-                             const StageInfo &si, int k, int slot_r, int slot_w, int warp,
-                             int lane, uint32_t &red_iter) {
+                             const StageInfo &si, int stg, int k, int slot_r, int slot_w,
+                             int warp, int lane, uint32_t &red_iter) {
   const int cg = warp / kGroupWarps, lw = warp % kGroupWarps;
   const NetDev &N = P.net;
   const int n = N.n;
@@ -483,8 +626,8 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
   const bool cached = S.dom_cached != 0;
   if (k == 1 && P.seed_var >= 0 && !slab_touches_seed(P, I, J, row0, nrows)) return;
   if constexpr (kVar >= kVarGated1) {
-    consume_slab_gated<Q, kVar - kVarGated1 + 1>(S, P, hdr, rel, si, k, slot_r, slot_w, warp,
-                                                 lane, cg, g, sub, wps, groups, red_iter);
+    consume_slab_scored<Q>(S, P, hdr, rel, si, stg, k, slot_w, warp, lane, cg, g, sub, wps,
+                           groups, red_iter);
   } else if constexpr (kVar == kVarFew) {
     // one to three states, each split over several warps: a short loop
     for (int s = g; s < P.n_states; s += groups) {
@@ -536,12 +679,12 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
 // kVar: the plain variants for one to three states (kVarFew: a state's rows
 // split over several warps) and for four or more (kVarMany: a warp per
 // state, words prefetched), and the variants of rac_enforce_learned (learned
-// gating and/or trace records) whose warp-wide MLP scores 16 or 32 states of
-// a warp at a time (one or two MMA M tiles).  Separate kernels keep each
+// gating and/or trace records) whose producer warp scores up to 16 or up to
+// 32 states at a time (one or two MMA M tiles).  Separate kernels keep each
 // one's instruction footprint small: a launch after an L2 flush fetches its
 // code from HBM.
 template <int Q, int kVar>
-__global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParams P) {
+__global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const LaunchParams P) {
   constexpr int kGate = kVar >= kVarGated1 ? 1 : 0;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *ring = smem_raw;
@@ -555,6 +698,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
   const int64_t gstride = int64_t(G) * blockDim.x;
   const int my_slabs = cta < N.n_slabs ? (N.n_slabs - cta + G - 1) / G : 0;
   const bool is_producer = warp == kConsumerWarps;
+  const bool is_scorer = warp > kConsumerWarps;  // gated variants only
   // consumer thread index and grid-wide consumer stride
   const int ctid = tid;
   const int64_t cgtid = int64_t(cta) * (kConsumerWarps * 32) + ctid;
@@ -562,8 +706,9 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
 
   if (tid == 0) {
     for (int i = 0; i < kStages; ++i) {
-      mbar_init(&S.full[i], 1);
+      mbar_init(&S.full[i], kGate > 0 ? 2 : 1);  // gated: the copy, then the decisions
       mbar_init(&S.empty[i], kGroupWarps);
+      mbar_init(&S.issued[i], 1);
     }
     fence_mbar_init();
     S.all_done = 0;
@@ -577,6 +722,15 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
       uint4 *dst = reinterpret_cast<uint4 *>(S.dom + (kDomWords - kMlpSmemWords));
       for (int i = tid; i < kPackVec4; i += blockDim.x) dst[i] = P.mlp[i];
     }
+    if (P.pend) {
+      // no pair of this CTA's slabs is pending yet (the per-state counts were
+      // zeroed before the launch)
+      for (int64_t i = tid; i < int64_t(my_slabs) * B; i += blockDim.x) {
+        const int sl = cta + int(i / B) * G;
+        P.pend[int64_t(sl) * P.flag_stride + (i % B)] = 0;
+      }
+      for (int j = tid; j < my_slabs; j += blockDim.x) P.pend_slab[cta + j * G] = 0;
+    }
   }
   for (int s = tid; s < B; s += blockDim.x) {
     S.st_info[s] = P.mlp ? kInfoGated : 0u;  // learned gating starts with a gated sweep
@@ -587,6 +741,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
 
   uint32_t ring_it = 0;   // consumer-side position in the ring (per consumer group)
   uint32_t prod_it = 0;   // producer-side position in the ring
+  uint32_t sc_it = 0;     // scorer-side position in its consumer group's stages
   uint32_t red_iter = 0;  // parity of the cross-warp reduction buffer
   if (is_producer) {
     if (lane == 0 && my_slabs > 0 && cta < P.n_first &&
@@ -597,6 +752,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
       S.stage[0].sl = cta;
       S.stage[0].ij = sd.ij;
       S.stage[0].rows = sd.rows;
+      if (kGate > 0) mbar_arrive(&S.issued[0]);
       mbar_arrive_expect_tx(&S.full[0], sd.nbytes);
       bulk_copy_g2s(ring, N.rel + size_t(sd.rel_off16), sd.nbytes, &S.full[0]);
       prod_it = 1;
@@ -621,9 +777,15 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
       const int slot_w = int((base + k) % 3), slot_r = int((base + k + 2) % 3);
       const int slot_c = int((base + k + 1) % 3);
 
-      if (is_producer) {
-        // producer: stream this CTA's active slabs through the ring
-        if (lane == 0) {
+      if (is_scorer) {
+        if constexpr (kGate > 0)
+          score_sweep<kVar - kVarGated1 + 1>(S, P, k, slot_r, warp - kConsumerWarps - 1, sc_it,
+                                             lane);
+      } else if (is_producer) {
+        if constexpr (kGate > 0) {
+          produce_gated(S, P, ring, k, slot_r, slot_c, cta, G, my_slabs, prod_it, lane);
+        } else if (lane == 0) {
+          // producer: stream this CTA's active slabs through the ring
           if (cta == 0) P.sync->bar[slot_c] = 0ull;  // last used two sweeps (or a launch) ago
           // (learned gating: every slab while some state is in its full phase)
           const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2 && !(P.mlp && S.load_all);
@@ -692,15 +854,6 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
         for (int64_t i = cgtid; i < stride * N.nb; i += cgstride)
           P.chg[slot_c * stride * N.nb + i] = 0u;
         for (int64_t i = cgtid; i < N.nb; i += cgstride) P.chgU[int64_t(slot_c) * N.nb + i] = 0u;
-        if (k == 1 && P.pend) {
-          // no pair of this CTA's slabs is pending yet (the per-state counts
-          // were zeroed before the launch)
-          for (int64_t i = ctid; i < int64_t(my_slabs) * B; i += kConsumerWarps * 32) {
-            const int sl = cta + int(i / B) * G;
-            P.pend[int64_t(sl) * P.flag_stride + (i % B)] = 0;
-          }
-          for (int j = ctid; j < my_slabs; j += kConsumerWarps * 32) P.pend_slab[cta + j * G] = 0;
-        }
         named_bar(kAllConsumersBar, kConsumerWarps * 32);
         if (k == 1) {
           // A := dom_in; B (all ones between launches) &= dom_in -- an AND,
@@ -750,7 +903,7 @@ __global__ void __launch_bounds__(kThreads, 1) rac_bits_kernel(const LaunchParam
           __syncwarp();
           const StageInfo si = S.stage[stg];
           if (si.sl >= 0)
-            consume_slab<Q, kVar>(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_r, slot_w, warp,
+            consume_slab<Q, kVar>(S, P, ring + size_t(stg) * kStageBytes, si, stg, k, slot_r, slot_w, warp,
                             lane, red_iter);
           __syncwarp();
           if (lane == 0) mbar_arrive(&S.empty[stg]);
@@ -879,7 +1032,8 @@ rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
                              int(smem));
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rac_bits_kernel<Q, kVar>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rac_bits_kernel<Q, kVar>,
+                                                      threads_for(kVar), smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
@@ -892,7 +1046,7 @@ rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(grid));
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(threads_for(kVar));
   cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
@@ -926,9 +1080,9 @@ rac_status launch_bits(const LaunchParams &P, cudaStream_t stream) {
   const bool gate = P.mlp != nullptr || P.tr_count != nullptr || P.tr_evals != nullptr;
   if (!gate) return P.n_states < 4 ? launch_width<kVarFew>(P, stream)
                                    : launch_width<kVarMany>(P, stream);
-  // a warp scores the states g, g + 4, ... of a 32-lane chunk: at most 16 of
-  // them while there are at most 64 states
-  return P.n_states <= 64 ? launch_width<kVarGated1>(P, stream)
+  // the producer warp scores 32 states at a time (lane = state): one MMA M
+  // tile covers them while there are at most 16
+  return P.n_states <= 16 ? launch_width<kVarGated1>(P, stream)
                           : launch_width<kVarGated2>(P, stream);
 }
 

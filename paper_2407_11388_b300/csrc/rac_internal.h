@@ -121,6 +121,7 @@ struct LaunchParams {
   // ends the state
   const uint4 *mlp;          // the predictor's fragment-packed weights
   float mlp_thr;
+  int32_t mlp_min_scored;    // a 32-state chunk is scored only with this many gated candidates
   // pending (slab, state) pairs: candidates a gated sweep skipped and no
   // sweep has evaluated since (RAC_VERIFY_FULL off).  pend[sl * flag_stride
   // + s] is owned by the CTA that owns slab sl; pend_slab[sl] counts the

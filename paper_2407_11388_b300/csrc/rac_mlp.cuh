@@ -216,10 +216,5 @@ __device__ __forceinline__ float mlp_warp_logits(const uint4 *wp, const float (&
   return upper ? mlp_warp_logits_mt<2>(wp, f) : mlp_warp_logits_mt<1>(wp, f);
 }
 
-// The sweep kernel's entry: both M tiles always (one inlined copy of the
-// routine keeps the kernel's register allocation within its 128 per thread).
-__device__ __forceinline__ float mlp_warp_logits32(const uint4 *wp, const float (&f)[kMlpIn]) {
-  return mlp_warp_logits_mt<2>(wp, f);
-}
 
 }  // namespace rac

@@ -102,7 +102,7 @@ def test_predictor_entry_points_check_arguments(L):
     assert L.rac_predictor_gradient(None, None, None, 0, 1.0, None, None) == rac.EINVAL
     assert L.rac_predictor_train(None, None, None, 0, 1, 1, 1e-3, 1.0, 0, None) == rac.EINVAL
     assert L.rac_predictor_predict(None, None, 1, None, 1) == rac.EINVAL
-    assert L.rac_enforce_learned(None, 1, None, None, None, None, 0, 0, None, 0.0, None,
+    assert L.rac_enforce_learned(None, 1, None, None, None, None, 0, 0, None, 0.0, 0, None,
                                  None) == rac.EINVAL
     assert L.rac_last_error().decode() != ""
 
