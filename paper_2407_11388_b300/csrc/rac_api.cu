@@ -23,6 +23,36 @@ rac_status cuda_fail(cudaError_t e, const char *what) {
   return RAC_ECUDA;
 }
 
+rac_status persistent_shape(LaunchCache &cache, const void *func, int threads, size_t smem,
+                            const char *what, int *per_sm, int *sms) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device index beyond the supported range");
+    return RAC_ENOTSUP;
+  }
+  std::lock_guard<std::mutex> lock(cache.mu);
+  if (cache.per_sm[dev] == 0) {
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    int p = 0, n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, func, threads, smem);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (p < 1) {
+      set_error(std::string(what) + ": the kernel does not fit on an SM");
+      return RAC_ECUDA;
+    }
+    cache.sms[dev] = n;
+    cache.per_sm[dev] = p;
+  }
+  *per_sm = cache.per_sm[dev];
+  *sms = cache.sms[dev];
+  return RAC_OK;
+}
+
 NetDev net_dev(const rac_network *net) {
   NetDev N;
   N.n = net->n;

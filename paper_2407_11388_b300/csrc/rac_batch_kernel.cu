@@ -44,10 +44,10 @@ struct BSmem {
   uint64_t full[kBStages];
   uint64_t empty[kBStages];
   BStage stage[kBStages];
-  uint32_t stage_ok[kBStages];
   uint32_t base, poisoned, abort, failed;
   uint32_t any_total, wipe_total, running_total;
   uint32_t cta_any, cta_wipe, cta_running;
+  uint32_t stage_ok[kBStages];
 };
 static_assert(size_t(kBStages) * kStageBytes + sizeof(BSmem) <= 232448,
               "shared memory of the batched kernel exceeds 227 KB");
@@ -57,6 +57,7 @@ constexpr uint32_t kInfoResB = 1u << 24;
 constexpr uint32_t kInfoWiped = 1u << 25;
 __device__ __forceinline__ uint32_t info_status_bits(int st) { return uint32_t(st + 8) << 27; }
 __device__ __forceinline__ int info_status(uint32_t v) { return int((v >> 27) & 31u) - 8; }
+
 
 __device__ __forceinline__ int group_bar(int cg) { return 1 + cg; }
 
@@ -514,28 +515,14 @@ __global__ void __launch_bounds__(kBThreads, 1) rac_batch_kernel(const BatchPara
 }  // namespace
 
 rac_status launch_batch(const BatchParams &P, cudaStream_t stream) {
-  static int grid = 0;
-  static int dev_cached = -1;
+  static LaunchCache cache;
   const size_t smem = size_t(kBStages) * kStageBytes + sizeof(BSmem);
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (grid == 0 || dev_cached != dev) {
-    e = cudaFuncSetAttribute(rac_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(smem));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute (batch)");
-    int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rac_batch_kernel, kBThreads, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy (batch)");
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-    if (per_sm < 1) {
-      set_error("batched kernel does not fit on an SM");
-      return RAC_ECUDA;
-    }
-    grid = per_sm * sms;
-    dev_cached = dev;
-  }
+  int per_sm = 0, sms = 0;
+  rac_status rc = persistent_shape(cache, reinterpret_cast<const void *>(rac_batch_kernel),
+                                   kBThreads, smem, "batched kernel set-up", &per_sm, &sms);
+  if (rc != RAC_OK) return rc;
+  const int grid = per_sm * sms;
+  cudaError_t e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(grid));
   cfg.blockDim = dim3(kBThreads);

@@ -1021,29 +1021,15 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
 
 template <int Q, int kVar>
 rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
-  static int grid = 0;
-  static int dev_cached = -1;
+  static LaunchCache cache;
   const size_t smem = size_t(kStages) * kStageBytes + sizeof(Smem);
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (grid == 0 || dev_cached != dev) {
-    e = cudaFuncSetAttribute(rac_bits_kernel<Q, kVar>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(smem));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-    int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rac_bits_kernel<Q, kVar>,
-                                                      threads_for(kVar), smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-    if (per_sm < 1) {
-      set_error("bit-packed kernel does not fit on an SM");
-      return RAC_ECUDA;
-    }
-    grid = per_sm * sms;
-    dev_cached = dev;
-  }
+  int per_sm = 0, sms = 0;
+  rac_status rc = persistent_shape(cache, reinterpret_cast<const void *>(rac_bits_kernel<Q, kVar>),
+                                   threads_for(kVar), smem, "bit-packed kernel set-up", &per_sm,
+                                   &sms);
+  if (rc != RAC_OK) return rc;
+  const int grid = per_sm * sms;
+  cudaError_t e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(grid));
   cfg.blockDim = dim3(threads_for(kVar));

@@ -230,6 +230,17 @@ struct rac_network {
 };
 
 namespace rac {
+// One-time, per-device launch set-up of a persistent kernel: raises its
+// dynamic shared-memory limit to `smem` and measures how many CTAs of
+// `threads` threads fit on an SM.  Safe for concurrent callers on any device.
+constexpr int kMaxDevices = 64;
+struct LaunchCache {
+  std::mutex mu;
+  int per_sm[kMaxDevices] = {};
+  int sms[kMaxDevices] = {};
+};
+rac_status persistent_shape(LaunchCache &cache, const void *func, int threads, size_t smem,
+                            const char *what, int *per_sm, int *sms);
 void set_error(const std::string &msg);
 rac_status cuda_fail(cudaError_t e, const char *what);
 NetDev net_dev(const rac_network *net);

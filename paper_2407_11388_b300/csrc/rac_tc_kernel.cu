@@ -635,31 +635,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
 }  // namespace
 
 rac_status launch_tc(const LaunchParams &P, cudaStream_t stream) {
-  static int grid = 0;
-  static int dev_cached = -1;
+  static LaunchCache cache;
   const size_t smem = size_t(kTcStages) * kStageBytes + sizeof(TcSmem);
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (P.n_states > kTcMaxStates) {
     set_error("the tensor-core kernel takes at most 128 states per launch");
     return RAC_EINVAL;
   }
-  if (grid == 0 || dev_cached != dev) {
-    e = cudaFuncSetAttribute(rac_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute (tensor)");
-    int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rac_tc_kernel, kTcThreads, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy (tensor)");
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-    if (per_sm != 1) {  // one CTA per SM: it owns all 512 tensor-memory columns
-      set_error("the tensor-core kernel must run one CTA per SM");
-      return RAC_ECUDA;
-    }
-    grid = sms;
-    dev_cached = dev;
+  int per_sm = 0, sms = 0;
+  rac_status rc = persistent_shape(cache, reinterpret_cast<const void *>(rac_tc_kernel),
+                                   kTcThreads, smem, "tensor-core kernel set-up", &per_sm, &sms);
+  if (rc != RAC_OK) return rc;
+  if (per_sm != 1) {  // one CTA per SM: it owns all 512 tensor-memory columns
+    set_error("the tensor-core kernel must run one CTA per SM");
+    return RAC_ECUDA;
   }
+  const int grid = sms;
+  cudaError_t e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(grid));
   cfg.blockDim = dim3(kTcThreads);
