@@ -330,8 +330,12 @@ __global__ void __launch_bounds__(kBThreads, 1) rac_batch_kernel(const BatchPara
             S.stage[stg].ij = sd.ij;
             S.stage[stg].rows = sd.rows;
             mbar_arrive_expect_tx(&S.full[stg], sd.nbytes);
-            bulk_copy_g2s(ring + size_t(stg) * kStageBytes, J.rel + size_t(sd.rel_off16),
-                          sd.nbytes, &S.full[stg]);
+            if (P.rel_evict_first)
+              bulk_copy_g2s_hint(ring + size_t(stg) * kStageBytes, J.rel + size_t(sd.rel_off16),
+                                 sd.nbytes, &S.full[stg], policy_evict_first());
+            else
+              bulk_copy_g2s(ring + size_t(stg) * kStageBytes, J.rel + size_t(sd.rel_off16),
+                            sd.nbytes, &S.full[stg]);
             ++prod_it;
           }
           for (int e = 0; e < kBGroups && ok; ++e) {

@@ -190,7 +190,9 @@ struct BatchParams {
   int32_t max_sweeps;
   uint32_t flags;
   uint64_t wait_limit_ns;
+  uint32_t rel_evict_first;    // the relation stores exceed L2: stream them evict-first
 };
+constexpr size_t kEvictFirstBytes = size_t(96) << 20;  // relation bytes above which streams go evict-first
 
 // Per-(network, stream) scratch.
 struct Workspace {
