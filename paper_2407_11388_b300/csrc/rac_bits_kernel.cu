@@ -44,6 +44,8 @@ struct StageInfo {
   uint32_t ij, rows, pad;
 };
 
+constexpr int kChgULocal = 64;  // variables <= 2048: the union is collected in shared memory
+
 struct Smem {
   uint64_t full[kStages];
   uint64_t empty[kStages];
@@ -55,6 +57,12 @@ struct Smem {
   uint32_t all_done;
   uint32_t abort;
   uint32_t dom_cached;
+  uint32_t chg_off;     // chg_cached: the words start at dom + chg_off
+  uint32_t chg_cached;  // sweep k >= 2 keeps the changed-variable words of sweep k-1 in dom
+  uint32_t chgu_local;  // RAC_INCREMENTAL with nb <= kChgULocal: chgu_loc collects the union
+  // this CTA's share of the sweep's changed-variable union (over the states),
+  // merged into P.chgU once per sweep instead of one global atomic per removal
+  uint32_t chgu_loc[kChgULocal];
   uint32_t any_total;   // CTAs that removed a value in the last sweep
   uint32_t wipe_total;  // CTAs that emptied a domain in the last sweep
   uint32_t failed;      // a wait of this CTA gave up, or another CTA reported one
@@ -163,6 +171,15 @@ __device__ __forceinline__ StateView state_view(const LaunchParams &P, int s, in
   return v;
 }
 
+// Word blk of the variables state s changed in sweep k-1 (sweep k >= 2): from
+// the copy the consumers made at the start of the sweep when it fits, else
+// from L2.
+__device__ __forceinline__ uint32_t chg_word(const Smem &S, const LaunchParams &P, int slot_r,
+                                             int s, uint32_t blk) {
+  if (S.chg_cached) return S.dom[S.chg_off + uint32_t(s) * uint32_t(P.net.nb) + blk];
+  return ld_dom(P.chg + (int64_t(slot_r) * P.flag_stride + s) * P.net.nb + blk);
+}
+
 // Apply a removal: D_k[v] &= keep, where keep is a strict subset of D_{k-1}[v].
 __device__ __forceinline__ void remove_values(Smem &S, const LaunchParams &P, int s, int slot_w,
                                               uint32_t *T, uint32_t v, uint32_t keep) {
@@ -172,7 +189,10 @@ __device__ __forceinline__ void remove_values(Smem &S, const LaunchParams &P, in
   const int nb = P.net.nb;
   const uint32_t bit = 1u << (v & 31u);
   atomicOr(P.chg + (int64_t(slot_w) * P.flag_stride + s) * nb + (v >> 5), bit);
-  if (P.flags & RAC_INCREMENTAL) atomicOr(P.chgU + int64_t(slot_w) * nb + (v >> 5), bit);
+  if (S.chgu_local)
+    atomicOr(&S.chgu_loc[v >> 5], bit);
+  else if (P.flags & RAC_INCREMENTAL)
+    atomicOr(P.chgU + int64_t(slot_w) * nb + (v >> 5), bit);
 }
 
 // Bounded grid barrier over all CTAs (co-resident: cooperative launch).  The
@@ -232,6 +252,15 @@ __device__ __forceinline__ void load_words(const Smem &S, const LaunchParams &P,
     Dy = input_word(P, y, Dy);
     Dxl = input_word(P, x_l, Dxl);
   }
+}
+
+// The states of a 32-state chunk (bit i: state c0 + i) that warp g of a
+// consumer group with `groups` warps evaluates: those of rank g, g + groups,
+// ... among the chunk's states to evaluate, so that the group's warps get
+// equal shares however the evaluated states fall.
+__device__ __forceinline__ uint32_t warp_share(uint32_t m, int g, int groups, int lane) {
+  const int rank = __popc(m & lanemask_lt());
+  return __ballot_sync(kFull, ((m >> lane) & 1u) && rank % groups == g);
 }
 
 // Evaluate one state on one slab: the support step of Eq. 1 restricted to the
@@ -482,22 +511,21 @@ __device__ void consume_slab_scored(Smem &S, const LaunchParams &P, const uint32
   const bool cached = S.dom_cached != 0;
   const bool recording = P.tr_count != nullptr;
   const uint32_t *dec = stage_dec(S, stg);
-  for (int c0 = g; c0 < B; c0 += 32 * groups) {
-    const int s_l = c0 + groups * lane;
-    const bool ev = s_l < B && ((dec[s_l >> 5] >> (s_l & 31)) & 1u);
-    uint32_t m = __ballot_sync(kFull, ev);
+  for (int c0 = 0; c0 < B; c0 += 32) {
+    const uint32_t ev_all = dec[c0 >> 5];  // states past B are never set
+    if (ev_all == 0u) continue;
+    uint32_t m = warp_share(ev_all, g, groups, lane);
     if (m == 0u) continue;
     int i = __ffs(m) - 1;
     m &= m - 1u;
     uint32_t Dy, Dxl;
-    load_words(S, P, c0 + groups * i, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
+    load_words(S, P, c0 + i, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
     for (;;) {
       const int inext = m ? __ffs(m) - 1 : -1;
       if (inext >= 0) m &= m - 1u;
       uint32_t Dy_n = 0u, Dx_n = 0u;
-      if (inext >= 0)
-        load_words(S, P, c0 + groups * inext, k, cached, y, y_ok, x_l, x_ok, Dy_n, Dx_n);
-      const int s = c0 + groups * i;
+      if (inext >= 0) load_words(S, P, c0 + inext, k, cached, y, y_ok, x_l, x_ok, Dy_n, Dx_n);
+      const int s = c0 + i;
       const bool removed = eval_state<Q, true, true>(S, P, s, k, slot_w, hdr, rel, I, row0, nrows,
                                                      y, y_ok, cached, Dy, Dxl, warp, lane, cg, g,
                                                      sub, wps, red_iter);
@@ -517,50 +545,84 @@ __device__ void consume_slab_scored(Smem &S, const LaunchParams &P, const uint32
   }
 }
 
-// The producer warp of rac_enforce_learned: the plain producer's slab stream
-// (lane 0 issues the copies), and after each stage's slab is set an arrival
-// on the stage's `issued` barrier, so that the stage's scorer warp can take
-// the decisions while the copy is in flight.  A stage's full barrier
-// completes with the copy and the scorer's arrival.
-__device__ void produce_gated(Smem &S, const LaunchParams &P, unsigned char *ring, int k,
+// Is slab sl (descriptor sd) streamed in a Proposition-2 sweep?  When a
+// variable of its rows or columns changed in the previous sweep in some state
+// (cu: the union over the states), or a pair of it is pending.
+__device__ __forceinline__ bool slab_streamed(const LaunchParams &P, const SlabDesc &sd, int sl,
+                                              const uint32_t *cu) {
+  const uint32_t I = sd.ij & 0xFFFFu, J = sd.ij >> 16;
+  const uint32_t row0 = sd.rows & 0xFFu, nrows = sd.rows >> 8;
+  const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
+  return ld_dom(cu + J) != 0u || (ld_dom(cu + I) & rowmask) != 0u ||
+         (P.pend_slab && ld_dom(reinterpret_cast<const uint32_t *>(P.pend_slab) + sl) != 0u);
+}
+
+// The producer warp's slab stream for sweep k: lane 0 issues a bulk copy for
+// every slab this CTA streams (slab_streamed), then one end marker per
+// consumer group.  Proposition-2 sweeps test 32 slabs at a time, a lane
+// each, so that the tests' L2 reads overlap; the other sweeps stream every
+// slab (sweep 1 of a search assignment: those on the assigned variable) from
+// lane 0 alone.  kGate: the learned variants, where the producer also
+// arrives on the stage's `issued` barrier once the slab is set (the stage's
+// scorer warp gives the full barrier's second arrival).
+template <int kGate>
+__device__ void produce_sweep(Smem &S, const LaunchParams &P, unsigned char *ring, int k,
                               int slot_r, int slot_c, int cta, int G, int my_slabs,
                               uint32_t &prod_it, int lane) {
-  if (lane != 0) return;
   const NetDev &N = P.net;
-  if (cta == 0) P.sync->bar[slot_c] = 0ull;  // last used two sweeps (or a launch) ago
-  // every slab while some state is in its full phase (RAC_VERIFY_FULL)
+  if (cta == 0 && lane == 0) P.sync->bar[slot_c] = 0ull;  // last used two sweeps (or a launch) ago
+  // (learned gating: every slab while some state is in its full phase)
   const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2 && !(P.mlp && S.load_all);
   const uint32_t *cu = P.chgU + int64_t(slot_r) * N.nb;
-  bool ok = true;
-  // in sweep 1 the first slab may already be on its way
-  for (int j = (k == 1 && prod_it == 1) ? 1 : 0; j < my_slabs; ++j) {
+  bool ok = true;  // lane 0's wait outcomes
+  // lane 0: the copy of this CTA's slab j into the next ring stage
+  auto issue = [&](int j) {
     const int sl = cta + j * G;
     const SlabDesc sd = j < kDescCache ? S.desc[j] : N.slabs[sl];
-    if (incr) {
-      const uint32_t I = sd.ij & 0xFFFFu, J = sd.ij >> 16;
-      const uint32_t row0 = sd.rows & 0xFFu, nrows = sd.rows >> 8;
-      const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
-      if (ld_dom(cu + J) == 0u && (ld_dom(cu + I) & rowmask) == 0u &&
-          !(P.pend_slab && ld_dom(reinterpret_cast<const uint32_t *>(P.pend_slab) + sl) != 0u))
-        continue;
-    }
     const int stg = prod_it % kStages;
     const uint32_t par = (prod_it / kStages) & 1u;
-    if (!mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err, P.wait_limit_ns)) {
-      ok = false;
-      break;
-    }
+    if (!mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err, P.wait_limit_ns)) return false;
     S.stage[stg].sl = sl;
     S.stage[stg].ij = sd.ij;
     S.stage[stg].rows = sd.rows;
-    mbar_arrive(&S.issued[stg]);
+    if (kGate > 0) mbar_arrive(&S.issued[stg]);
     mbar_arrive_expect_tx(&S.full[stg], sd.nbytes);
     bulk_copy_g2s(ring + size_t(stg) * kStageBytes, N.rel + size_t(sd.rel_off16), sd.nbytes,
                   &S.full[stg]);
     ++prod_it;
+    return true;
+  };
+  if (!incr) {
+    if (lane != 0) return;
+    // in sweep 1 the first slab may already be on its way
+    for (int j = (k == 1 && prod_it == 1) ? 1 : 0; j < my_slabs; ++j) {
+      if (k == 1 && P.seed_var >= 0) {
+        const SlabDesc sd = j < kDescCache ? S.desc[j] : N.slabs[cta + j * G];
+        if (!slab_touches_seed(P, sd.ij & 0xFFFFu, sd.ij >> 16, sd.rows & 0xFFu, sd.rows >> 8))
+          continue;  // sweep 1 of an assignment: only constraints on the assigned variable
+      }
+      if (!(ok = issue(j))) break;
+    }
+  } else {
+    for (int j0 = 0; j0 < my_slabs; j0 += 32) {
+      const int jl = j0 + lane;
+      bool act = false;
+      if (jl < my_slabs) {
+        const int sl = cta + jl * G;
+        act = slab_streamed(P, jl < kDescCache ? S.desc[jl] : N.slabs[sl], sl, cu);
+      }
+      uint32_t am = __ballot_sync(kFull, act);
+      if (lane == 0) {
+        while (am != 0u && ok) {
+          ok = issue(j0 + __ffs(am) - 1);
+          am &= am - 1u;
+        }
+      }
+      if (__shfl_sync(kFull, ok ? 1 : 0, 0) == 0) break;
+    }
+    if (lane != 0) return;
   }
-  // end of this sweep's slabs: one marker for each consumer group (its
-  // scorer gives the second arrival)
+  // end of this sweep's slabs: one marker for each consumer group
   for (int e = 0; e < kGroups && ok; ++e) {
     const int stg = prod_it % kStages;
     const uint32_t par = (prod_it / kStages) & 1u;
@@ -569,7 +631,7 @@ __device__ void produce_gated(Smem &S, const LaunchParams &P, unsigned char *rin
       break;
     }
     S.stage[stg].sl = -1;
-    mbar_arrive(&S.issued[stg]);
+    if (kGate > 0) mbar_arrive(&S.issued[stg]);
     mbar_arrive(&S.full[stg]);
     ++prod_it;
   }
@@ -632,41 +694,40 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
     // one to three states, each split over several warps: a short loop
     for (int s = g; s < P.n_states; s += groups) {
       if (S.st_info[s] & kInfoSweepMask) continue;  // finished state
-      if (incr) {
-        const uint32_t *ch = P.chg + (int64_t(slot_r) * P.flag_stride + s) * N.nb;
-        if (ld_dom(ch + J) == 0u && (ld_dom(ch + I) & rowmask) == 0u) continue;
-      }
+      if (incr && chg_word(S, P, slot_r, s, J) == 0u &&
+          (chg_word(S, P, slot_r, s, I) & rowmask) == 0u)
+        continue;
       eval_state<Q, false, false>(S, P, s, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, cached,
                                   0u, 0u, warp, lane, cg, g, sub, wps, red_iter);
     }
   } else {
     const int x_l = int(I) * 32 + int(row0) + lane;
     const bool x_ok = lane < int(nrows) && x_l < n;
-    // one warp per state (four or more states): the warp's states, 32 at a
-    // time (lane i checks state c0 + groups * i: running, and with
-    // RAC_INCREMENTAL a Proposition-2 candidate); the words of the next
-    // state are loaded while the current one is evaluated
-    for (int c0 = g; c0 < P.n_states; c0 += 32 * groups) {
-      const int s_l = c0 + groups * lane;
+    // one warp per state (four or more states): 32 states at a time, lane i
+    // checking state c0 + i (running, and with RAC_INCREMENTAL a
+    // Proposition-2 candidate), the warp taking its share of them; the words
+    // of the next state are loaded while the current one is evaluated
+    for (int c0 = 0; c0 < P.n_states; c0 += 32) {
+      const int s_l = c0 + lane;
       bool act = s_l < P.n_states && !(S.st_info[s_l] & kInfoSweepMask);
-      if (act && incr) {
-        const uint32_t *ch = P.chg + (int64_t(slot_r) * P.flag_stride + s_l) * N.nb;
-        act = ld_dom(ch + J) != 0u || (ld_dom(ch + I) & rowmask) != 0u;
-      }
+      if (act && incr)
+        act = chg_word(S, P, slot_r, s_l, J) != 0u ||
+              (chg_word(S, P, slot_r, s_l, I) & rowmask) != 0u;
       uint32_t am = __ballot_sync(kFull, act);
+      if (am == 0u) continue;
+      am = warp_share(am, g, groups, lane);
       if (am == 0u) continue;
       int i = __ffs(am) - 1;
       am &= am - 1u;
       uint32_t Dy, Dxl;
-      load_words(S, P, c0 + groups * i, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
+      load_words(S, P, c0 + i, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
       for (;;) {
         const int inext = am ? __ffs(am) - 1 : -1;
         if (inext >= 0) am &= am - 1u;
         uint32_t Dy_n = 0u, Dx_n = 0u;
-        if (inext >= 0)
-          load_words(S, P, c0 + groups * inext, k, cached, y, y_ok, x_l, x_ok, Dy_n, Dx_n);
-        eval_state<Q, false, true>(S, P, c0 + groups * i, k, slot_w, hdr, rel, I, row0, nrows, y,
-                                   y_ok, cached, Dy, Dxl, warp, lane, cg, g, sub, wps, red_iter);
+        if (inext >= 0) load_words(S, P, c0 + inext, k, cached, y, y_ok, x_l, x_ok, Dy_n, Dx_n);
+        eval_state<Q, false, true>(S, P, c0 + i, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok,
+                                   cached, Dy, Dxl, warp, lane, cg, g, sub, wps, red_iter);
         if (inext < 0) break;
         i = inext;
         Dy = Dy_n;
@@ -716,6 +777,11 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
     S.abort = 0;
     S.failed = 0;
     S.dom_cached = int64_t(B) * n <= dom_cache_words<kGate>() ? 1u : 0u;
+    // the changed-variable words of every state go after the cached domains
+    S.chg_off = S.dom_cached ? uint32_t((int64_t(B) * n + 3) & ~int64_t(3)) : 0u;
+    S.chg_cached =
+        int64_t(S.chg_off) + int64_t(B) * N.nb <= dom_cache_words<kGate>() ? 1u : 0u;
+    S.chgu_local = (P.flags & RAC_INCREMENTAL) && N.nb <= kChgULocal ? 1u : 0u;
   }
   if constexpr (kGate > 0) {
     if (P.mlp) {
@@ -732,6 +798,7 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
       for (int j = tid; j < my_slabs; j += blockDim.x) P.pend_slab[cta + j * G] = 0;
     }
   }
+  for (int w = tid; w < kChgULocal; w += blockDim.x) S.chgu_loc[w] = 0u;
   for (int s = tid; s < B; s += blockDim.x) {
     S.st_info[s] = P.mlp ? kInfoGated : 0u;  // learned gating starts with a gated sweep
     S.any_loc[s] = 0;
@@ -782,59 +849,7 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
           score_sweep<kVar - kVarGated1 + 1>(S, P, k, slot_r, warp - kConsumerWarps - 1, sc_it,
                                              lane);
       } else if (is_producer) {
-        if constexpr (kGate > 0) {
-          produce_gated(S, P, ring, k, slot_r, slot_c, cta, G, my_slabs, prod_it, lane);
-        } else if (lane == 0) {
-          // producer: stream this CTA's active slabs through the ring
-          if (cta == 0) P.sync->bar[slot_c] = 0ull;  // last used two sweeps (or a launch) ago
-          // (learned gating: every slab while some state is in its full phase)
-          const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2 && !(P.mlp && S.load_all);
-          const uint32_t *cu = P.chgU + int64_t(slot_r) * N.nb;
-          bool ok = true;
-          // in sweep 1 the first slab may already be on its way
-          for (int j = (k == 1 && prod_it == 1) ? 1 : 0; j < my_slabs; ++j) {
-            const int sl = cta + j * G;
-            const SlabDesc sd = j < kDescCache ? S.desc[j] : N.slabs[sl];
-            if (incr) {
-              const uint32_t I = sd.ij & 0xFFFFu, J = sd.ij >> 16;
-              const uint32_t row0 = sd.rows & 0xFFu, nrows = sd.rows >> 8;
-              const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
-              if (ld_dom(cu + J) == 0u && (ld_dom(cu + I) & rowmask) == 0u &&
-                  !(P.pend_slab && ld_dom(reinterpret_cast<const uint32_t *>(P.pend_slab) + sl) != 0u))
-                continue;
-            } else if (k == 1 && P.seed_var >= 0 &&
-                       !slab_touches_seed(P, sd.ij & 0xFFFFu, sd.ij >> 16, sd.rows & 0xFFu,
-                                          sd.rows >> 8)) {
-              continue;  // sweep 1 of an assignment: only constraints on the assigned variable
-            }
-            const int stg = prod_it % kStages;
-            const uint32_t par = (prod_it / kStages) & 1u;
-            if (!mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err, P.wait_limit_ns)) {
-              ok = false;
-              break;
-            }
-            S.stage[stg].sl = sl;
-            S.stage[stg].ij = sd.ij;
-            S.stage[stg].rows = sd.rows;
-            mbar_arrive_expect_tx(&S.full[stg], sd.nbytes);
-            bulk_copy_g2s(ring + size_t(stg) * kStageBytes, N.rel + size_t(sd.rel_off16),
-                          sd.nbytes, &S.full[stg]);
-            ++prod_it;
-          }
-          // end of this sweep's slabs: one marker for each consumer group
-          for (int e = 0; e < kGroups && ok; ++e) {
-            const int stg = prod_it % kStages;
-            const uint32_t par = (prod_it / kStages) & 1u;
-            if (!mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err, P.wait_limit_ns)) {
-              ok = false;
-              break;
-            }
-            S.stage[stg].sl = -1;
-            mbar_arrive(&S.full[stg]);
-            ++prod_it;
-          }
-          if (!ok) S.abort = 1;
-        }
+        produce_sweep<kGate>(S, P, ring, k, slot_r, slot_c, cta, G, my_slabs, prod_it, lane);
       } else {
         const int64_t stride = P.flag_stride;
         // this sweep's domains D_{k-1} into shared memory
@@ -854,6 +869,13 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
         for (int64_t i = cgtid; i < stride * N.nb; i += cgstride)
           P.chg[slot_c * stride * N.nb + i] = 0u;
         for (int64_t i = cgtid; i < N.nb; i += cgstride) P.chgU[int64_t(slot_c) * N.nb + i] = 0u;
+        // the variables every state changed in sweep k-1, read once here
+        // instead of once per slab
+        if (k >= 2 && S.chg_cached) {
+          const uint32_t *src = P.chg + int64_t(slot_r) * stride * N.nb;
+          for (int i = ctid; i < B * N.nb; i += kConsumerWarps * 32)
+            S.dom[S.chg_off + i] = ld_dom(src + i);
+        }
         named_bar(kAllConsumersBar, kConsumerWarps * 32);
         if (k == 1) {
           // A := dom_in; B (all ones between launches) &= dom_in -- an AND,
@@ -868,19 +890,16 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
             if (v == 0u) S.wipe_loc[s] = 1;  // D_1 will hold this empty domain
           }
         } else {
-          // owner step: T still holds D_{k-2}; AND D_{k-1} into it where it differs
-          for (int64_t i = cgtid; i < int64_t(B) * N.nb; i += cgstride) {
+          // owner step: T still holds D_{k-2}; AND D_{k-1} into it where it
+          // differs (a warp per 32-variable block of a state, lane = variable)
+          const int64_t cw = int64_t(cta) * kConsumerWarps + warp;
+          for (int64_t i = cw; i < int64_t(B) * N.nb; i += int64_t(G) * kConsumerWarps) {
             const int s = int(i / N.nb), blk = int(i % N.nb);
             if (S.st_info[s] & kInfoSweepMask) continue;
-            uint32_t w = ld_dom(P.chg + (int64_t(slot_r) * stride + s) * N.nb + blk);
-            if (w == 0u) continue;
+            const int x = blk * 32 + lane;
+            if (!((chg_word(S, P, slot_r, s, uint32_t(blk)) >> lane) & 1u)) continue;
             const StateView V = state_view(P, s, k);
-            while (w) {
-              const int b = __ffs(w) - 1;
-              w &= w - 1u;
-              const int x = blk * 32 + b;
-              atomicAnd(V.T + x, S.dom_cached ? S.dom[s * n + x] : ld_dom(V.C + x));
-            }
+            atomicAnd(V.T + x, S.dom_cached ? S.dom[s * n + x] : ld_dom(V.C + x));
           }
         }
         // consumer group cg takes ring positions cg, cg + kGroups, ...
@@ -929,6 +948,15 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
           if (B > 1) atomicOr(P.wipe + slot_w * P.flag_stride + s, 1u);
           S.cta_wipe = 1;
           S.wipe_loc[s] = 0;
+        }
+      }
+      if (S.chgu_local) {
+        for (int w = tid; w < N.nb; w += blockDim.x) {
+          const uint32_t u = S.chgu_loc[w];
+          if (u != 0u) {
+            atomicOr(P.chgU + int64_t(slot_w) * N.nb + w, u);
+            S.chgu_loc[w] = 0u;
+          }
         }
       }
       if (S.abort) S.failed = 1;

@@ -55,7 +55,7 @@ constexpr int kStageBytes = kSlabRelBytes + 256;     // + header (at most 32 row
 constexpr int kStages = 6;
 constexpr int kMaxStatesPerLaunch = 1024;
 constexpr int kDescCache = 256;   // slab descriptors a CTA keeps in shared memory
-constexpr int kDomWords = 5120;   // domain words a CTA keeps in shared memory per sweep
+constexpr int kDomWords = 5040;   // domain words a CTA keeps in shared memory per sweep
 
 struct NetDev {
   int32_t n, d, dp, q, nb, rows_per_slab, n_slabs;
