@@ -120,29 +120,51 @@ __device__ __forceinline__ void support_dispatch_q(const uint4 *mine, uint32_t s
     support_relation<Q, false>(mine, stride, Dx, Dy, fwd, rev);
 }
 
-__device__ __forceinline__ void batch_remove(BSmem &S, const BatchParams &P, const BatchJob &J,
-                                             int t, int64_t chgoff, int slot_w, uint32_t *T,
-                                             uint32_t v, uint32_t keep) {
-  const uint32_t old = atomicAnd(T + v, keep);
-  S.cta_any = 1;
-  atomicOr(P.any + int64_t(slot_w) * P.total_states + t, 1u);
-  if (old != 0u && (old & keep) == 0u) {
-    S.cta_wipe = 1;
-    atomicOr(P.wipe + int64_t(slot_w) * P.total_states + t, 1u);
+// Apply a removal to state t: D_k[v] &= keep.  As in kernel (a), only
+// RAC_STOP_ON_WIPEOUT needs to know at once whether it emptied the domain;
+// otherwise the next sweep's owner step finds emptied domains.
+__device__ __forceinline__ void batch_remove(BSmem &S, const BatchParams &P, int t, int slot_w,
+                                             uint32_t *T, uint32_t v, uint32_t keep) {
+  if (P.flags & RAC_STOP_ON_WIPEOUT) {
+    const uint32_t old = atomicAnd(T + v, keep);
+    if (old != 0u && (old & keep) == 0u) {
+      S.cta_wipe = 1;
+      atomicOr(P.wipe + int64_t(slot_w) * P.total_states + t, 1u);
+    }
+  } else {
+    atomicAnd(T + v, keep);
   }
-  const uint32_t bit = 1u << (v & 31u);
-  atomicOr(P.chg + int64_t(slot_w) * P.chg_slot_words + chgoff + (v >> 5), bit);
-  if (P.flags & RAC_INCREMENTAL)
-    atomicOr(P.chgU + int64_t(slot_w) * P.u_slot_words + J.u_off + (v >> 5), bit);
 }
 
-// One slab of job J for every running state of J, by one consumer group: the
-// group's warps own the job's states s = 4 i + lw.  A warp takes its states
-// 32 at a time (lane i checks state base + 4 i: running, and with
-// RAC_INCREMENTAL a Proposition-2 candidate) and evaluates the ones that
-// need it, one after the other: each state's column words (lane = column)
-// and row words (lane = row) come in two coalesced loads, issued for the
-// next state while the current one is evaluated.
+// The variables one evaluation of state t removed values from (xbits in
+// block I, ybits in block Jb): one flag and at most four atomics per
+// evaluation instead of one per removal.
+__device__ __forceinline__ void batch_mark(BSmem &S, const BatchParams &P, const BatchJob &J,
+                                           int t, int64_t chgoff, int slot_w, uint32_t I,
+                                           uint32_t xbits, uint32_t Jb, uint32_t ybits) {
+  S.cta_any = 1;
+  atomicOr(P.any + int64_t(slot_w) * P.total_states + t, 1u);
+  uint32_t *ch = P.chg + int64_t(slot_w) * P.chg_slot_words + chgoff;
+  uint32_t *cu = P.chgU + int64_t(slot_w) * P.u_slot_words + J.u_off;
+  const bool incr = (P.flags & RAC_INCREMENTAL) != 0u;
+  if (xbits) {
+    atomicOr(ch + I, xbits);
+    if (incr) atomicOr(cu + I, xbits);
+  }
+  if (ybits) {
+    atomicOr(ch + Jb, ybits);
+    if (incr) atomicOr(cu + Jb, ybits);
+  }
+}
+
+// One slab of job J for every running state of J, by one consumer group.  The
+// job's states go 32 at a time (lane i checks state base + i: running, and
+// with RAC_INCREMENTAL a Proposition-2 candidate); warp lw of the group takes
+// those of rank lw, lw + 4, ... among the ones to evaluate, so the group's
+// warps get equal shares, and evaluates them one after the other: each
+// state's column words (lane = column) and row words (lane = row) come in two
+// coalesced loads, issued for the next state while the current one is
+// evaluated.
 template <int Q>
 __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &J,
                                 const unsigned char *stage, const BStage &si, int k, int slot_r,
@@ -159,9 +181,9 @@ __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &
   const uint32_t dfull = J.d >= 32 ? kFull : ((1u << J.d) - 1u);
   const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
   const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
-  for (int base = lw; base < J.n_states; base += 32 * kBGroupWarps) {
-    // lane i: state t = state_base + base + 4 i
-    const int q = base + kBGroupWarps * lane;
+  for (int base = 0; base < J.n_states; base += 32) {
+    // lane i: state t = state_base + base + i
+    const int q = base + lane;
     const int t = J.state_base + q;
     bool act = false;
     int64_t c_off = 0, t_off = 0, chgoff = 0;
@@ -180,6 +202,9 @@ __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &
       }
     }
     uint32_t am = __ballot_sync(kFull, act);
+    if (am == 0u) continue;
+    // this warp's share: the states of rank lw, lw + 4, ... among them
+    am = __ballot_sync(kFull, act && __popc(am & lanemask_lt()) % kBGroupWarps == lw);
     if (am == 0u) continue;
     // words of the first state
     int i = __ffs(am) - 1;
@@ -201,7 +226,7 @@ __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &
       const int64_t to = __shfl_sync(kFull, t_off, i);
       const int64_t co = __shfl_sync(kFull, chgoff, i);
       uint32_t *T = ((k == 1 || (k & 1)) ? P.bufB : P.dom_out) + to;
-      uint32_t racc = kFull;
+      uint32_t racc = kFull, xbits = 0u;
       for (int r = 0; r < int(nrows); ++r) {
         const uint32_t pm = hdr[r];
         if (pm == 0u) continue;
@@ -213,16 +238,23 @@ __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &
                                 dfull, fwd, rev);
         }
         const uint32_t keep_x = __reduce_and_sync(kFull, fwd) & Dx;
-        if (keep_x != Dx && lane == 0) {
-          const int x = int(I) * 32 + int(row0) + r;
-          batch_remove(S, P, J, ts, co, slot_w, T, uint32_t(x), keep_x);
+        if (keep_x != Dx) {
+          if (lane == 0) batch_remove(S, P, ts, slot_w, T, I * 32u + row0 + uint32_t(r), keep_x);
+          xbits |= 1u << (row0 + uint32_t(r));
         }
         racc &= rev;
       }
+      bool rem_y = false;
       if (y_ok) {
         const uint32_t keep_y = racc & Dy;
-        if (keep_y != Dy) batch_remove(S, P, J, ts, co, slot_w, T, uint32_t(y), keep_y);
+        if (keep_y != Dy) {
+          batch_remove(S, P, ts, slot_w, T, uint32_t(y), keep_y);
+          rem_y = true;
+        }
       }
+      const uint32_t ybits = __ballot_sync(kFull, rem_y);
+      if (lane == 0 && (xbits | ybits) != 0u)
+        batch_mark(S, P, J, ts, co, slot_w, I, xbits, Jb, ybits);
       if (inext < 0) break;
       i = inext;
       Dy = Dy_n;
@@ -376,11 +408,18 @@ __global__ void __launch_bounds__(kBThreads, 1) rac_batch_kernel(const BatchPara
               uint32_t w = ld_dom(ch + blk);
               if (w == 0u) continue;
               const BView V = bview(P, t, k);
+              bool emptied = false;  // a domain sweep k-1 emptied (see batch_remove)
               while (w) {
                 const int b = __ffs(w) - 1;
                 w &= w - 1u;
                 const int x = blk * 32 + b;
-                atomicAnd(V.T + x, ld_dom(V.C + x));
+                const uint32_t c = ld_dom(V.C + x);
+                atomicAnd(V.T + x, c);
+                emptied = emptied || c == 0u;
+              }
+              if (emptied) {
+                S.cta_wipe = 1;
+                atomicOr(P.wipe + int64_t(slot_w) * T_total + t, 1u);
               }
             }
           }

@@ -181,18 +181,48 @@ __device__ __forceinline__ uint32_t chg_word(const Smem &S, const LaunchParams &
 }
 
 // Apply a removal: D_k[v] &= keep, where keep is a strict subset of D_{k-1}[v].
-__device__ __forceinline__ void remove_values(Smem &S, const LaunchParams &P, int s, int slot_w,
-                                              uint32_t *T, uint32_t v, uint32_t keep) {
-  const uint32_t old = atomicAnd(T + v, keep);
+// Whether it empties the domain matters at once only with RAC_STOP_ON_WIPEOUT
+// (the state ends after this sweep): there the atomic returns the old word.
+// Otherwise an emptied domain only decides the final status, and the next
+// sweep's owner step finds it (it reads D_k of every variable that changed),
+// so the removal does not wait for the atomic's round trip.
+__device__ __forceinline__ void remove_value(Smem &S, const LaunchParams &P, int s, uint32_t *T,
+                                             uint32_t v, uint32_t keep) {
+  if (P.flags & RAC_STOP_ON_WIPEOUT) {
+    const uint32_t old = atomicAnd(T + v, keep);
+    if (old != 0u && (old & keep) == 0u) S.wipe_loc[s] = 1;
+  } else {
+    atomicAnd(T + v, keep);
+  }
+}
+
+// Record the variables one evaluation of state s removed values from: xbits
+// in 32-variable block I (the slab's rows), ybits in block J (its columns).
+// One atomic per block and evaluation instead of one per removal; the union
+// over the states (Proposition 2) goes to the CTA's shared copy when it has
+// one.
+__device__ __forceinline__ void mark_changed(Smem &S, const LaunchParams &P, int s, int slot_w,
+                                             uint32_t I, uint32_t xbits, uint32_t J,
+                                             uint32_t ybits) {
   S.any_loc[s] = 1;
-  if (old != 0u && (old & keep) == 0u) S.wipe_loc[s] = 1;
   const int nb = P.net.nb;
-  const uint32_t bit = 1u << (v & 31u);
-  atomicOr(P.chg + (int64_t(slot_w) * P.flag_stride + s) * nb + (v >> 5), bit);
-  if (S.chgu_local)
-    atomicOr(&S.chgu_loc[v >> 5], bit);
-  else if (P.flags & RAC_INCREMENTAL)
-    atomicOr(P.chgU + int64_t(slot_w) * nb + (v >> 5), bit);
+  uint32_t *ch = P.chg + (int64_t(slot_w) * P.flag_stride + s) * nb;
+  uint32_t *cu = P.chgU + int64_t(slot_w) * nb;
+  const bool incr = (P.flags & RAC_INCREMENTAL) != 0u;
+  if (xbits) {
+    atomicOr(ch + I, xbits);
+    if (S.chgu_local)
+      atomicOr(&S.chgu_loc[I], xbits);
+    else if (incr)
+      atomicOr(cu + I, xbits);
+  }
+  if (ybits) {
+    atomicOr(ch + J, ybits);
+    if (S.chgu_local)
+      atomicOr(&S.chgu_loc[J], ybits);
+    else if (incr)
+      atomicOr(cu + J, ybits);
+  }
 }
 
 // Bounded grid barrier over all CTAs (co-resident: cooperative launch).  The
@@ -286,7 +316,7 @@ __device__ __forceinline__ bool eval_state(Smem &S, const LaunchParams &P, int s
     if (k == 1 && !cached) Dy = input_word(P, y, Dy);
   }
   uint32_t racc = kFull;
-  bool rem = false;
+  uint32_t xbits = 0u;  // rows of this warp whose domain lost a value
   for (int r = sub; r < int(nrows); r += wps) {
     const uint32_t pm = hdr[r];
     if (pm == 0u) continue;
@@ -310,11 +340,12 @@ __device__ __forceinline__ bool eval_state(Smem &S, const LaunchParams &P, int s
     }
     const uint32_t keep_x = __reduce_and_sync(kFull, fwd) & Dx;  // warp-uniform
     if (keep_x != Dx) {
-      if (lane == 0) remove_values(S, P, s, slot_w, V.T, uint32_t(x), keep_x);
-      rem = true;
+      if (lane == 0) remove_value(S, P, s, V.T, uint32_t(x), keep_x);
+      xbits |= 1u << (row0 + uint32_t(r));
     }
     racc &= rev;
   }
+  bool rem = xbits != 0u;
   if (wps > 1) {
     const int buf = red_iter & 1;
     S.red[buf][warp][lane] = racc;
@@ -332,11 +363,14 @@ __device__ __forceinline__ bool eval_state(Smem &S, const LaunchParams &P, int s
   if (sub == 0 && y_ok) {
     const uint32_t keep_y = racc & Dy;
     if (keep_y != Dy) {
-      remove_values(S, P, s, slot_w, V.T, uint32_t(y), keep_y);
+      remove_value(S, P, s, V.T, uint32_t(y), keep_y);
       rem_y = true;
     }
   }
-  if (kLabel) rem = rem || __any_sync(kFull, rem_y);
+  const uint32_t ybits = __ballot_sync(kFull, rem_y);
+  if (lane == 0 && (xbits | ybits) != 0u)
+    mark_changed(S, P, s, slot_w, I, xbits, uint32_t(y) >> 5, ybits);
+  if (kLabel) rem = rem || ybits != 0u;
   return rem;
 }
 
@@ -891,7 +925,8 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
           }
         } else {
           // owner step: T still holds D_{k-2}; AND D_{k-1} into it where it
-          // differs (a warp per 32-variable block of a state, lane = variable)
+          // differs (a warp per 32-variable block of a state, lane = variable);
+          // a domain that sweep k-1 emptied is found here (see remove_value)
           const int64_t cw = int64_t(cta) * kConsumerWarps + warp;
           for (int64_t i = cw; i < int64_t(B) * N.nb; i += int64_t(G) * kConsumerWarps) {
             const int s = int(i / N.nb), blk = int(i % N.nb);
@@ -899,7 +934,9 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
             const int x = blk * 32 + lane;
             if (!((chg_word(S, P, slot_r, s, uint32_t(blk)) >> lane) & 1u)) continue;
             const StateView V = state_view(P, s, k);
-            atomicAnd(V.T + x, S.dom_cached ? S.dom[s * n + x] : ld_dom(V.C + x));
+            const uint32_t c = S.dom_cached ? S.dom[s * n + x] : ld_dom(V.C + x);
+            atomicAnd(V.T + x, c);
+            if (c == 0u) S.wipe_loc[s] = 1;
           }
         }
         // consumer group cg takes ring positions cg, cg + kGroups, ...
