@@ -329,48 +329,77 @@ __global__ void __launch_bounds__(kBThreads, 1) rac_batch_kernel(const BatchPara
       const int slot_w = int((base + k) % 3), slot_r = int((base + k + 2) % 3);
       const int slot_c = int((base + k + 1) % 3);
       if (is_producer) {
-        if (lane == 0) {
-          if (cta == 0) {  // barrier words last used two sweeps (or a launch) ago
+        {
+          if (cta == 0 && lane == 0) {  // barrier words last used two sweeps (or a launch) ago
             P.sync->bar[slot_c] = 0ull;
             P.sync->bar2[slot_c] = 0ull;
           }
           const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
-          bool ok = true;
-          int j = 0;
-          for (int g = cta; g < P.total_slabs; g += G) {
-            while (j + 1 < P.n_jobs && P.jobs[j + 1].slab_base <= g) ++j;
-            const BatchJob &J = P.jobs[j];
-            if (k >= 2 && ld_dom(P.job_alive + int64_t(slot_r) * P.n_jobs + j) == 0u) continue;
-            const int local = g - J.slab_base;
-            const SlabDesc sd = J.slabs[local];
-            if (incr) {
-              const uint32_t I = sd.ij & 0xFFFFu, Jb = sd.ij >> 16;
-              const uint32_t row0 = sd.rows & 0xFFu, nrows = sd.rows >> 8;
-              const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
-              const uint32_t *cu = P.chgU + int64_t(slot_r) * P.u_slot_words + J.u_off;
-              if (ld_dom(cu + Jb) == 0u && (ld_dom(cu + I) & rowmask) == 0u) continue;
+          bool ok = true;  // lane 0's wait outcomes
+          // the jobs 32 at a time (lane = job): alive ones in order; for each,
+          // this CTA's slabs of it (global slab g = cta + i G) 32 at a time
+          // (lane = slab): the Proposition-2 test, then lane 0 issues the
+          // copies of the slabs that pass
+          for (int j0 = 0; j0 < P.n_jobs && ok; j0 += 32) {
+            const int jl = j0 + lane;
+            bool alive = jl < P.n_jobs;
+            if (alive && k >= 2) alive = ld_dom(P.job_alive + int64_t(slot_r) * P.n_jobs + jl) != 0u;
+            for (uint32_t am = __ballot_sync(kFull, alive); am != 0u && ok; am &= am - 1u) {
+              const int j = j0 + __ffs(am) - 1;
+              const BatchJob &J = P.jobs[j];
+              const int sb = J.slab_base, se = J.slab_base + J.n_slabs;
+              const int first = sb + ((cta - sb) % G + G) % G;  // first g >= sb with g = cta (mod G)
+              for (int g0 = first; g0 < se && ok; g0 += 32 * G) {
+                const int g = g0 + lane * G;
+                bool act = g < se;
+                SlabDesc sd = {};
+                if (act) {
+                  sd = J.slabs[g - sb];
+                  if (incr) {
+                    const uint32_t I = sd.ij & 0xFFFFu, Jb = sd.ij >> 16;
+                    const uint32_t row0 = sd.rows & 0xFFu, nrows = sd.rows >> 8;
+                    const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
+                    const uint32_t *cu = P.chgU + int64_t(slot_r) * P.u_slot_words + J.u_off;
+                    act = ld_dom(cu + Jb) != 0u || (ld_dom(cu + I) & rowmask) != 0u;
+                  }
+                }
+                for (uint32_t sm = __ballot_sync(kFull, act); sm != 0u; sm &= sm - 1u) {
+                  const int src = __ffs(sm) - 1;
+                  const uint32_t off16 = __shfl_sync(kFull, sd.rel_off16, src);
+                  const uint32_t nbytes = __shfl_sync(kFull, sd.nbytes, src);
+                  const uint32_t ij = __shfl_sync(kFull, sd.ij, src);
+                  const uint32_t rows = __shfl_sync(kFull, sd.rows, src);
+                  uint32_t got = 1u;
+                  if (lane == 0) {
+                    const int stg = prod_it % kBStages;
+                    const uint32_t par = (prod_it / kBStages) & 1u;
+                    if (mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err, P.wait_limit_ns)) {
+                      S.stage[stg].job = j;
+                      S.stage[stg].slab = g0 + src * G - sb;
+                      S.stage[stg].ij = ij;
+                      S.stage[stg].rows = rows;
+                      mbar_arrive_expect_tx(&S.full[stg], nbytes);
+                      if (P.rel_evict_first)
+                        bulk_copy_g2s_hint(ring + size_t(stg) * kStageBytes, J.rel + size_t(off16),
+                                           nbytes, &S.full[stg], policy_evict_first());
+                      else
+                        bulk_copy_g2s(ring + size_t(stg) * kStageBytes, J.rel + size_t(off16),
+                                      nbytes, &S.full[stg]);
+                      ++prod_it;
+                    } else {
+                      got = 0u;
+                    }
+                  }
+                  if (__shfl_sync(kFull, got, 0) == 0u) {
+                    ok = false;
+                    break;
+                  }
+                }
+              }
             }
-            const int stg = prod_it % kBStages;
-            const uint32_t par = (prod_it / kBStages) & 1u;
-            if (!mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err,
-                           P.wait_limit_ns)) {
-              ok = false;
-              break;
-            }
-            S.stage[stg].job = j;
-            S.stage[stg].slab = local;
-            S.stage[stg].ij = sd.ij;
-            S.stage[stg].rows = sd.rows;
-            mbar_arrive_expect_tx(&S.full[stg], sd.nbytes);
-            if (P.rel_evict_first)
-              bulk_copy_g2s_hint(ring + size_t(stg) * kStageBytes, J.rel + size_t(sd.rel_off16),
-                                 sd.nbytes, &S.full[stg], policy_evict_first());
-            else
-              bulk_copy_g2s(ring + size_t(stg) * kStageBytes, J.rel + size_t(sd.rel_off16),
-                            sd.nbytes, &S.full[stg]);
-            ++prod_it;
           }
-          for (int e = 0; e < kBGroups && ok; ++e) {
+          // end of this sweep's slabs: one marker for each consumer group
+          for (int e = 0; e < kBGroups && ok && lane == 0; ++e) {
             const int stg = prod_it % kBStages;
             const uint32_t par = (prod_it / kBStages) & 1u;
             if (!mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err,
@@ -382,7 +411,7 @@ __global__ void __launch_bounds__(kBThreads, 1) rac_batch_kernel(const BatchPara
             mbar_arrive(&S.full[stg]);
             ++prod_it;
           }
-          if (!ok) S.abort = 1;
+          if (lane == 0 && !ok) S.abort = 1;
         }
       } else {
         // clear the slots written next sweep (last read two sweeps ago)
@@ -399,28 +428,37 @@ __global__ void __launch_bounds__(kBThreads, 1) rac_batch_kernel(const BatchPara
         for (int64_t i = cgtid; i < P.n_jobs; i += cgstride)
           P.job_alive[int64_t(slot_c) * P.n_jobs + i] = 0u;
         if (k >= 2) {
-          // owner step: T still holds D_{k-2}; AND D_{k-1} into it where it differs
-          for (int t = cta; t < T_total; t += G) {
+          // owner step: T still holds D_{k-2}; AND D_{k-1} into it where it
+          // differs.  A thread per word of the chg slot (32 variables of one
+          // state), over the whole grid; a domain sweep k-1 emptied is found
+          // here (see batch_remove).
+          const uint32_t *chs = P.chg + int64_t(slot_r) * P.chg_slot_words;
+          for (int64_t i = cgtid; i < P.chg_slot_words; i += cgstride) {
+            const uint32_t w = ld_dom(chs + i);
+            const int t = P.chg_state[i];
+            if (w == 0u) continue;
             if (ld_dom(P.st_info + t) & kInfoSweepMask) continue;  // finished state
-            const int nb = P.jobs[P.state_job[t]].nb;
-            const uint32_t *ch = P.chg + int64_t(slot_r) * P.chg_slot_words + P.chg_off[t];
-            for (int blk = tid; blk < nb; blk += kBConsumerWarps * 32) {
-              uint32_t w = ld_dom(ch + blk);
-              if (w == 0u) continue;
-              const BView V = bview(P, t, k);
-              bool emptied = false;  // a domain sweep k-1 emptied (see batch_remove)
-              while (w) {
-                const int b = __ffs(w) - 1;
-                w &= w - 1u;
-                const int x = blk * 32 + b;
-                const uint32_t c = ld_dom(V.C + x);
-                atomicAnd(V.T + x, c);
-                emptied = emptied || c == 0u;
+            const int blk = int(i - P.chg_off[t]);
+            const BView V = bview(P, t, k);
+            const uint32_t *Cb = V.C + blk * 32;
+            uint32_t *Tb = V.T + blk * 32;
+            bool emptied = false;
+#pragma unroll
+            for (int h = 0; h < 32; h += 16) {  // sixteen loads in flight
+              uint32_t c[16];
+#pragma unroll
+              for (int b = 0; b < 16; ++b) c[b] = ((w >> (h + b)) & 1u) ? ld_dom(Cb + h + b) : kFull;
+#pragma unroll
+              for (int b = 0; b < 16; ++b) {
+                if ((w >> (h + b)) & 1u) {
+                  atomicAnd(Tb + h + b, c[b]);
+                  emptied = emptied || c[b] == 0u;
+                }
               }
-              if (emptied) {
-                S.cta_wipe = 1;
-                atomicOr(P.wipe + int64_t(slot_w) * T_total + t, 1u);
-              }
+            }
+            if (emptied) {
+              S.cta_wipe = 1;
+              atomicOr(P.wipe + int64_t(slot_w) * T_total + t, 1u);
             }
           }
         }

@@ -185,6 +185,7 @@ struct BatchParams {
   uint32_t *st_info;           // [total_states], zero between launches
   uint32_t *job_alive;         // [3][n_jobs] some state of the job still runs
   const int32_t *state_job;    // job of state t
+  const int32_t *chg_state;    // state whose words hold word i of a chg slot
   int64_t chg_slot_words, u_slot_words;
   BatchSync *sync;
   int32_t max_sweeps;

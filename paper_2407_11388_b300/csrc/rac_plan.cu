@@ -23,6 +23,7 @@ struct rac_plan {
   BatchJob *jobs = nullptr;
   int64_t *state_off = nullptr, *scratch_off = nullptr, *chg_off = nullptr;
   int32_t *res_idx = nullptr, *state_job = nullptr;
+  int32_t *chg_state = nullptr;  // state of each word of a chg slot
   // device workspace (clean between launches)
   uint32_t *bufB = nullptr, *any = nullptr, *wipe = nullptr, *chg = nullptr, *chgU = nullptr;
   uint32_t *st_info = nullptr, *job_alive = nullptr;
@@ -36,7 +37,7 @@ namespace {
 struct PlanHost {
   std::vector<BatchJob> jobs;
   std::vector<int64_t> state_off, scratch_off, chg_off;
-  std::vector<int32_t> res_idx, state_job;
+  std::vector<int32_t> res_idx, state_job, chg_state;
   int32_t total_slabs = 0;
   int64_t chg_slot_words = 0, u_slot_words = 0, bufB_words = 0;
   size_t rel_bytes = 0;
@@ -92,6 +93,7 @@ rac_status build_host_plan(const rac_network *const *nets, int32_t n_nets, int32
       H.bufB_words += (int64_t(net->n) + 31) / 32 * 32;
       H.chg_off.push_back(H.chg_slot_words);
       H.chg_slot_words += net->nb;
+      H.chg_state.insert(H.chg_state.end(), size_t(net->nb), int32_t(H.state_job.size()));
       H.res_idx.push_back(item);
       H.state_job.push_back(job);
     }
@@ -110,6 +112,7 @@ cudaError_t dev_alloc(rac_plan *p, T **ptr, size_t count) {
 void plan_free(rac_plan *p) {
   if (!p) return;
   void *ptrs[] = {p->jobs, p->state_off, p->scratch_off, p->chg_off, p->res_idx, p->state_job,
+                  p->chg_state,
                   p->bufB, p->any, p->wipe, p->chg, p->chgU, p->st_info, p->job_alive, p->sync};
   for (void *q : ptrs) {
     if (!q) continue;
@@ -132,6 +135,7 @@ rac_status plan_upload(rac_plan *p, const PlanHost &H, cudaStream_t s) {
             dev_alloc(p, &p->chg_off, size_t(T)) == cudaSuccess &&
             dev_alloc(p, &p->res_idx, size_t(T)) == cudaSuccess &&
             dev_alloc(p, &p->state_job, size_t(T)) == cudaSuccess &&
+            dev_alloc(p, &p->chg_state, size_t(H.chg_slot_words)) == cudaSuccess &&
             dev_alloc(p, &p->bufB, size_t(H.bufB_words)) == cudaSuccess &&
             dev_alloc(p, &p->any, size_t(3 * T)) == cudaSuccess &&
             dev_alloc(p, &p->wipe, size_t(3 * T)) == cudaSuccess &&
@@ -158,6 +162,7 @@ rac_status plan_upload(rac_plan *p, const PlanHost &H, cudaStream_t s) {
   cp(p->chg_off, H.chg_off.data(), H.chg_off.size() * 8);
   cp(p->res_idx, H.res_idx.data(), H.res_idx.size() * 4);
   cp(p->state_job, H.state_job.data(), H.state_job.size() * 4);
+  cp(p->chg_state, H.chg_state.data(), H.chg_state.size() * 4);
   // the state every launch expects: scratch domains all ones, the rest zero
   zero(p->bufB, 0xFF, size_t(H.bufB_words) * 4);
   zero(p->any, 0, size_t(3 * T) * 4);
@@ -203,6 +208,7 @@ rac_status plan_launch(const rac_plan *p, const uint32_t *dom_in, uint32_t *dom_
   P.st_info = p->st_info;
   P.job_alive = p->job_alive;
   P.state_job = p->state_job;
+  P.chg_state = p->chg_state;
   P.chg_slot_words = p->chg_slot_words;
   P.u_slot_words = p->u_slot_words;
   P.sync = p->sync;

@@ -157,3 +157,37 @@ def test_tile_rows_do_not_change_results(rows):
                 n = nets_np[i].n
                 assert np.array_equal(got1[0][offs[j]:offs[j] + n], got[0][offs[j]:offs[j] + n])
                 assert got1[1][a] == got[1][j] and got1[2][a] == got[2][j]
+
+
+@pytest.mark.parametrize("flags", [0, rac.INCREMENTAL, rac.STOP_ON_WIPEOUT])
+def test_batch_wipe_split_over_slabs(flags):
+    """A domain emptied only by the AND of two slabs' removals (see
+    test_parity_gpu._split_wipe_network), batched with a random network, in
+    the batched kernel."""
+    from test_parity_gpu import _split_wipe_network
+    n, d, scope, rel, dom = _split_wipe_network()
+    other = racgen.random_network(8, 1, 300, 12, 0.6, 0.3)
+    shapes = [(n, d, scope, rel), (other.n, other.d, other.scope, other.rel)]
+    doms, items, offs, pos = [], [], [], 0
+    for s in range(6):
+        i = s % 2
+        dm = dom.copy() if i == 0 else racgen.assignment_state(8, 1, s, other.n, other.d)
+        if i == 0 and s >= 2:
+            dm[7] = 3
+        doms.append(dm)
+        items.append(i)
+        offs.append(pos)
+        pos += shapes[i][0]
+    flat = np.concatenate(doms).astype(np.uint32)
+    items, offs = np.array(items, np.int32), np.array(offs, np.int64)
+    nets = [rac.Network(*sh) for sh in shapes]
+    with rac.Plan(nets, items, offs) as plan:
+        out, its, sts = _run(nets, items, offs, flat, flags, plan=plan)
+    for j in range(len(items)):
+        nn, dd, sc, rl = shapes[items[j]]
+        ro, ri, rs = oracle.rac(nn, dd, sc, rl, doms[j],
+                                stop_on_wipeout=bool(flags & rac.STOP_ON_WIPEOUT), threads=8)
+        o = offs[j]
+        assert np.array_equal(out[o:o + nn], ro) and its[j] == ri and sts[j] == rs, j
+        if items[j] == 0:
+            assert rs == rac.WIPEOUT and ri == (1 if flags & rac.STOP_ON_WIPEOUT else 3)

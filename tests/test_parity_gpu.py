@@ -269,3 +269,30 @@ def test_many_launches_on_one_workspace():
             assert not np.any(got[2] == rac.EBARRIER), "launch %d gave up a wait" % rep
             assert_same(got, want, "launch %d (B=%d flags=%d)" % (rep, B, flags))
     assert refs[1].max() >= 3
+
+
+def _split_wipe_network():
+    """Variable 0 is emptied by the AND of two removals from different slabs,
+    neither of which empties it alone: (0, 40) keeps {0, 1} and (0, 65) keeps
+    {2, 3} while variables 40 and 65 hold the value 0.  By Eq. 1 the first
+    sweep empties variable 0, the second empties 40 and 65 (their only value
+    lost its support), the third removes nothing: 3 sweeps, wiped out; with
+    stop-on-wipeout the run ends after sweep 1."""
+    n, d = 70, 4
+    scope = np.array([[0, 40], [0, 65], [3, 50], [33, 66]], np.int32)
+    rel = np.array([[1, 1, 0, 0], [0, 0, 1, 1], [15, 15, 15, 15], [15, 15, 15, 15]], np.uint32)
+    dom = np.full(n, 15, np.uint32)
+    dom[40] = dom[65] = 1
+    return n, d, scope, rel, dom
+
+
+@pytest.mark.parametrize("B", [1, 5])
+def test_wipe_split_over_slabs(B):
+    n, d, scope, rel, dom = _split_wipe_network()
+    doms = np.tile(dom, (B, 1))
+    doms[1:, 7] = 3  # the other states differ elsewhere
+    for flags in FLAG_SETS:
+        ref = oracle_enforce(n, d, scope, rel, doms, flags)
+        stop = bool(flags & rac.STOP_ON_WIPEOUT)
+        assert list(ref[1]) == [1 if stop else 3] * B and list(ref[2]) == [rac.WIPEOUT] * B
+        assert_same(gpu_enforce(n, d, scope, rel, doms, flags), ref, "split wipe-out")
