@@ -374,6 +374,77 @@ __device__ __forceinline__ bool eval_state(Smem &S, const LaunchParams &P, int s
   return rem;
 }
 
+// Evaluate two states s1, s2 on one slab in one pass (a warp that owns whole
+// states): each relation chunk is read from shared memory once for both, and
+// the two support tests give the warp independent work.  Dy*, Dx*l as in
+// eval_state with kPre.  Returns, in rem1 / rem2, whether each removed a
+// value.
+template <int Q>
+__device__ __forceinline__ void eval_pair(Smem &S, const LaunchParams &P, int s1, int s2, int k,
+                                          int slot_w, const uint32_t *hdr, const uint4 *rel,
+                                          uint32_t I, uint32_t row0, uint32_t nrows, int y,
+                                          bool y_ok, uint32_t Dy1, uint32_t Dx1l, uint32_t Dy2,
+                                          uint32_t Dx2l, int lane, bool &rem1, bool &rem2) {
+  const NetDev &N = P.net;
+  const uint32_t dfull = N.d >= 32 ? kFull : ((1u << N.d) - 1u);
+  uint32_t *T1 = state_view(P, s1, k).T;
+  uint32_t *T2 = state_view(P, s2, k).T;
+  uint32_t racc1 = kFull, racc2 = kFull, xb1 = 0u, xb2 = 0u;
+  for (int r = 0; r < int(nrows); ++r) {
+    const uint32_t pm = hdr[r];
+    if (pm == 0u) continue;
+    const uint32_t Dx1 = __shfl_sync(kFull, Dx1l, r);
+    const uint32_t Dx2 = __shfl_sync(kFull, Dx2l, r);
+    uint32_t f1 = kFull, v1 = kFull, f2 = kFull, v2 = kFull;
+    if ((pm >> lane) & 1u) {
+      const uint32_t t = __popc(pm & lanemask_lt());
+      const uint4 *mine = rel + hdr[nrows + r] * Q + t;
+      if (Dx1 == dfull && Dx2 == dfull)
+        support_relation_pair<Q, true>(mine, __popc(pm), Dx1, Dy1, Dx2, Dy2, f1, v1, f2, v2);
+      else
+        support_relation_pair<Q, false>(mine, __popc(pm), Dx1, Dy1, Dx2, Dy2, f1, v1, f2, v2);
+    }
+    const uint32_t keep1 = __reduce_and_sync(kFull, f1) & Dx1;  // warp-uniform
+    const uint32_t keep2 = __reduce_and_sync(kFull, f2) & Dx2;
+    const uint32_t x = I * 32u + row0 + uint32_t(r);
+    if (keep1 != Dx1) {
+      if (lane == 0) remove_value(S, P, s1, T1, x, keep1);
+      xb1 |= 1u << (row0 + uint32_t(r));
+    }
+    if (keep2 != Dx2) {
+      if (lane == 0) remove_value(S, P, s2, T2, x, keep2);
+      xb2 |= 1u << (row0 + uint32_t(r));
+    }
+    racc1 &= v1;
+    racc2 &= v2;
+  }
+  bool ry1 = false, ry2 = false;
+  if (y_ok) {
+    const uint32_t keep1 = racc1 & Dy1, keep2 = racc2 & Dy2;
+    if (keep1 != Dy1) {
+      remove_value(S, P, s1, T1, uint32_t(y), keep1);
+      ry1 = true;
+    }
+    if (keep2 != Dy2) {
+      remove_value(S, P, s2, T2, uint32_t(y), keep2);
+      ry2 = true;
+    }
+  }
+  const uint32_t yb1 = __ballot_sync(kFull, ry1), yb2 = __ballot_sync(kFull, ry2);
+  const uint32_t J = uint32_t(y) >> 5;
+  if (lane == 0 && (xb1 | yb1) != 0u) mark_changed(S, P, s1, slot_w, I, xb1, J, yb1);
+  if (lane == 0 && (xb2 | yb2) != 0u) mark_changed(S, P, s2, slot_w, I, xb2, J, yb2);
+  rem1 = (xb1 | yb1) != 0u;
+  rem2 = (xb2 | yb2) != 0u;
+}
+
+// Next state of a mask (bit i: state c0 + i), or -1.
+__device__ __forceinline__ int pop_state(uint32_t &m) {
+  const int i = m ? __ffs(m) - 1 : -1;
+  m &= m - 1u;
+  return i;
+}
+
 // The decisions of rac_enforce_learned for the slab in ring stage `stg`,
 // taken by the producer warp right after it issued the slab's copy, so that
 // they run ahead of the consumers (every sweep; the first one counts a
@@ -550,19 +621,8 @@ __device__ void consume_slab_scored(Smem &S, const LaunchParams &P, const uint32
     if (ev_all == 0u) continue;
     uint32_t m = warp_share(ev_all, g, groups, lane);
     if (m == 0u) continue;
-    int i = __ffs(m) - 1;
-    m &= m - 1u;
-    uint32_t Dy, Dxl;
-    load_words(S, P, c0 + i, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
-    for (;;) {
-      const int inext = m ? __ffs(m) - 1 : -1;
-      if (inext >= 0) m &= m - 1u;
-      uint32_t Dy_n = 0u, Dx_n = 0u;
-      if (inext >= 0) load_words(S, P, c0 + inext, k, cached, y, y_ok, x_l, x_ok, Dy_n, Dx_n);
-      const int s = c0 + i;
-      const bool removed = eval_state<Q, true, true>(S, P, s, k, slot_w, hdr, rel, I, row0, nrows,
-                                                     y, y_ok, cached, Dy, Dxl, warp, lane, cg, g,
-                                                     sub, wps, red_iter);
+    // an evaluated record gets its label
+    auto label = [&](int s, bool removed) {
       if (recording && sub == 0 && lane == 0) {
         const uint32_t need = dec[32 + (s >> 5)];
         if ((need >> (s & 31)) & 1u) {
@@ -571,10 +631,45 @@ __device__ void consume_slab_scored(Smem &S, const LaunchParams &P, const uint32
           if (r < P.tr_cap) P.tr_y[r] = removed ? 1.0f : 0.0f;
         }
       }
-      if (inext < 0) break;
-      i = inext;
-      Dy = Dy_n;
-      Dxl = Dx_n;
+    };
+    if (wps > 1) {  // fewer than four states: a state's rows over several warps
+      for (int i = pop_state(m); i >= 0; i = pop_state(m)) {
+        uint32_t Dy, Dxl;
+        load_words(S, P, c0 + i, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
+        label(c0 + i, eval_state<Q, true, true>(S, P, c0 + i, k, slot_w, hdr, rel, I, row0, nrows,
+                                                y, y_ok, cached, Dy, Dxl, warp, lane, cg, g, sub,
+                                                wps, red_iter));
+      }
+      continue;
+    }
+    // two states per pass; the next pair's words load during this one
+    int i1 = pop_state(m), i2 = pop_state(m);
+    uint32_t Dy1, Dx1, Dy2 = 0u, Dx2 = 0u;
+    load_words(S, P, c0 + i1, k, cached, y, y_ok, x_l, x_ok, Dy1, Dx1);
+    if (i2 >= 0) load_words(S, P, c0 + i2, k, cached, y, y_ok, x_l, x_ok, Dy2, Dx2);
+    for (;;) {
+      const int n1 = pop_state(m), n2 = pop_state(m);
+      uint32_t Ny1 = 0u, Nx1 = 0u, Ny2 = 0u, Nx2 = 0u;
+      if (n1 >= 0) load_words(S, P, c0 + n1, k, cached, y, y_ok, x_l, x_ok, Ny1, Nx1);
+      if (n2 >= 0) load_words(S, P, c0 + n2, k, cached, y, y_ok, x_l, x_ok, Ny2, Nx2);
+      if (i2 >= 0) {
+        bool r1, r2;
+        eval_pair<Q>(S, P, c0 + i1, c0 + i2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, Dy1,
+                     Dx1, Dy2, Dx2, lane, r1, r2);
+        label(c0 + i1, r1);
+        label(c0 + i2, r2);
+      } else {
+        label(c0 + i1, eval_state<Q, true, true>(S, P, c0 + i1, k, slot_w, hdr, rel, I, row0,
+                                                 nrows, y, y_ok, cached, Dy1, Dx1, warp, lane, cg,
+                                                 g, sub, wps, red_iter));
+      }
+      if (n1 < 0) break;
+      i1 = n1;
+      i2 = n2;
+      Dy1 = Ny1;
+      Dx1 = Nx1;
+      Dy2 = Ny2;
+      Dx2 = Nx2;
     }
   }
 }
@@ -751,21 +846,32 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
       if (am == 0u) continue;
       am = warp_share(am, g, groups, lane);
       if (am == 0u) continue;
-      int i = __ffs(am) - 1;
-      am &= am - 1u;
-      uint32_t Dy, Dxl;
-      load_words(S, P, c0 + i, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
+      // two states per pass (eval_pair); the next pair's words load during
+      // this one
+      int i1 = pop_state(am), i2 = pop_state(am);
+      uint32_t Dy1, Dx1, Dy2 = 0u, Dx2 = 0u;
+      load_words(S, P, c0 + i1, k, cached, y, y_ok, x_l, x_ok, Dy1, Dx1);
+      if (i2 >= 0) load_words(S, P, c0 + i2, k, cached, y, y_ok, x_l, x_ok, Dy2, Dx2);
       for (;;) {
-        const int inext = am ? __ffs(am) - 1 : -1;
-        if (inext >= 0) am &= am - 1u;
-        uint32_t Dy_n = 0u, Dx_n = 0u;
-        if (inext >= 0) load_words(S, P, c0 + inext, k, cached, y, y_ok, x_l, x_ok, Dy_n, Dx_n);
-        eval_state<Q, false, true>(S, P, c0 + i, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok,
-                                   cached, Dy, Dxl, warp, lane, cg, g, sub, wps, red_iter);
-        if (inext < 0) break;
-        i = inext;
-        Dy = Dy_n;
-        Dxl = Dx_n;
+        const int n1 = pop_state(am), n2 = pop_state(am);
+        uint32_t Ny1 = 0u, Nx1 = 0u, Ny2 = 0u, Nx2 = 0u;
+        if (n1 >= 0) load_words(S, P, c0 + n1, k, cached, y, y_ok, x_l, x_ok, Ny1, Nx1);
+        if (n2 >= 0) load_words(S, P, c0 + n2, k, cached, y, y_ok, x_l, x_ok, Ny2, Nx2);
+        if (i2 >= 0) {
+          bool r1, r2;
+          eval_pair<Q>(S, P, c0 + i1, c0 + i2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, Dy1,
+                       Dx1, Dy2, Dx2, lane, r1, r2);
+        } else {
+          eval_state<Q, false, true>(S, P, c0 + i1, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok,
+                                     cached, Dy1, Dx1, warp, lane, cg, g, sub, wps, red_iter);
+        }
+        if (n1 < 0) break;
+        i1 = n1;
+        i2 = n2;
+        Dy1 = Ny1;
+        Dx1 = Nx1;
+        Dy2 = Ny2;
+        Dx2 = Nx2;
       }
     }
   }

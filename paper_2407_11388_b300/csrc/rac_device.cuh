@@ -148,5 +148,45 @@ __device__ __forceinline__ void support_relation(const uint4 *rel, uint32_t stri
   rev = r0 | r1;
 }
 
+// The support test of one relation for two domain states at once (Dx1, Dy1)
+// and (Dx2, Dy2): each 16-byte chunk is read once and serves both.  Same
+// results as support_relation for each state.
+template <int Q, bool kDxFull>
+__device__ __forceinline__ void support_relation_pair(const uint4 *rel, uint32_t stride,
+                                                      uint32_t Dx1, uint32_t Dy1, uint32_t Dx2,
+                                                      uint32_t Dy2, uint32_t &fwd1, uint32_t &rev1,
+                                                      uint32_t &fwd2, uint32_t &rev2) {
+  uint32_t f1 = 0, g1 = 0, f2 = 0, g2 = 0, r1 = 0, q1 = 0, r2 = 0, q2 = 0;
+#pragma unroll
+  for (int c = 0; c < Q; ++c) {
+    const uint4 w = rel[c * stride];
+    if ((w.x & Dy1) != 0u) f1 |= 1u << (4 * c + 0);
+    if ((w.y & Dy1) != 0u) g1 |= 1u << (4 * c + 1);
+    if ((w.z & Dy1) != 0u) f1 |= 1u << (4 * c + 2);
+    if ((w.w & Dy1) != 0u) g1 |= 1u << (4 * c + 3);
+    if ((w.x & Dy2) != 0u) f2 |= 1u << (4 * c + 0);
+    if ((w.y & Dy2) != 0u) g2 |= 1u << (4 * c + 1);
+    if ((w.z & Dy2) != 0u) f2 |= 1u << (4 * c + 2);
+    if ((w.w & Dy2) != 0u) g2 |= 1u << (4 * c + 3);
+    if (kDxFull) {  // both row domains full: every row of R counts for both
+      r1 |= w.x | w.z;
+      q1 |= w.y | w.w;
+    } else {
+      r1 |= w.x & (0u - ((Dx1 >> (4 * c + 0)) & 1u));
+      q1 |= w.y & (0u - ((Dx1 >> (4 * c + 1)) & 1u));
+      r1 |= w.z & (0u - ((Dx1 >> (4 * c + 2)) & 1u));
+      q1 |= w.w & (0u - ((Dx1 >> (4 * c + 3)) & 1u));
+      r2 |= w.x & (0u - ((Dx2 >> (4 * c + 0)) & 1u));
+      q2 |= w.y & (0u - ((Dx2 >> (4 * c + 1)) & 1u));
+      r2 |= w.z & (0u - ((Dx2 >> (4 * c + 2)) & 1u));
+      q2 |= w.w & (0u - ((Dx2 >> (4 * c + 3)) & 1u));
+    }
+  }
+  fwd1 = f1 | g1;
+  fwd2 = f2 | g2;
+  rev1 = r1 | q1;
+  rev2 = kDxFull ? rev1 : (r2 | q2);
+}
+
 }  // namespace dev
 }  // namespace rac
