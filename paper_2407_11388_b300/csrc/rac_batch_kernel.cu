@@ -157,13 +157,82 @@ __device__ __forceinline__ void batch_mark(BSmem &S, const BatchParams &P, const
   }
 }
 
+// One or two states (kTwo) of job J on one slab in one pass: each relation
+// chunk is read once for both, and the two support tests give the warp
+// independent work.  State u: index t_u, D_k buffer T_u, chg offset co_u,
+// column word Dy_u and row words Dx_ul (lane r: row r).
+template <int Q, bool kTwo>
+__device__ __forceinline__ void batch_eval(BSmem &S, const BatchParams &P, const BatchJob &J,
+                                           int slot_w, const uint32_t *hdr, const uint4 *rel,
+                                           uint32_t I, uint32_t Jb, uint32_t row0, uint32_t nrows,
+                                           int y, bool y_ok, int lane, int t1, uint32_t *T1,
+                                           int64_t co1, uint32_t Dy1, uint32_t Dx1l, int t2,
+                                           uint32_t *T2, int64_t co2, uint32_t Dy2,
+                                           uint32_t Dx2l) {
+  const uint32_t dfull = J.d >= 32 ? kFull : ((1u << J.d) - 1u);
+  uint32_t racc1 = kFull, racc2 = kFull, xb1 = 0u, xb2 = 0u;
+  for (int r = 0; r < int(nrows); ++r) {
+    const uint32_t pm = hdr[r];
+    if (pm == 0u) continue;
+    const uint32_t Dx1 = __shfl_sync(kFull, Dx1l, r);
+    const uint32_t Dx2 = kTwo ? __shfl_sync(kFull, Dx2l, r) : 0u;
+    uint32_t f1 = kFull, v1 = kFull, f2 = kFull, v2 = kFull;
+    if ((pm >> lane) & 1u) {
+      const uint32_t tt = __popc(pm & lanemask_lt());
+      const uint4 *mine = rel + hdr[nrows + r] * uint32_t(Q) + tt;
+      if (!kTwo)
+        support_dispatch_q<Q>(mine, __popc(pm), Dx1, Dy1, dfull, f1, v1);
+      else if (Dx1 == dfull && Dx2 == dfull)
+        support_relation_pair<Q, true>(mine, __popc(pm), Dx1, Dy1, Dx2, Dy2, f1, v1, f2, v2);
+      else
+        support_relation_pair<Q, false>(mine, __popc(pm), Dx1, Dy1, Dx2, Dy2, f1, v1, f2, v2);
+    }
+    const uint32_t x = I * 32u + row0 + uint32_t(r);
+    const uint32_t keep1 = __reduce_and_sync(kFull, f1) & Dx1;
+    if (keep1 != Dx1) {
+      if (lane == 0) batch_remove(S, P, t1, slot_w, T1, x, keep1);
+      xb1 |= 1u << (row0 + uint32_t(r));
+    }
+    racc1 &= v1;
+    if (kTwo) {
+      const uint32_t keep2 = __reduce_and_sync(kFull, f2) & Dx2;
+      if (keep2 != Dx2) {
+        if (lane == 0) batch_remove(S, P, t2, slot_w, T2, x, keep2);
+        xb2 |= 1u << (row0 + uint32_t(r));
+      }
+      racc2 &= v2;
+    }
+  }
+  bool ry1 = false, ry2 = false;
+  if (y_ok) {
+    const uint32_t keep1 = racc1 & Dy1;
+    if (keep1 != Dy1) {
+      batch_remove(S, P, t1, slot_w, T1, uint32_t(y), keep1);
+      ry1 = true;
+    }
+    if (kTwo) {
+      const uint32_t keep2 = racc2 & Dy2;
+      if (keep2 != Dy2) {
+        batch_remove(S, P, t2, slot_w, T2, uint32_t(y), keep2);
+        ry2 = true;
+      }
+    }
+  }
+  const uint32_t yb1 = __ballot_sync(kFull, ry1);
+  if (lane == 0 && (xb1 | yb1) != 0u) batch_mark(S, P, J, t1, co1, slot_w, I, xb1, Jb, yb1);
+  if (kTwo) {
+    const uint32_t yb2 = __ballot_sync(kFull, ry2);
+    if (lane == 0 && (xb2 | yb2) != 0u) batch_mark(S, P, J, t2, co2, slot_w, I, xb2, Jb, yb2);
+  }
+}
+
 // One slab of job J for every running state of J, by one consumer group.  The
 // job's states go 32 at a time (lane i checks state base + i: running, and
 // with RAC_INCREMENTAL a Proposition-2 candidate); warp lw of the group takes
 // those of rank lw, lw + 4, ... among the ones to evaluate, so the group's
-// warps get equal shares, and evaluates them one after the other: each
+// warps get equal shares, and evaluates them two per pass (batch_eval): each
 // state's column words (lane = column) and row words (lane = row) come in two
-// coalesced loads, issued for the next state while the current one is
+// coalesced loads, issued for the next pair while the current one is
 // evaluated.
 template <int Q>
 __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &J,
@@ -178,9 +247,10 @@ __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &
   const bool y_ok = y < n;
   const int x_l = int(I) * 32 + int(row0) + lane;
   const bool x_ok = lane < int(nrows) && x_l < n;
-  const uint32_t dfull = J.d >= 32 ? kFull : ((1u << J.d) - 1u);
   const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
   const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
+  const uint32_t *Cbase = k == 1 ? P.dom_in : ((k & 1) ? P.dom_out : P.bufB);
+  uint32_t *Tbase = (k == 1 || (k & 1)) ? P.bufB : P.dom_out;
   for (int base = 0; base < J.n_states; base += 32) {
     // lane i: state t = state_base + base + i
     const int q = base + lane;
@@ -206,59 +276,49 @@ __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &
     // this warp's share: the states of rank lw, lw + 4, ... among them
     am = __ballot_sync(kFull, act && __popc(am & lanemask_lt()) % kBGroupWarps == lw);
     if (am == 0u) continue;
-    // words of the first state
-    int i = __ffs(am) - 1;
-    am &= am - 1u;
+    auto pop = [&]() {
+      const int i = am ? __ffs(am) - 1 : -1;
+      am &= am - 1u;
+      return i;
+    };
+    // the words of the state in lane ii (every lane must call this)
     auto fetch = [&](int ii, uint32_t &dy, uint32_t &dx) {
-      const int64_t co = __shfl_sync(kFull, c_off, ii);
-      const uint32_t *C = (k == 1 ? P.dom_in : ((k & 1) ? P.dom_out : P.bufB)) + co;
+      const int64_t co = __shfl_sync(kFull, c_off, ii < 0 ? 0 : ii);
+      dy = dx = 0u;
+      if (ii < 0) return;
+      const uint32_t *C = Cbase + co;
       dy = y_ok ? ld_dom(C + y) : 0u;
       dx = x_ok ? ld_dom(C + x_l) : 0u;
     };
-    uint32_t Dy, Dxl;
-    fetch(i, Dy, Dxl);
+    int i1 = pop(), i2 = pop();
+    uint32_t Dy1, Dx1, Dy2, Dx2;
+    fetch(i1, Dy1, Dx1);
+    fetch(i2, Dy2, Dx2);
     for (;;) {
-      const int inext = am ? __ffs(am) - 1 : -1;
-      if (inext >= 0) am &= am - 1u;
-      uint32_t Dy_n = 0u, Dx_n = 0u;
-      if (inext >= 0) fetch(inext, Dy_n, Dx_n);  // in flight during this evaluation
-      const int ts = __shfl_sync(kFull, t, i);
-      const int64_t to = __shfl_sync(kFull, t_off, i);
-      const int64_t co = __shfl_sync(kFull, chgoff, i);
-      uint32_t *T = ((k == 1 || (k & 1)) ? P.bufB : P.dom_out) + to;
-      uint32_t racc = kFull, xbits = 0u;
-      for (int r = 0; r < int(nrows); ++r) {
-        const uint32_t pm = hdr[r];
-        if (pm == 0u) continue;
-        const uint32_t Dx = __shfl_sync(kFull, Dxl, r);
-        uint32_t fwd = kFull, rev = kFull;
-        if ((pm >> lane) & 1u) {
-          const uint32_t tt = __popc(pm & lanemask_lt());
-          support_dispatch_q<Q>(rel + hdr[nrows + r] * uint32_t(Q) + tt, __popc(pm), Dx, Dy,
-                                dfull, fwd, rev);
-        }
-        const uint32_t keep_x = __reduce_and_sync(kFull, fwd) & Dx;
-        if (keep_x != Dx) {
-          if (lane == 0) batch_remove(S, P, ts, slot_w, T, I * 32u + row0 + uint32_t(r), keep_x);
-          xbits |= 1u << (row0 + uint32_t(r));
-        }
-        racc &= rev;
-      }
-      bool rem_y = false;
-      if (y_ok) {
-        const uint32_t keep_y = racc & Dy;
-        if (keep_y != Dy) {
-          batch_remove(S, P, ts, slot_w, T, uint32_t(y), keep_y);
-          rem_y = true;
-        }
-      }
-      const uint32_t ybits = __ballot_sync(kFull, rem_y);
-      if (lane == 0 && (xbits | ybits) != 0u)
-        batch_mark(S, P, J, ts, co, slot_w, I, xbits, Jb, ybits);
-      if (inext < 0) break;
-      i = inext;
-      Dy = Dy_n;
-      Dxl = Dx_n;
+      const int n1 = pop(), n2 = pop();
+      uint32_t Ny1, Nx1, Ny2, Nx2;
+      fetch(n1, Ny1, Nx1);  // in flight during this evaluation
+      fetch(n2, Ny2, Nx2);
+      const int t1 = __shfl_sync(kFull, t, i1);
+      const int64_t to1 = __shfl_sync(kFull, t_off, i1);
+      const int64_t co1 = __shfl_sync(kFull, chgoff, i1);
+      const int j2 = i2 < 0 ? i1 : i2;
+      const int t2 = __shfl_sync(kFull, t, j2);
+      const int64_t to2 = __shfl_sync(kFull, t_off, j2);
+      const int64_t co2 = __shfl_sync(kFull, chgoff, j2);
+      if (i2 >= 0)
+        batch_eval<Q, true>(S, P, J, slot_w, hdr, rel, I, Jb, row0, nrows, y, y_ok, lane, t1,
+                            Tbase + to1, co1, Dy1, Dx1, t2, Tbase + to2, co2, Dy2, Dx2);
+      else
+        batch_eval<Q, false>(S, P, J, slot_w, hdr, rel, I, Jb, row0, nrows, y, y_ok, lane, t1,
+                             Tbase + to1, co1, Dy1, Dx1, -1, nullptr, 0, 0u, 0u);
+      if (n1 < 0) break;
+      i1 = n1;
+      i2 = n2;
+      Dy1 = Ny1;
+      Dx1 = Nx1;
+      Dy2 = Ny2;
+      Dx2 = Nx2;
     }
   }
 }
