@@ -52,6 +52,8 @@ WORKLOADS = {
     # 256 networks, n ~ U{50..800}, d ~ U{8..32}, density ~ U[0.3,1],
     # tightness ~ U[0.2,0.4], 64 assignment states each: one launch per step
     "batch256_x64": dict(batch=True, networks=256, states_per_net=64),
+    # the same generator at a size small enough for full profiler captures
+    "batch32_x16": dict(batch=True, networks=32, states_per_net=16),
 }
 DEFAULT_WORKLOAD = "dense_n500_d20"
 
