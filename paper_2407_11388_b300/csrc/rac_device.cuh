@@ -118,12 +118,23 @@ __device__ __forceinline__ void named_bar(int id, int nthreads) {
 // Domain words change between sweeps through L2 atomics: read them at L2.
 __device__ __forceinline__ uint32_t ld_dom(const uint32_t *p) { return __ldcg(p); }
 
+// r |= w when (m & bit) != 0, as a test into a predicate and a predicated OR
+// (the many-state paths: fewer integer instructions than forming a mask)
+__device__ __forceinline__ void or_if_bit(uint32_t &r, uint32_t w, uint32_t m, uint32_t bit) {
+  asm("{\n .reg .pred p;\n .reg .b32 t;\n and.b32 t, %1, %2;\n setp.ne.u32 p, t, 0;\n"
+      " @p or.b32 %0, %0, %3;\n}\n"
+      : "+r"(r)
+      : "r"(m), "r"(bit), "r"(w));
+}
+
 // The support test of one relation, rows a = 0..4Q-1 (padding rows are 0),
 // read as Q 16-byte chunks `stride` chunks apart:
 //   fwd bit a  = (R[a] & Dy) != 0        (Sup_xy[a] > 0, Fig. 1)
 //   rev        = OR over a in Dx of R[a] (bit b: (y,b) has a support in Dx)
-// Two independent accumulators per result keep the OR chains short.
-template <int Q, bool kDxFull>
+// Two independent accumulators per result keep the OR chains short.  kPred:
+// the reverse rows of a partial D_x through or_if_bit (the single-state
+// launches keep the mask form, which their code layout favours).
+template <int Q, bool kDxFull, bool kPred = false>
 __device__ __forceinline__ void support_relation(const uint4 *rel, uint32_t stride, uint32_t Dx,
                                                  uint32_t Dy, uint32_t &fwd, uint32_t &rev) {
   uint32_t f0 = 0, f1 = 0, r0 = 0, r1 = 0;
@@ -137,6 +148,11 @@ __device__ __forceinline__ void support_relation(const uint4 *rel, uint32_t stri
     if (kDxFull) {  // every row of R is in Dx (rows >= d are zero)
       r0 |= w.x | w.z;
       r1 |= w.y | w.w;
+    } else if (kPred) {
+      or_if_bit(r0, w.x, Dx, 1u << (4 * c + 0));
+      or_if_bit(r1, w.y, Dx, 1u << (4 * c + 1));
+      or_if_bit(r0, w.z, Dx, 1u << (4 * c + 2));
+      or_if_bit(r1, w.w, Dx, 1u << (4 * c + 3));
     } else {
       r0 |= w.x & (0u - ((Dx >> (4 * c + 0)) & 1u));
       r1 |= w.y & (0u - ((Dx >> (4 * c + 1)) & 1u));
@@ -172,14 +188,14 @@ __device__ __forceinline__ void support_relation_pair(const uint4 *rel, uint32_t
       r1 |= w.x | w.z;
       q1 |= w.y | w.w;
     } else {
-      r1 |= w.x & (0u - ((Dx1 >> (4 * c + 0)) & 1u));
-      q1 |= w.y & (0u - ((Dx1 >> (4 * c + 1)) & 1u));
-      r1 |= w.z & (0u - ((Dx1 >> (4 * c + 2)) & 1u));
-      q1 |= w.w & (0u - ((Dx1 >> (4 * c + 3)) & 1u));
-      r2 |= w.x & (0u - ((Dx2 >> (4 * c + 0)) & 1u));
-      q2 |= w.y & (0u - ((Dx2 >> (4 * c + 1)) & 1u));
-      r2 |= w.z & (0u - ((Dx2 >> (4 * c + 2)) & 1u));
-      q2 |= w.w & (0u - ((Dx2 >> (4 * c + 3)) & 1u));
+      or_if_bit(r1, w.x, Dx1, 1u << (4 * c + 0));
+      or_if_bit(q1, w.y, Dx1, 1u << (4 * c + 1));
+      or_if_bit(r1, w.z, Dx1, 1u << (4 * c + 2));
+      or_if_bit(q1, w.w, Dx1, 1u << (4 * c + 3));
+      or_if_bit(r2, w.x, Dx2, 1u << (4 * c + 0));
+      or_if_bit(q2, w.y, Dx2, 1u << (4 * c + 1));
+      or_if_bit(r2, w.z, Dx2, 1u << (4 * c + 2));
+      or_if_bit(q2, w.w, Dx2, 1u << (4 * c + 3));
     }
   }
   fwd1 = f1 | g1;
