@@ -118,8 +118,10 @@ __device__ __forceinline__ void named_bar(int id, int nthreads) {
 // Domain words change between sweeps through L2 atomics: read them at L2.
 __device__ __forceinline__ uint32_t ld_dom(const uint32_t *p) { return __ldcg(p); }
 
-// r |= w when (m & bit) != 0, as a test into a predicate and a predicated OR
-// (the many-state paths: fewer integer instructions than forming a mask)
+// r |= w when (m & bit) != 0, as a test into a predicate and a predicated OR:
+// on the many-state paths both the forward test ((R[a] & D_y) != 0 sets bit
+// a) and the masked reverse OR take this form, with fewer integer
+// instructions than comparing and selecting or forming a mask
 __device__ __forceinline__ void or_if_bit(uint32_t &r, uint32_t w, uint32_t m, uint32_t bit) {
   asm("{\n .reg .pred p;\n .reg .b32 t;\n and.b32 t, %1, %2;\n setp.ne.u32 p, t, 0;\n"
       " @p or.b32 %0, %0, %3;\n}\n"
@@ -132,8 +134,8 @@ __device__ __forceinline__ void or_if_bit(uint32_t &r, uint32_t w, uint32_t m, u
 //   fwd bit a  = (R[a] & Dy) != 0        (Sup_xy[a] > 0, Fig. 1)
 //   rev        = OR over a in Dx of R[a] (bit b: (y,b) has a support in Dx)
 // Two independent accumulators per result keep the OR chains short.  kPred:
-// the reverse rows of a partial D_x through or_if_bit (the single-state
-// launches keep the mask form, which their code layout favours).
+// the tests through or_if_bit (the single-state launches keep the plain
+// form, which their code layout favours).
 template <int Q, bool kDxFull, bool kPred = false>
 __device__ __forceinline__ void support_relation(const uint4 *rel, uint32_t stride, uint32_t Dx,
                                                  uint32_t Dy, uint32_t &fwd, uint32_t &rev) {
@@ -141,10 +143,17 @@ __device__ __forceinline__ void support_relation(const uint4 *rel, uint32_t stri
 #pragma unroll
   for (int c = 0; c < Q; ++c) {
     const uint4 w = rel[c * stride];
-    if ((w.x & Dy) != 0u) f0 |= 1u << (4 * c + 0);
-    if ((w.y & Dy) != 0u) f1 |= 1u << (4 * c + 1);
-    if ((w.z & Dy) != 0u) f0 |= 1u << (4 * c + 2);
-    if ((w.w & Dy) != 0u) f1 |= 1u << (4 * c + 3);
+    if (kPred) {
+      or_if_bit(f0, 1u << (4 * c + 0), w.x, Dy);
+      or_if_bit(f1, 1u << (4 * c + 1), w.y, Dy);
+      or_if_bit(f0, 1u << (4 * c + 2), w.z, Dy);
+      or_if_bit(f1, 1u << (4 * c + 3), w.w, Dy);
+    } else {
+      if ((w.x & Dy) != 0u) f0 |= 1u << (4 * c + 0);
+      if ((w.y & Dy) != 0u) f1 |= 1u << (4 * c + 1);
+      if ((w.z & Dy) != 0u) f0 |= 1u << (4 * c + 2);
+      if ((w.w & Dy) != 0u) f1 |= 1u << (4 * c + 3);
+    }
     if (kDxFull) {  // every row of R is in Dx (rows >= d are zero)
       r0 |= w.x | w.z;
       r1 |= w.y | w.w;
@@ -176,14 +185,14 @@ __device__ __forceinline__ void support_relation_pair(const uint4 *rel, uint32_t
 #pragma unroll
   for (int c = 0; c < Q; ++c) {
     const uint4 w = rel[c * stride];
-    if ((w.x & Dy1) != 0u) f1 |= 1u << (4 * c + 0);
-    if ((w.y & Dy1) != 0u) g1 |= 1u << (4 * c + 1);
-    if ((w.z & Dy1) != 0u) f1 |= 1u << (4 * c + 2);
-    if ((w.w & Dy1) != 0u) g1 |= 1u << (4 * c + 3);
-    if ((w.x & Dy2) != 0u) f2 |= 1u << (4 * c + 0);
-    if ((w.y & Dy2) != 0u) g2 |= 1u << (4 * c + 1);
-    if ((w.z & Dy2) != 0u) f2 |= 1u << (4 * c + 2);
-    if ((w.w & Dy2) != 0u) g2 |= 1u << (4 * c + 3);
+    or_if_bit(f1, 1u << (4 * c + 0), w.x, Dy1);
+    or_if_bit(g1, 1u << (4 * c + 1), w.y, Dy1);
+    or_if_bit(f1, 1u << (4 * c + 2), w.z, Dy1);
+    or_if_bit(g1, 1u << (4 * c + 3), w.w, Dy1);
+    or_if_bit(f2, 1u << (4 * c + 0), w.x, Dy2);
+    or_if_bit(g2, 1u << (4 * c + 1), w.y, Dy2);
+    or_if_bit(f2, 1u << (4 * c + 2), w.z, Dy2);
+    or_if_bit(g2, 1u << (4 * c + 3), w.w, Dy2);
     if (kDxFull) {  // both row domains full: every row of R counts for both
       r1 |= w.x | w.z;
       q1 |= w.y | w.w;
