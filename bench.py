@@ -351,7 +351,7 @@ def run_reference(args):
 
 # a slab's 32-state group is scored only with at least this many gated
 # candidates (fewer are evaluated unscored: measured faster on B300)
-LEARNED_MIN_SCORED = 16
+LEARNED_MIN_SCORED = 28
 
 
 def train_predictor(rac, torch, seed, recall=0.995, log=None):

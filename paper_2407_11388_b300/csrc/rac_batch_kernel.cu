@@ -115,9 +115,9 @@ __device__ __forceinline__ void support_dispatch_q(const uint4 *mine, uint32_t s
                                                    uint32_t Dy, uint32_t dfull, uint32_t &fwd,
                                                    uint32_t &rev) {
   if (Dx == dfull)
-    support_relation<Q, true, true>(mine, stride, Dx, Dy, fwd, rev);
+    support_relation<Q, true>(mine, stride, Dx, Dy, fwd, rev);
   else
-    support_relation<Q, false, true>(mine, stride, Dx, Dy, fwd, rev);
+    support_relation<Q, false>(mine, stride, Dx, Dy, fwd, rev);
 }
 
 // Apply a removal to state t: D_k[v] &= keep.  As in kernel (a), only

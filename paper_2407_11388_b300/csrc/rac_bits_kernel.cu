@@ -334,9 +334,9 @@ __device__ __forceinline__ bool eval_state(Smem &S, const LaunchParams &P, int s
       const uint32_t t = __popc(pm & lanemask_lt());
       const uint4 *mine = rel + hdr[nrows + r] * Q + t;
       if (Dx == dfull)
-        support_relation<Q, true, kPre>(mine, __popc(pm), Dx, Dy, fwd, rev);
+        support_relation<Q, true>(mine, __popc(pm), Dx, Dy, fwd, rev);
       else
-        support_relation<Q, false, kPre>(mine, __popc(pm), Dx, Dy, fwd, rev);
+        support_relation<Q, false>(mine, __popc(pm), Dx, Dy, fwd, rev);
     }
     const uint32_t keep_x = __reduce_and_sync(kFull, fwd) & Dx;  // warp-uniform
     if (keep_x != Dx) {

@@ -119,9 +119,9 @@ __device__ __forceinline__ void named_bar(int id, int nthreads) {
 __device__ __forceinline__ uint32_t ld_dom(const uint32_t *p) { return __ldcg(p); }
 
 // r |= w when (m & bit) != 0, as a test into a predicate and a predicated OR:
-// on the many-state paths both the forward test ((R[a] & D_y) != 0 sets bit
-// a) and the masked reverse OR take this form, with fewer integer
-// instructions than comparing and selecting or forming a mask
+// both the forward test ((R[a] & D_y) != 0 sets bit a) and the masked reverse
+// OR take this form, with fewer integer instructions than comparing and
+// selecting or forming a mask
 __device__ __forceinline__ void or_if_bit(uint32_t &r, uint32_t w, uint32_t m, uint32_t bit) {
   asm("{\n .reg .pred p;\n .reg .b32 t;\n and.b32 t, %1, %2;\n setp.ne.u32 p, t, 0;\n"
       " @p or.b32 %0, %0, %3;\n}\n"
@@ -133,40 +133,26 @@ __device__ __forceinline__ void or_if_bit(uint32_t &r, uint32_t w, uint32_t m, u
 // read as Q 16-byte chunks `stride` chunks apart:
 //   fwd bit a  = (R[a] & Dy) != 0        (Sup_xy[a] > 0, Fig. 1)
 //   rev        = OR over a in Dx of R[a] (bit b: (y,b) has a support in Dx)
-// Two independent accumulators per result keep the OR chains short.  kPred:
-// the tests through or_if_bit (the single-state launches keep the plain
-// form, which their code layout favours).
-template <int Q, bool kDxFull, bool kPred = false>
+// Two independent accumulators per result keep the OR chains short.
+template <int Q, bool kDxFull>
 __device__ __forceinline__ void support_relation(const uint4 *rel, uint32_t stride, uint32_t Dx,
                                                  uint32_t Dy, uint32_t &fwd, uint32_t &rev) {
   uint32_t f0 = 0, f1 = 0, r0 = 0, r1 = 0;
 #pragma unroll
   for (int c = 0; c < Q; ++c) {
     const uint4 w = rel[c * stride];
-    if (kPred) {
-      or_if_bit(f0, 1u << (4 * c + 0), w.x, Dy);
-      or_if_bit(f1, 1u << (4 * c + 1), w.y, Dy);
-      or_if_bit(f0, 1u << (4 * c + 2), w.z, Dy);
-      or_if_bit(f1, 1u << (4 * c + 3), w.w, Dy);
-    } else {
-      if ((w.x & Dy) != 0u) f0 |= 1u << (4 * c + 0);
-      if ((w.y & Dy) != 0u) f1 |= 1u << (4 * c + 1);
-      if ((w.z & Dy) != 0u) f0 |= 1u << (4 * c + 2);
-      if ((w.w & Dy) != 0u) f1 |= 1u << (4 * c + 3);
-    }
+    or_if_bit(f0, 1u << (4 * c + 0), w.x, Dy);
+    or_if_bit(f1, 1u << (4 * c + 1), w.y, Dy);
+    or_if_bit(f0, 1u << (4 * c + 2), w.z, Dy);
+    or_if_bit(f1, 1u << (4 * c + 3), w.w, Dy);
     if (kDxFull) {  // every row of R is in Dx (rows >= d are zero)
       r0 |= w.x | w.z;
       r1 |= w.y | w.w;
-    } else if (kPred) {
+    } else {
       or_if_bit(r0, w.x, Dx, 1u << (4 * c + 0));
       or_if_bit(r1, w.y, Dx, 1u << (4 * c + 1));
       or_if_bit(r0, w.z, Dx, 1u << (4 * c + 2));
       or_if_bit(r1, w.w, Dx, 1u << (4 * c + 3));
-    } else {
-      r0 |= w.x & (0u - ((Dx >> (4 * c + 0)) & 1u));
-      r1 |= w.y & (0u - ((Dx >> (4 * c + 1)) & 1u));
-      r0 |= w.z & (0u - ((Dx >> (4 * c + 2)) & 1u));
-      r1 |= w.w & (0u - ((Dx >> (4 * c + 3)) & 1u));
     }
   }
   fwd = f0 | f1;
