@@ -248,8 +248,13 @@ RAC_API void rac_plan_destroy(rac_plan *plan);
  * rac_enforce_host -- rac_enforce on HOST buffers: copies the n_states
  * states (n_states x n_vars words, state s at word s*n_vars) to the device,
  * enforces them as one batch on `net`, copies domains, iterations and status
- * back, and waits for `stream` before returning.  Pinned host memory makes
- * the copies asynchronous-capable; pageable memory also works.
+ * back, and waits for `stream` before returning.  The caller's buffers (any
+ * host memory) are copied with memcpy to and from a pinned staging buffer
+ * that the library allocates per (network, stream) and frees in rac_destroy;
+ * the device copies and the launches of one call form a CUDA graph, recorded
+ * on the first call with a given (n_states, max_sweeps, flags) and replayed
+ * by later calls with the same ones.  Calls on the same (network, stream)
+ * must not overlap.
  * Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA.
  */
 RAC_API rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint32_t *dom_in,

@@ -76,7 +76,9 @@ void free_workspace(Workspace *w) {
   cudaFree(w->state_off);
   cudaFree(w->res_idx);
   cudaFree(w->host_dom);
-  cudaFree(w->host_res);
+  cudaFreeHost(w->host_pin);
+  if (w->host_graph) cudaGraphExecDestroy(w->host_graph);
+  if (w->cap_stream) cudaStreamDestroy(w->cap_stream);
   cudaFree(w->pend);
   cudaFree(w->pend_slab);
   cudaFree(w->pcount);
@@ -584,56 +586,102 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
   if (!check_device(net)) return RAC_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t words = size_t(n_states) * net->n;
+  const size_t total = words + 2 * size_t(n_states);  // domains, iterations, status
   rac_status rc = RAC_OK;
   Workspace *w0 = get_workspace(net, s, std::min<int32_t>(n_states, kMaxStatesPerLaunch), 0, &rc);
   if (!w0) return rc;
-  if (w0->host_cap < words) {
+  if (w0->host_cap < total) {
     cudaError_t er = cudaStreamSynchronize(s);
     if (er != cudaSuccess) return cuda_fail(er, "cudaStreamSynchronize");
+    if (w0->host_graph) cudaGraphExecDestroy(w0->host_graph);
+    w0->host_graph = nullptr;
+    w0->graph_states = -1;
     cudaFree(w0->host_dom);
-    cudaFree(w0->host_res);
+    cudaFreeHost(w0->host_pin);
     w0->host_dom = nullptr;
-    w0->host_res = nullptr;
+    w0->host_pin = nullptr;
     w0->host_cap = 0;
-    if (cudaMalloc(&w0->host_dom, words * 4) != cudaSuccess ||
-        cudaMalloc(&w0->host_res, size_t(n_states) * 8 + 8) != cudaSuccess) {
+    if (cudaMalloc(&w0->host_dom, total * 4) != cudaSuccess ||
+        cudaMallocHost(&w0->host_pin, total * 4) != cudaSuccess) {
       cudaGetLastError();
       cudaFree(w0->host_dom);
       w0->host_dom = nullptr;
-      set_error("out of device memory for the host-path staging buffers");
+      set_error("out of memory for the host-path staging buffers");
       return RAC_ENOMEM;
     }
-    w0->host_cap = words;
-    w0->host_res_cap = size_t(n_states);
+    w0->host_cap = total;
   }
   uint32_t *d_dom = w0->host_dom;
-  int32_t *d_res = w0->host_res;
-  cudaError_t e = cudaMemcpyAsync(d_dom, dom_in, words * 4, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) rc = cuda_fail(e, "host-to-device copy");
-  const int32_t chunk = (flags & RAC_KERNEL_TENSOR) ? kTensorMaxStates : kMaxStatesPerLaunch;
-  for (int32_t base = 0; rc == RAC_OK && base < n_states; base += chunk) {
-    const int cnt = std::min<int32_t>(chunk, n_states - base);
-    Workspace *w = get_workspace(net, s, cnt, 0, &rc);
-    if (!w) break;
-    LaunchParams P = base_params(net, w, cnt, max_sweeps, flags);
-    P.contiguous = 1;
-    P.dom_in = d_dom + size_t(base) * net->n;
-    P.dom_out = d_dom + size_t(base) * net->n;
-    P.iterations = d_res + base;
-    P.status = d_res + n_states + base;
-    rc = launch_for(P, flags, s);
+  int32_t *d_res = reinterpret_cast<int32_t *>(d_dom + words);
+  uint32_t *pin = w0->host_pin;
+  // the copy in, the launches (state chunks) and the single copy out, on `q`
+  auto enqueue = [&](cudaStream_t q) -> rac_status {
+    cudaError_t e = cudaMemcpyAsync(d_dom, pin, words * 4, cudaMemcpyHostToDevice, q);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    const int32_t chunk = (flags & RAC_KERNEL_TENSOR) ? kTensorMaxStates : kMaxStatesPerLaunch;
+    for (int32_t base = 0; base < n_states; base += chunk) {
+      const int cnt = std::min<int32_t>(chunk, n_states - base);
+      LaunchParams P = base_params(net, w0, cnt, max_sweeps, flags);
+      P.contiguous = 1;
+      P.dom_in = d_dom + size_t(base) * net->n;
+      P.dom_out = d_dom + size_t(base) * net->n;
+      P.iterations = d_res + base;
+      P.status = d_res + n_states + base;
+      const rac_status r = launch_for(P, flags, q);
+      if (r != RAC_OK) return r;
+    }
+    e = cudaMemcpyAsync(pin, d_dom, total * 4, cudaMemcpyDeviceToHost, q);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+    return RAC_OK;
+  };
+  // the caller's buffers meet only host copies: the pinned staging is what
+  // the device copies read and write
+  std::memcpy(pin, dom_in, words * 4);
+  const bool same = w0->graph_states == n_states && w0->graph_max_sweeps == max_sweeps &&
+                    w0->graph_flags == flags;
+  if (same && w0->host_graph) {
+    const cudaError_t e = cudaGraphLaunch(w0->host_graph, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphLaunch of the host path");
+  } else {
+    // the first call of this shape runs eagerly (it also sets up the kernel
+    // attributes), then records the same work as a graph for the next calls;
+    // a shape whose capture failed keeps running eagerly
+    rc = enqueue(s);
+    if (rc == RAC_OK && !same) {
+      if (w0->host_graph) cudaGraphExecDestroy(w0->host_graph);
+      w0->host_graph = nullptr;
+      w0->graph_states = -1;
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      bool ok = w0->cap_stream ||
+                cudaStreamCreateWithFlags(&w0->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+      ok = ok && cudaStreamBeginCapture(w0->cap_stream, cudaStreamCaptureModeThreadLocal) ==
+                     cudaSuccess;
+      if (ok) {
+        const rac_status r = enqueue(w0->cap_stream);
+        ok = cudaStreamEndCapture(w0->cap_stream, &g) == cudaSuccess && r == RAC_OK;
+        ok = ok && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+      }
+      if (g) cudaGraphDestroy(g);
+      if (!ok) {
+        cudaGetLastError();
+        if (ge) cudaGraphExecDestroy(ge);
+        ge = nullptr;
+      }
+      w0->host_graph = ge;
+      w0->graph_states = n_states;
+      w0->graph_max_sweeps = max_sweeps;
+      w0->graph_flags = flags;
+      set_error("");
+    }
   }
-  if (rc == RAC_OK) {
-    e = cudaMemcpyAsync(dom_out, d_dom, words * 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(iterations, d_res, size_t(n_states) * 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(status, d_res + n_states, size_t(n_states) * 4, cudaMemcpyDeviceToHost,
-                          s);
-    if (e != cudaSuccess) rc = cuda_fail(e, "device-to-host copy");
-  }
-  e = cudaStreamSynchronize(s);
+  const cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess && rc == RAC_OK) rc = cuda_fail(e, "cudaStreamSynchronize");
+  if (rc == RAC_OK) {
+    std::memcpy(dom_out, pin, words * 4);
+    std::memcpy(iterations, pin + words, size_t(n_states) * 4);
+    std::memcpy(status, pin + words + n_states, size_t(n_states) * 4);
+  }
   return rc;
 }
 

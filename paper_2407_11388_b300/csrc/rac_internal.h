@@ -206,10 +206,17 @@ struct Workspace {
   int64_t *state_off = nullptr;
   int32_t *res_idx = nullptr;
   int cap_items = 0;
-  uint32_t *host_dom = nullptr;  // staging for rac_enforce_host
-  int32_t *host_res = nullptr;
+  // rac_enforce_host: device staging (domains, then iterations and status,
+  // host_cap words in all), a pinned host copy of it, and the CUDA graph of
+  // the copy in, the launches and the copy out for one (state count, sweep
+  // cap, flags), captured on cap_stream and replayed on the caller's stream
+  uint32_t *host_dom = nullptr;
+  uint32_t *host_pin = nullptr;
   size_t host_cap = 0;
-  size_t host_res_cap = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t host_graph = nullptr;
+  int32_t graph_states = -1, graph_max_sweeps = 0;
+  uint32_t graph_flags = 0;
   // learned gating: pending pairs (allocated on the first learned call)
   uint8_t *pend = nullptr;       // [n_slabs][cap_states]
   int32_t *pend_slab = nullptr;  // [n_slabs]

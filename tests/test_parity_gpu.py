@@ -212,6 +212,26 @@ def test_host_entry_point():
     assert_same((out, it, st), oracle_enforce(300, 24, net_np.scope, net_np.rel, doms), "host")
 
 
+def test_host_entry_point_replayed():
+    """Repeated host calls replay a recorded graph: new inputs each call, a
+    change of state count, flags or sweep cap records a new one, and every
+    result matches the oracle."""
+    n, d = 260, 16
+    net_np = racgen.random_network(12, 0, n, d, 0.6, 0.35)
+    all_doms = np.array([racgen.assignment_state(12, 0, s, n, d) for s in range(12)])
+    calls = [(slice(0, 4), 0, 0), (slice(4, 8), 0, 0), (slice(8, 12), 0, 0),   # replays
+             (slice(0, 6), 0, 0), (slice(6, 12), 0, 0),                         # new count
+             (slice(0, 6), rac.INCREMENTAL, 0), (slice(6, 12), rac.INCREMENTAL, 0),
+             (slice(0, 6), rac.STOP_ON_WIPEOUT, 2), (slice(6, 12), rac.STOP_ON_WIPEOUT, 2),
+             (slice(0, 4), 0, 0)]
+    with rac.Network(n, d, net_np.scope, net_np.rel) as net:
+        for sl, flags, cap in calls:
+            doms = all_doms[sl]
+            got = rac.enforce_host(net, doms, max_sweeps=cap, flags=flags)
+            ref = oracle_enforce(n, d, net_np.scope, net_np.rel, doms, flags, max_sweeps=cap)
+            assert_same(got, ref, "host replay %s flags %d cap %d" % (sl, flags, cap))
+
+
 def test_two_streams():
     """Each stream gets its own workspace; concurrent calls do not interfere."""
     T = torch()
