@@ -620,10 +620,10 @@ __device__ void consume_slab_scored(Smem &S, const LaunchParams &P, const uint32
     const uint32_t ev_all = dec[c0 >> 5];  // states past B are never set
     if (ev_all == 0u) continue;
     uint32_t m = warp_share(ev_all, g, groups, lane);
-    if (m == 0u) continue;
-    // an evaluated record gets its label
-    auto label = [&](int s, bool removed) {
-      if (recording && sub == 0 && lane == 0) {
+    // an evaluated record gets its label, from the warp that holds the whole
+    // result (the first of the state's warps)
+    auto label = [&](int s, bool removed, bool writer) {
+      if (recording && writer && lane == 0) {
         const uint32_t need = dec[32 + (s >> 5)];
         if ((need >> (s & 31)) & 1u) {
           const int64_t r = int64_t(dec[64 + (s >> 5)] | (uint64_t(dec[96 + (s >> 5)]) << 32)) +
@@ -636,12 +636,28 @@ __device__ void consume_slab_scored(Smem &S, const LaunchParams &P, const uint32
       for (int i = pop_state(m); i >= 0; i = pop_state(m)) {
         uint32_t Dy, Dxl;
         load_words(S, P, c0 + i, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
-        label(c0 + i, eval_state<Q, true, true>(S, P, c0 + i, k, slot_w, hdr, rel, I, row0, nrows,
-                                                y, y_ok, cached, Dy, Dxl, warp, lane, cg, g, sub,
-                                                wps, red_iter));
+        label(c0 + i,
+              eval_state<Q, true, true>(S, P, c0 + i, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok,
+                                        cached, Dy, Dxl, warp, lane, cg, g, sub, wps, red_iter),
+              sub == 0);
       }
       continue;
     }
+    if (__popc(ev_all) <= 2) {
+      // one or two states to evaluate on this slab: the group's warps split
+      // their rows, four or two warps per state
+      const int wps2 = __popc(ev_all) == 1 ? kGroupWarps : kGroupWarps / 2;
+      const int g2 = (warp % kGroupWarps) / wps2, sub2 = (warp % kGroupWarps) % wps2;
+      const int s2 = c0 + __fns(ev_all, 0, g2 + 1);  // the state of rank g2
+      uint32_t Dy, Dxl;
+      load_words(S, P, s2, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
+      label(s2,
+            eval_state<Q, true, true>(S, P, s2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok,
+                                      cached, Dy, Dxl, warp, lane, cg, g2, sub2, wps2, red_iter),
+            sub2 == 0);
+      continue;
+    }
+    if (m == 0u) continue;
     // two states per pass; the next pair's words load during this one
     int i1 = pop_state(m), i2 = pop_state(m);
     uint32_t Dy1, Dx1, Dy2 = 0u, Dx2 = 0u;
@@ -656,12 +672,14 @@ __device__ void consume_slab_scored(Smem &S, const LaunchParams &P, const uint32
         bool r1, r2;
         eval_pair<Q>(S, P, c0 + i1, c0 + i2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, Dy1,
                      Dx1, Dy2, Dx2, lane, r1, r2);
-        label(c0 + i1, r1);
-        label(c0 + i2, r2);
+        label(c0 + i1, r1, true);
+        label(c0 + i2, r2, true);
       } else {
-        label(c0 + i1, eval_state<Q, true, true>(S, P, c0 + i1, k, slot_w, hdr, rel, I, row0,
-                                                 nrows, y, y_ok, cached, Dy1, Dx1, warp, lane, cg,
-                                                 g, sub, wps, red_iter));
+        label(c0 + i1,
+              eval_state<Q, true, true>(S, P, c0 + i1, k, slot_w, hdr, rel, I, row0, nrows, y,
+                                        y_ok, cached, Dy1, Dx1, warp, lane, cg, g, sub, wps,
+                                        red_iter),
+              true);
       }
       if (n1 < 0) break;
       i1 = n1;
@@ -842,8 +860,20 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
       if (act && incr)
         act = chg_word(S, P, slot_r, s_l, J) != 0u ||
               (chg_word(S, P, slot_r, s_l, I) & rowmask) != 0u;
-      uint32_t am = __ballot_sync(kFull, act);
+      uint32_t am = __ballot_sync(kFull, act);  // the same in every warp of the group
       if (am == 0u) continue;
+      if (__popc(am) <= 2) {
+        // one or two states on this slab (late sweeps): the group's warps
+        // split their rows, four or two warps per state, as with few states
+        const int wps2 = __popc(am) == 1 ? kGroupWarps : kGroupWarps / 2;
+        const int g2 = lw / wps2, sub2 = lw % wps2;
+        const int s2 = c0 + __fns(am, 0, g2 + 1);  // the state of rank g2
+        uint32_t Dy, Dxl;
+        load_words(S, P, s2, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
+        eval_state<Q, false, true>(S, P, s2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, cached,
+                                   Dy, Dxl, warp, lane, cg, g2, sub2, wps2, red_iter);
+        continue;
+      }
       am = warp_share(am, g, groups, lane);
       if (am == 0u) continue;
       // two states per pass (eval_pair); the next pair's words load during
