@@ -48,6 +48,7 @@ struct BSmem {
   uint32_t any_total, wipe_total, running_total;
   uint32_t cta_any, cta_wipe, cta_running;
   uint32_t stage_ok[kBStages];
+  uint32_t red[kBConsumerWarps][32];  // reverse masks of a state's rows split over warps
 };
 static_assert(size_t(kBStages) * kStageBytes + sizeof(BSmem) <= 232448,
               "shared memory of the batched kernel exceeds 227 KB");
@@ -60,6 +61,10 @@ __device__ __forceinline__ int info_status(uint32_t v) { return int((v >> 27) & 
 
 
 __device__ __forceinline__ int group_bar(int cg) { return 1 + cg; }
+// the warps of state group g (< 2) of consumer group cg when a slab's rows
+// are split over them
+__device__ __forceinline__ int split_bar(int cg, int g) { return 1 + kBGroups + 2 * cg + g; }
+static_assert(1 + kBGroups + 2 * kBGroups <= 16, "named barrier ids");
 
 struct BView {
   const uint32_t *C;
@@ -226,6 +231,55 @@ __device__ __forceinline__ void batch_eval(BSmem &S, const BatchParams &P, const
   }
 }
 
+// One state of job J on one slab with its rows split over the wps warps of
+// state group g2 (sub = this warp's place): each warp takes rows sub, sub +
+// wps, ...; the reverse masks meet in shared memory, and the group's first
+// warp applies the column removals.  The caller has the consumer group meet
+// before the call, which also frees the reduction slots of the previous one.
+template <int Q>
+__device__ __forceinline__ void batch_eval_split(BSmem &S, const BatchParams &P, const BatchJob &J,
+                                                 int slot_w, const uint32_t *hdr,
+                                                 const uint4 *rel, uint32_t I, uint32_t Jb,
+                                                 uint32_t row0, uint32_t nrows, int y, bool y_ok,
+                                                 int lane, int warp, int cg, int g2, int sub,
+                                                 int wps, int t, uint32_t *T, int64_t co,
+                                                 uint32_t Dy, uint32_t Dxl) {
+  const uint32_t dfull = J.d >= 32 ? kFull : ((1u << J.d) - 1u);
+  uint32_t racc = kFull, xb = 0u;
+  for (int r = sub; r < int(nrows); r += wps) {
+    const uint32_t pm = hdr[r];
+    if (pm == 0u) continue;
+    const uint32_t Dx = __shfl_sync(kFull, Dxl, r);
+    uint32_t f = kFull, v = kFull;
+    if ((pm >> lane) & 1u) {
+      const uint32_t tt = __popc(pm & lanemask_lt());
+      support_dispatch_q<Q>(rel + hdr[nrows + r] * uint32_t(Q) + tt, __popc(pm), Dx, Dy, dfull, f,
+                            v);
+    }
+    const uint32_t keep = __reduce_and_sync(kFull, f) & Dx;
+    if (keep != Dx) {
+      if (lane == 0) batch_remove(S, P, t, slot_w, T, I * 32u + row0 + uint32_t(r), keep);
+      xb |= 1u << (row0 + uint32_t(r));
+    }
+    racc &= v;
+  }
+  S.red[warp][lane] = racc;
+  named_bar(split_bar(cg, g2), wps * 32);
+  bool ry = false;
+  if (sub == 0) {
+    for (int j = 1; j < wps; ++j) racc &= S.red[warp + j][lane];
+    if (y_ok) {
+      const uint32_t keep = racc & Dy;
+      if (keep != Dy) {
+        batch_remove(S, P, t, slot_w, T, uint32_t(y), keep);
+        ry = true;
+      }
+    }
+  }
+  const uint32_t yb = __ballot_sync(kFull, ry);
+  if (lane == 0 && (xb | yb) != 0u) batch_mark(S, P, J, t, co, slot_w, I, xb, Jb, yb);
+}
+
 // One slab of job J for every running state of J, by one consumer group.  The
 // job's states go 32 at a time (lane i checks state base + i: running, and
 // with RAC_INCREMENTAL a Proposition-2 candidate); warp lw of the group takes
@@ -237,7 +291,7 @@ __device__ __forceinline__ void batch_eval(BSmem &S, const BatchParams &P, const
 template <int Q>
 __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &J,
                                 const unsigned char *stage, const BStage &si, int k, int slot_r,
-                                int slot_w, int lw, int lane) {
+                                int slot_w, int cg, int lw, int lane) {
   const int n = J.n;
   const uint32_t I = si.ij & 0xFFFFu, Jb = si.ij >> 16;
   const uint32_t row0 = si.rows & 0xFFu, nrows = si.rows >> 8;
@@ -271,8 +325,29 @@ __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &
         t_off = (k == 1 || (k & 1)) ? b : a;
       }
     }
-    uint32_t am = __ballot_sync(kFull, act);
+    uint32_t am = __ballot_sync(kFull, act);  // the same in every warp of the group
     if (am == 0u) continue;
+    if (__popc(am) <= 2) {
+      // one or two states on this slab: the group's warps split their rows,
+      // four or two warps per state.  The group meets first: which warps
+      // share a split barrier depends on the chunk, and a warp still in an
+      // earlier chunk's split must not meet one of this chunk's on the same
+      // barrier.
+      named_bar(group_bar(cg), kBGroupWarps * 32);
+      const int wps = __popc(am) == 1 ? kBGroupWarps : kBGroupWarps / 2;
+      const int g2 = lw / wps, sub = lw % wps;
+      const int i = __fns(am, 0, g2 + 1);  // lane of the state of rank g2
+      const int ts = __shfl_sync(kFull, t, i);
+      const int64_t to = __shfl_sync(kFull, t_off, i);
+      const int64_t co = __shfl_sync(kFull, chgoff, i);
+      const int64_t cc = __shfl_sync(kFull, c_off, i);
+      const uint32_t *C = Cbase + cc;
+      const uint32_t Dy = y_ok ? ld_dom(C + y) : 0u;
+      const uint32_t Dxl = x_ok ? ld_dom(C + x_l) : 0u;
+      batch_eval_split<Q>(S, P, J, slot_w, hdr, rel, I, Jb, row0, nrows, y, y_ok, lane,
+                          cg * kBGroupWarps + lw, cg, g2, sub, wps, ts, Tbase + to, co, Dy, Dxl);
+      continue;
+    }
     // this warp's share: the states of rank lw, lw + 4, ... among them
     am = __ballot_sync(kFull, act && __popc(am & lanemask_lt()) % kBGroupWarps == lw);
     if (am == 0u) continue;
@@ -324,17 +399,18 @@ __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &
 }
 
 __device__ void batch_consume(BSmem &S, const BatchParams &P, const unsigned char *stage,
-                              const BStage &si, int k, int slot_r, int slot_w, int lw, int lane) {
+                              const BStage &si, int k, int slot_r, int slot_w, int cg, int lw,
+                              int lane) {
   const BatchJob J = P.jobs[si.job];
   switch (J.q) {
-    case 1: batch_consume_q<1>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
-    case 2: batch_consume_q<2>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
-    case 3: batch_consume_q<3>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
-    case 4: batch_consume_q<4>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
-    case 5: batch_consume_q<5>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
-    case 6: batch_consume_q<6>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
-    case 7: batch_consume_q<7>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
-    default: batch_consume_q<8>(S, P, J, stage, si, k, slot_r, slot_w, lw, lane); break;
+    case 1: batch_consume_q<1>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
+    case 2: batch_consume_q<2>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
+    case 3: batch_consume_q<3>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
+    case 4: batch_consume_q<4>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
+    case 5: batch_consume_q<5>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
+    case 6: batch_consume_q<6>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
+    case 7: batch_consume_q<7>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
+    default: batch_consume_q<8>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
   }
 }
 
@@ -540,7 +616,7 @@ __global__ void __launch_bounds__(kBThreads, 1) rac_batch_kernel(const BatchPara
           __syncwarp();
           const BStage si = S.stage[stg];
           if (si.job >= 0)
-            batch_consume(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_r, slot_w, lw,
+            batch_consume(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_r, slot_w, cg, lw,
                           lane);
           __syncwarp();
           if (lane == 0) mbar_arrive(&S.empty[stg]);

@@ -645,7 +645,9 @@ __device__ void consume_slab_scored(Smem &S, const LaunchParams &P, const uint32
     }
     if (__popc(ev_all) <= 2) {
       // one or two states to evaluate on this slab: the group's warps split
-      // their rows, four or two warps per state
+      // their rows, four or two warps per state (after meeting, as in
+      // consume_slab)
+      named_bar(group_bar(cg), kGroupWarps * 32);
       const int wps2 = __popc(ev_all) == 1 ? kGroupWarps : kGroupWarps / 2;
       const int g2 = (warp % kGroupWarps) / wps2, sub2 = (warp % kGroupWarps) % wps2;
       const int s2 = c0 + __fns(ev_all, 0, g2 + 1);  // the state of rank g2
@@ -864,7 +866,11 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
       if (am == 0u) continue;
       if (__popc(am) <= 2) {
         // one or two states on this slab (late sweeps): the group's warps
-        // split their rows, four or two warps per state, as with few states
+        // split their rows, four or two warps per state, as with few states.
+        // The group meets first: which warps share a state barrier depends
+        // on the chunk, and a warp still in an earlier chunk's split must not
+        // meet one of this chunk's on the same barrier.
+        named_bar(group_bar(cg), kGroupWarps * 32);
         const int wps2 = __popc(am) == 1 ? kGroupWarps : kGroupWarps / 2;
         const int g2 = lw / wps2, sub2 = lw % wps2;
         const int s2 = c0 + __fns(am, 0, g2 + 1);  // the state of rank g2

@@ -145,10 +145,13 @@ def test_weights_round_trip_and_training_learns():
 TRACE_CASES = [(100, 12, 0.5, 0.2), (100, 20, 0.6, 0.1), (45, 5, 0.7, 0.15)]
 
 
-@pytest.mark.parametrize("n,d,dens,c", TRACE_CASES)
-def test_trace_matches_oracle(n, d, dens, c):
+@pytest.mark.parametrize("n,d,dens,c,B", [case + (6,) for case in TRACE_CASES] +
+                         [TRACE_CASES[2] + (70,)])
+def test_trace_matches_oracle(n, d, dens, c, B):
+    """B = 70: three 32-state chunks per slab, each split over the group's
+    warps its own way in late sweeps."""
     scope, rel = _random_net(n * 7 + d, n, d, dens, tuned_tightness(n, d, dens, c))
-    doms = _states(d, n, d, 6)
+    doms = _states(d, n, d, B)
     with rac.Network(n, d, scope, rel) as net:
         rows = net.info()["rows_per_slab"]
         out, sw, st, trace = _run_learned(net, doms, cap=200000)
@@ -243,6 +246,29 @@ def test_learned_exact_and_kernel_logits(n, d, dens, c):
         zref, _ = mlp.forward(w, rec["features"], bf16=True)
         err = np.abs(z - zref)
         assert np.all(err <= 2e-3 * (1.0 + np.abs(zref))), err.max()
+
+
+@pytest.mark.parametrize("B", [48, 80])
+def test_learned_many_states(B):
+    """Learned gating with several 32-state chunks per slab: exact results and
+    every trace label equal to whether the evaluation removed a value, with a
+    random predictor and without one (the Proposition-2 recurrence)."""
+    T = torch()
+    n, d, dens, c = 100, 12, 0.5, 0.2
+    scope, rel = _random_net(n * 11 + B, n, d, dens, tuned_tightness(n, d, dens, c))
+    doms = _states(3 * n + B, n, d, B)
+    ref = oracle_enforce(n, d, scope, rel, doms)
+    with rac.Network(n, d, scope, rel) as net:
+        for pred in (None, rac.Predictor(seed=B)):
+            thr = 0.0
+            if pred is not None:
+                xs, _, _ = learned.collect_traces([(net, T.from_numpy(doms.view(np.int32)).cuda())])
+                thr = float(np.median(learned.logits(pred, xs).cpu().numpy()))
+            out, sw, st, trace = _run_learned(net, doms, pred, thr=thr, cap=300000)
+            _assert_exact(out, st, ref, "B=%d predictor %s" % (B, pred is not None))
+            rec = trace.records()
+            assert rec["label"].shape[0] == trace.count() > 0
+            assert np.all(np.isin(rec["label"], (-1.0, 0.0, 1.0)))
 
 
 def test_learned_stop_on_wipeout():

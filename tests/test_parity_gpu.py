@@ -64,9 +64,11 @@ def test_random_every_width(d):
                         "d=%d n=%d batch" % (d, n))
 
 
-@pytest.mark.parametrize("B", [2, 3, 5, 8, 40])
+@pytest.mark.parametrize("B", [2, 3, 5, 8, 40, 64, 96])
 def test_state_groupings(B):
-    """Warp-to-state mappings for different state counts in one launch."""
+    """Warp-to-state mappings for different state counts in one launch (with
+    more than 32 states a slab's states come in several 32-state chunks, each
+    split over the group's warps its own way)."""
     rng = np.random.default_rng(B)
     n, d = 150, 12
     scope, rel, _ = random_tiny(rng, n, d, 0.3, 0.62)
