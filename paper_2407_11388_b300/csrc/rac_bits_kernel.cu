@@ -44,6 +44,20 @@ struct StageInfo {
   uint32_t ij, rows, pad;
 };
 
+// kernel variants (see rac_bits_kernel)
+constexpr int kVarFew = 0, kVarMany = 1, kVarGated1 = 2, kVarGated2 = 3;
+// warps of a consumer group: five in the many-state variant (16 warps with
+// the producer: one more warp per SM sub-partition to hide the support
+// test's latencies), four in the others
+constexpr int group_warps(int var) { return var == kVarMany ? kGroupWarps + 1 : kGroupWarps; }
+constexpr int consumer_warps(int var) { return group_warps(var) * kGroups; }
+constexpr int kMaxConsumerWarps = (kGroupWarps + 1) * kGroups;
+// the gated variants add one scorer warp per consumer group (16 warps: at most
+// 4 per SM sub-partition, so the 128 registers per thread still fit)
+constexpr int kScorerWarps = kGroups;
+constexpr int threads_for(int var) {
+  return (consumer_warps(var) + 1 + (var >= kVarGated1 ? kScorerWarps : 0)) * 32;
+}
 constexpr int kChgULocal = 64;  // variables <= 2048: the union is collected in shared memory
 
 struct Smem {
@@ -69,8 +83,8 @@ struct Smem {
   uint32_t cta_any;
   uint32_t cta_wipe;
   uint32_t load_all;    // learned gating: some running state is in its full phase
-  uint32_t red[2][kConsumerWarps][32];
-  uint32_t remw[2][kConsumerWarps];  // per-warp "removed a value" of a state group
+  uint32_t red[2][kMaxConsumerWarps][32];
+  uint32_t remw[2][kMaxConsumerWarps];  // per-warp "removed a value" of a state group
   uint32_t st_info[kMaxStatesPerLaunch];  // see kInfo* below
   uint8_t any_loc[kMaxStatesPerLaunch];
   uint8_t wipe_loc[kMaxStatesPerLaunch];
@@ -108,14 +122,6 @@ constexpr uint32_t kInfoResB = 1u << 24;
 constexpr uint32_t kInfoWiped = 1u << 25;
 constexpr uint32_t kInfoGated = 1u << 26;  // learned gating: the state is in its gated phase
 
-// kernel variants (see rac_bits_kernel)
-constexpr int kVarFew = 0, kVarMany = 1, kVarGated1 = 2, kVarGated2 = 3;
-// the gated variants add one scorer warp per consumer group (16 warps: at most
-// 4 per SM sub-partition, so the 128 registers per thread still fit)
-constexpr int kScorerWarps = kGroups;
-constexpr int threads_for(int var) {
-  return var >= kVarGated1 ? kThreads + kScorerWarps * 32 : kThreads;
-}
 __device__ __forceinline__ uint32_t info_status_bits(int st) { return uint32_t(st + 8) << 27; }
 __device__ __forceinline__ int info_status(uint32_t v) { return int((v >> 27) & 31u) - 8; }
 
@@ -818,7 +824,8 @@ template <int Q, int kVar>
 __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char *stage,
                              const StageInfo &si, int stg, int k, int slot_r, int slot_w,
                              int warp, int lane, uint32_t &red_iter) {
-  const int cg = warp / kGroupWarps, lw = warp % kGroupWarps;
+  constexpr int kGW = group_warps(kVar);
+  const int cg = warp / kGW, lw = warp % kGW;
   const NetDev &N = P.net;
   const int n = N.n;
   const uint32_t I = si.ij & 0xFFFFu, J = si.ij >> 16;
@@ -830,7 +837,7 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
   // states are split over warp groups, rows over the warps of a group
   static_assert(kGroupWarps == 4, "state grouping below assumes 4 warps per consumer group");
   const int wps = P.n_states >= 4 ? 1 : (P.n_states >= 2 ? 2 : 4);
-  const int groups = kGroupWarps / wps;
+  const int groups = kGW / wps;
   const int g = lw / wps, sub = lw % wps;
   const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
   const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
@@ -870,14 +877,19 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
         // The group meets first: which warps share a state barrier depends
         // on the chunk, and a warp still in an earlier chunk's split must not
         // meet one of this chunk's on the same barrier.
-        named_bar(group_bar(cg), kGroupWarps * 32);
-        const int wps2 = __popc(am) == 1 ? kGroupWarps : kGroupWarps / 2;
+        named_bar(group_bar(cg), kGW * 32);
+        const int na = __popc(am);
+        const int wps2 = na == 1 ? kGW : kGW / 2;  // a fifth warp of a group sits out two states
         const int g2 = lw / wps2, sub2 = lw % wps2;
-        const int s2 = c0 + __fns(am, 0, g2 + 1);  // the state of rank g2
-        uint32_t Dy, Dxl;
-        load_words(S, P, s2, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
-        eval_state<Q, false, true>(S, P, s2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, cached,
-                                   Dy, Dxl, warp, lane, cg, g2, sub2, wps2, red_iter);
+        if (g2 < na) {
+          const int s2 = c0 + __fns(am, 0, g2 + 1);  // the state of rank g2
+          uint32_t Dy, Dxl;
+          load_words(S, P, s2, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
+          eval_state<Q, false, true>(S, P, s2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok,
+                                     cached, Dy, Dxl, warp, lane, cg, g2, sub2, wps2, red_iter);
+        } else {
+          ++red_iter;  // every warp of the group keeps the same reduction-buffer parity
+        }
         continue;
       }
       am = warp_share(am, g, groups, lane);
@@ -923,6 +935,7 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
 template <int Q, int kVar>
 __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const LaunchParams P) {
   constexpr int kGate = kVar >= kVarGated1 ? 1 : 0;
+  constexpr int kGW = group_warps(kVar), kCW = consumer_warps(kVar);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *ring = smem_raw;
   Smem &S = *reinterpret_cast<Smem *>(smem_raw + size_t(kStages) * kStageBytes);
@@ -934,17 +947,17 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
   const int64_t gtid = int64_t(cta) * blockDim.x + tid;
   const int64_t gstride = int64_t(G) * blockDim.x;
   const int my_slabs = cta < N.n_slabs ? (N.n_slabs - cta + G - 1) / G : 0;
-  const bool is_producer = warp == kConsumerWarps;
-  const bool is_scorer = warp > kConsumerWarps;  // gated variants only
+  const bool is_producer = warp == kCW;
+  const bool is_scorer = warp > kCW;  // gated variants only
   // consumer thread index and grid-wide consumer stride
   const int ctid = tid;
-  const int64_t cgtid = int64_t(cta) * (kConsumerWarps * 32) + ctid;
-  const int64_t cgstride = int64_t(G) * (kConsumerWarps * 32);
+  const int64_t cgtid = int64_t(cta) * (kCW * 32) + ctid;
+  const int64_t cgstride = int64_t(G) * (kCW * 32);
 
   if (tid == 0) {
     for (int i = 0; i < kStages; ++i) {
       mbar_init(&S.full[i], kGate > 0 ? 2 : 1);  // gated: the copy, then the decisions
-      mbar_init(&S.empty[i], kGroupWarps);
+      mbar_init(&S.empty[i], kGW);
       mbar_init(&S.issued[i], 1);
     }
     fence_mbar_init();
@@ -1022,7 +1035,7 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
 
       if (is_scorer) {
         if constexpr (kGate > 0)
-          score_sweep<kVar - kVarGated1 + 1>(S, P, k, slot_r, warp - kConsumerWarps - 1, sc_it,
+          score_sweep<kVar - kVarGated1 + 1>(S, P, k, slot_r, warp - kCW - 1, sc_it,
                                              lane);
       } else if (is_producer) {
         produce_sweep<kGate>(S, P, ring, k, slot_r, slot_c, cta, G, my_slabs, prod_it, lane);
@@ -1030,7 +1043,7 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
         const int64_t stride = P.flag_stride;
         // this sweep's domains D_{k-1} into shared memory
         if (S.dom_cached) {
-          for (int i = ctid; i < B * n; i += kConsumerWarps * 32) {
+          for (int i = ctid; i < B * n; i += kCW * 32) {
             const int s = i / n;
             if (S.st_info[s] & kInfoSweepMask) continue;
             const uint32_t v = ld_dom(state_view(P, s, k).C + (i - s * n));
@@ -1049,10 +1062,10 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
         // instead of once per slab
         if (k >= 2 && S.chg_cached) {
           const uint32_t *src = P.chg + int64_t(slot_r) * stride * N.nb;
-          for (int i = ctid; i < B * N.nb; i += kConsumerWarps * 32)
+          for (int i = ctid; i < B * N.nb; i += kCW * 32)
             S.dom[S.chg_off + i] = ld_dom(src + i);
         }
-        named_bar(kAllConsumersBar, kConsumerWarps * 32);
+        named_bar(kAllConsumersBar, kCW * 32);
         if (k == 1) {
           // A := dom_in; B (all ones between launches) &= dom_in -- an AND,
           // so it needs no ordering against this sweep's removals; note
@@ -1069,8 +1082,8 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
           // owner step: T still holds D_{k-2}; AND D_{k-1} into it where it
           // differs (a warp per 32-variable block of a state, lane = variable);
           // a domain that sweep k-1 emptied is found here (see remove_value)
-          const int64_t cw = int64_t(cta) * kConsumerWarps + warp;
-          for (int64_t i = cw; i < int64_t(B) * N.nb; i += int64_t(G) * kConsumerWarps) {
+          const int64_t cw = int64_t(cta) * kCW + warp;
+          for (int64_t i = cw; i < int64_t(B) * N.nb; i += int64_t(G) * kCW) {
             const int s = int(i / N.nb), blk = int(i % N.nb);
             if (S.st_info[s] & kInfoSweepMask) continue;
             const int x = blk * 32 + lane;
@@ -1082,8 +1095,8 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
           }
         }
         // consumer group cg takes ring positions cg, cg + kGroups, ...
-        const int cg = warp / kGroupWarps;
-        const bool group_leader = (warp % kGroupWarps) == 0 && lane == 0;
+        const int cg = warp / kGW;
+        const bool group_leader = (warp % kGW) == 0 && lane == 0;
         for (;;) {
           const uint32_t pos = ring_it * kGroups + cg;
           const int stg = pos % kStages;
@@ -1092,7 +1105,7 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
           // follows its outcome, so a wait that gives up never leaves a peer
           // warp blocked on a named barrier inside the slab evaluation.
           if (group_leader) S.stage_ok[stg] = mbar_wait(&S.full[stg], par, &P.sync->err, P.wait_limit_ns) ? 1u : 0u;
-          named_bar(group_bar(cg), kGroupWarps * 32);
+          named_bar(group_bar(cg), kGW * 32);
           if (!S.stage_ok[stg]) {
             if (group_leader) S.abort = 1;
             break;

@@ -54,7 +54,7 @@ constexpr int kStageBytes = kSlabRelBytes + 256;     // + header (at most 32 row
 // parity test cannot tell those two phases apart.
 constexpr int kStages = 6;
 constexpr int kMaxStatesPerLaunch = 1024;
-constexpr int kDescCache = 256;   // slab descriptors a CTA keeps in shared memory
+constexpr int kDescCache = 200;   // slab descriptors a CTA keeps in shared memory
 constexpr int kDomWords = 5040;   // domain words a CTA keeps in shared memory per sweep
 
 struct NetDev {
