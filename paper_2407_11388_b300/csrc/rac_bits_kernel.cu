@@ -873,7 +873,7 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
       if (am == 0u) continue;
       if (__popc(am) <= 2) {
         // one or two states on this slab (late sweeps): the group's warps
-        // split their rows, four or two warps per state, as with few states.
+        // split their rows, five (all) or two warps per state, as with few states.
         // The group meets first: which warps share a state barrier depends
         // on the chunk, and a warp still in an earlier chunk's split must not
         // meet one of this chunk's on the same barrier.
