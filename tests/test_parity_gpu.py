@@ -225,12 +225,14 @@ def test_host_entry_point_replayed():
              (slice(0, 6), 0, 0), (slice(6, 12), 0, 0),                         # new count
              (slice(0, 6), rac.INCREMENTAL, 0), (slice(6, 12), rac.INCREMENTAL, 0),
              (slice(0, 6), rac.STOP_ON_WIPEOUT, 2), (slice(6, 12), rac.STOP_ON_WIPEOUT, 2),
+             (slice(0, 5), rac.KERNEL_TENSOR, 0), (slice(5, 10), rac.KERNEL_TENSOR, 0),
              (slice(0, 4), 0, 0)]
     with rac.Network(n, d, net_np.scope, net_np.rel) as net:
         for sl, flags, cap in calls:
             doms = all_doms[sl]
             got = rac.enforce_host(net, doms, max_sweeps=cap, flags=flags)
-            ref = oracle_enforce(n, d, net_np.scope, net_np.rel, doms, flags, max_sweeps=cap)
+            ref = oracle_enforce(n, d, net_np.scope, net_np.rel, doms,
+                                 flags & ~rac.KERNEL_TENSOR, max_sweeps=cap)
             assert_same(got, ref, "host replay %s flags %d cap %d" % (sl, flags, cap))
 
 
