@@ -7,12 +7,12 @@
 // read once per sweep for all of its network's states.
 //
 // Work: global slab g of job (network) j; CTA c streams slabs c, c+G, ...
-// through a 6-stage bulk-copy ring (one producer thread).  Three groups of
-// four consumer warps take alternate stages; the warps of a group own every
-// fourth state of the slab's job and evaluate them independently, loading a
-// state's column and row words straight into registers (the next state's
-// while the current one is evaluated).  The relation width is dispatched
-// once per slab.
+// through a 6-stage bulk-copy ring (a producer warp).  Three groups of four
+// consumer warps take alternate stages; the warps of a group take the slab's
+// job states by rank and evaluate them two per pass (one or two states: the
+// group splits their rows), loading a state's column and row words straight
+// into registers (the next pair's while the current one is evaluated).  The
+// relation width is dispatched once per slab.
 //
 // Per sweep: one barrier after the removals (its word counts the CTAs that
 // removed values), then the owners of the states (state t belongs to CTA

@@ -10,14 +10,18 @@
 // iff it keeps a support on every constraint of C_x (Algorithm 1
 // `tensorRevise`: the sum over the constraints must equal their number).
 //
-// Mapping: a CTA owns every G-th relation slab.  One producer thread streams
+// Mapping: a CTA owns every G-th relation slab.  A producer warp streams
 // slabs into a shared-memory ring with bulk copies (cp.async.bulk, completion
-// on mbarriers); 8 consumer warps evaluate them.  A lane holds one relation
-// (the pair (x, y = 32 J + lane)); the AND over C_x of the forward masks is a
-// warp AND-reduction (redux.sync) for the row's x, and the reverse masks are
-// AND-accumulated per lane over the rows for y.  Partial results reach the
-// next-domain buffer through atomicAnd only when they remove something; the
-// value returned by the atomic tells the writer whether it emptied a domain.
+// on mbarriers); three consumer groups of four warps (five in the many-state
+// variant) take alternate stages.  A lane holds one relation (the pair (x,
+// y = 32 J + lane)); the AND over C_x of the forward masks is a warp
+// AND-reduction (redux.sync) for the row's x, and the reverse masks are
+// AND-accumulated per lane over the rows for y.  With few states a state's
+// rows are split over a group's warps; with many, the group's warps take the
+// slab's states by rank, two per pass.  Partial results reach the
+// next-domain buffer through atomicAnd only when they remove something; an
+// emptied domain is found by the next sweep's owner step (with
+// RAC_STOP_ON_WIPEOUT, by the value the atomic returns).
 //
 // Sweeps are synchronous (Jacobi) as Eq. 1 requires: sweep k reads D_{k-1}
 // from one buffer and ANDs into the other, which still holds D_{k-2} (a
