@@ -236,6 +236,19 @@ def test_host_entry_point_replayed():
             assert_same(got, ref, "host replay %s flags %d cap %d" % (sl, flags, cap))
 
 
+def test_more_states_than_one_launch():
+    """1,100 states of one network: two launches of 1,024 and 76 states on the
+    same workspace, through the device and the host entry points."""
+    n, d = 40, 8
+    net_np = racgen.random_network(21, 0, n, d, 0.6, 0.33)
+    doms = np.array([racgen.assignment_state(21, 0, s, n, d) for s in range(1100)])
+    ref = oracle_enforce(n, d, net_np.scope, net_np.rel, doms, rac.INCREMENTAL)
+    with rac.Network(n, d, net_np.scope, net_np.rel) as net:
+        assert_same(gpu_enforce(n, d, net_np.scope, net_np.rel, doms, rac.INCREMENTAL, net=net,
+                                shuffle_seed=3), ref, "1100 states")
+        assert_same(rac.enforce_host(net, doms, flags=rac.INCREMENTAL), ref, "1100 states, host")
+
+
 def test_two_streams():
     """Each stream gets its own workspace; concurrent calls do not interfere."""
     T = torch()
