@@ -55,6 +55,10 @@ WORKLOADS = {
     "batch256_x64": dict(batch=True, networks=256, states_per_net=64),
     # the same generator at a size small enough for full profiler captures
     "batch32_x16": dict(batch=True, networks=32, states_per_net=16),
+    # Algorithm 2 on the n=500 d=20 network: a step is one assignment and its
+    # seeded enforcement (rac_assign_enforce) inside the device-state search
+    "search_n500_d20": dict(n=500, d=20, density=1.0, tightness=0.35, states="full", n_states=1,
+                            search=True),
 }
 DEFAULT_WORKLOAD = "dense_n500_d20"
 
@@ -331,6 +335,9 @@ def run_reference(args):
         return
     import oracle
     spec = WORKLOADS[args.workload]
+    if spec.get("search"):
+        run_reference_search(args, spec)
+        return
     if spec.get("batch"):
         nets_np, items, _, doms, _ = make_batch(args.seed, spec["networks"], spec["states_per_net"])
         cfg = {"workload": args.workload, "networks": spec["networks"],
@@ -370,6 +377,39 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": "fixpoints/s", "cores": threads,
                              "kind": "oracle",
                              "sample": "%d whole fixpoints (requested %d steps)" % (steps, args.steps)},
+            "e2e": {"value": value, "unit": "fixpoints/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_search(args, spec):
+    """The reference arm of a search workload: the oracle's Algorithm 2 on the
+    same network, the root enforcement and up to --steps assignments (each a
+    whole Eq. 1 enforcement on all host cores), capped to a few minutes."""
+    from oracle.search import dfs as oracle_dfs
+    _, x, _ = make_inputs(args.workload, args.seed)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle_dfs(x.n, x.d, x.scope, x.rel, racgen_full(x), 2, threads=threads)
+    est = (time.perf_counter() - t0) / 3.0
+    steps = max(1, min(args.steps, int(150.0 / max(est, 1e-6))))
+    t0 = time.perf_counter()
+    out = oracle_dfs(x.n, x.d, x.scope, x.rel, racgen_full(x), steps, threads=threads)
+    el = time.perf_counter() - t0
+    fix = out["nodes"] + 1  # the root enforcement is a fixpoint too
+    value = fix / el
+    line = {"metric": METRIC, "value": value, "unit": "fixpoints/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": fix, "warmup": 0, "ms_per_step": 1000.0 * el / fix,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": x.n, "d": x.d, "density": spec["density"],
+                       "tightness": spec["tightness"], "constraints": int(x.m),
+                       "state_kind": "search (Algorithm 2: assign, then enforce)"},
+            "sweeps_per_fixpoint": float(np.mean([s[3] for s in out["steps"]])) if out["steps"] else 0.0,
+            "cpu_baseline": {"value": value, "unit": "fixpoints/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": "the root and %d assignments of the oracle's search"
+                                       % out["nodes"]},
             "e2e": {"value": value, "unit": "fixpoints/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -742,10 +782,133 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def _search_alg_bytes(x, steps):
+    """Algorithmic bytes of the timed assignments: the seeded first sweep reads
+    the assigned variable's constraints, every later sweep the whole store
+    (m d^2 / 8 bytes)."""
+    deg = np.bincount(np.asarray(x.scope).reshape(-1), minlength=x.n)
+    return sum(deg[var] * x.d * x.d / 8.0 + (it - 1) * x.m * x.d * x.d / 8.0
+               for _, var, _, it, _ in steps)
+
+
+def cpu_search_baseline(x, budget_s=15.0):
+    """The oracle's Algorithm 2 on the same network: assignments per second
+    (each a whole Eq. 1 enforcement on all host cores) for about budget_s."""
+    from oracle.search import dfs as oracle_dfs
+    threads = os.cpu_count() or 1
+    nodes, el = 8, 0.0
+    while True:
+        t0 = time.perf_counter()
+        out = oracle_dfs(x.n, x.d, x.scope, x.rel, racgen_full(x), nodes, threads=threads)
+        el = time.perf_counter() - t0
+        if el >= budget_s or out["nodes"] < nodes or nodes >= 4096:
+            break
+        nodes = int(nodes * max(2.0, min(8.0, budget_s / max(el, 1e-3))))
+    done = max(1, out["nodes"])
+    return {"value": done / el, "unit": "fixpoints/s", "cores": threads, "kind": "oracle",
+            "sample": "the first %d assignments of the oracle's Algorithm 2 search on this "
+                      "network (each a whole Eq. 1 enforcement), %.1f s" % (done, el)}
+
+
+def racgen_full(x):
+    import racgen
+    return racgen.full_domain(x.n, x.d)
+
+
+def run_search(args):
+    """One step = one assignment of Algorithm 2's search and its seeded
+    enforcement, timed on the device (CUDA events around each launch, L2
+    flushed before each, outside the events); the whole search's wall time
+    per assignment (the host's variable choice reads each child state back)
+    is the end-to-end figure."""
+    import torch
+    import paper_2407_11388_b300 as rac
+    from paper_2407_11388_b300.search import dfs
+
+    world, rank, local = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec, x, _ = make_inputs(args.workload, args.seed + rank)
+    net = rac.Network(x.n, x.d, x.scope, x.rel)
+    stream = torch.cuda.current_stream()
+    flush = L2Flush(torch, dev)
+    W, K = max(3, args.warmup), args.steps
+    events = []
+
+    def hook(phase):
+        if phase == "before":
+            flush()
+            events.append([torch.cuda.Event(enable_timing=True),
+                           torch.cuda.Event(enable_timing=True)])
+            events[-1][0].record(stream)
+        else:
+            events[-1][1].record(stream)
+
+    gc.collect()
+    gc.disable()
+    with ClockSampler(local) as clk:
+        res = dfs(net, racgen_full(x), max_nodes=W + K, stream=stream, flags=args.flags, hook=hook)
+        torch.cuda.synchronize()
+    gc.enable()
+    timed = res.steps[W:]
+    if not timed:
+        raise SystemExit("the search ended after %d assignments: no step to time" % res.nodes)
+    dev_s = sum(a.elapsed_time(b) for a, b in events[W:]) / 1000.0
+    per_step_s = dev_s / len(timed)
+    # end to end: the same search from the host domains, no flushes, wall clock
+    gc.collect()
+    gc.disable()
+    t0 = time.perf_counter()
+    res2 = dfs(net, racgen_full(x), max_nodes=W + K, stream=stream, flags=args.flags)
+    wall = time.perf_counter() - t0
+    gc.enable()
+    if res2.steps != res.steps:
+        raise SystemExit("the untimed search took other steps than the timed one")
+    peaks = measured_peaks()
+    hbm_peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6400.0
+    alg = _search_alg_bytes(x, timed) / len(timed)
+    its = [s[3] for s in timed]
+    line = {"metric": METRIC, "value": 1.0 / per_step_s, "unit": "fixpoints/s", "n_gpus": world,
+            "steps": len(timed), "warmup": W, "ms_per_step": per_step_s * 1000.0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded random binary CSP, generated in-process)",
+            "config": {"workload": args.workload, "n": x.n, "d": x.d, "density": spec["density"],
+                       "tightness": spec["tightness"], "constraints": int(x.m),
+                       "state_kind": "search (Algorithm 2: assign, then seeded enforcement)",
+                       "seed_generated": True, "l2": L2_NOTE},
+            "sweeps_per_fixpoint": float(np.mean(its)),
+            "search": {"assignments": res.nodes, "root_sweeps": res.root_iterations,
+                       "solution_found": res.solution is not None,
+                       "wipeouts": int(sum(1 for s in timed if s[4] == rac.WIPEOUT)),
+                       "sweeps_per_assignment": float(np.mean(its)),
+                       "paper_table1_range": "3.44-4.83 sweeps per assignment (its own networks)"},
+            "roofline": {"bound": "hbm", "achieved": alg / per_step_s / 1e9, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": alg / per_step_s / 1e9 / hbm_peak,
+                         "traffic": traffic_from_profiles(args.workload),
+                         "peak_source": "measured" if peaks else "fallback",
+                         "kernel": "rac_bits_kernel", "alg_bytes_per_launch": alg},
+            "clocks": clk.summary(),
+            "gpu_launches": len(timed),
+            "e2e": {"value": res2.nodes / wall, "unit": "fixpoints/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": int(x.n * 4 + 8), "steps": res2.nodes,
+                    "note": "the whole search on the host's clock: an assignment's inputs are "
+                            "launch parameters (the parent state stays on the device); the "
+                            "child state and its sweep count are read back for the next choice"}}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_search_baseline(x)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    net.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif WORKLOADS[args.workload].get("search"):
+        run_search(args)
     else:
         run_ours(args)
 

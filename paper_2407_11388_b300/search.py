@@ -32,16 +32,19 @@ class SearchResult:
 
 def choose_variable(dom):
     """Smallest domain of size > 1, lowest index; None when all are singletons."""
-    sizes = np.array([bin(int(w)).count("1") for w in dom])
+    words = np.ascontiguousarray(dom, dtype=np.uint32)
+    sizes = np.unpackbits(words.view(np.uint8)).reshape(-1, 32).sum(1)
     open_vars = np.flatnonzero(sizes > 1)
     if open_vars.size == 0:
         return None
     return int(open_vars[np.argmin(sizes[open_vars])])
 
 
-def dfs(net, dom0, max_nodes=10_000, stream=None, flags=0):
+def dfs(net, dom0, max_nodes=10_000, stream=None, flags=0, hook=None):
     """Depth-first search of Algorithm 2 on the device.  dom0: host uint32
-    words (n).  Returns a SearchResult."""
+    words (n).  hook, if given, is called with "before" and "after" around
+    each assignment's enforcement launch (to time it on the stream).  Returns
+    a SearchResult."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     n = net.n
@@ -69,8 +72,12 @@ def dfs(net, dom0, max_nodes=10_000, stream=None, flags=0):
                 res.exhausted = True
                 return False
             res.nodes += 1
+            if hook:
+                hook("before")
             assign_enforce(net, levels[level], levels[level + 1], var, value, it, st,
                            flags=flags, stream=stream)
+            if hook:
+                hook("after")
             iters, status = int(it.item()), int(st.item())
             res.steps.append((level, var, value, iters, status))
             if status == OK and rec(level + 1):

@@ -7,43 +7,11 @@ import pytest
 
 import oracle
 import racgen
+from oracle.search import dfs as oracle_dfs
 import paper_2407_11388_b300 as rac
-from paper_2407_11388_b300.search import choose_variable, dfs
+from paper_2407_11388_b300.search import dfs
 
 pytestmark = pytest.mark.gpu
-
-
-def oracle_dfs(n, d, scope, rel, dom0, max_nodes):
-    out = {"steps": [], "nodes": 0, "solution": None, "exhausted": False}
-    root, rit, rst = oracle.rac(n, d, scope, rel, dom0)
-    out["root"] = (rit, rst)
-    if rst != oracle.OK:
-        return out
-
-    def rec(level, dom):
-        var = choose_variable(dom)
-        if var is None:
-            out["solution"] = dom.copy()
-            return True
-        for value in range(d):
-            if not (int(dom[var]) >> value) & 1:
-                continue
-            if out["nodes"] >= max_nodes:
-                out["exhausted"] = True
-                return False
-            out["nodes"] += 1
-            nxt = dom.copy()
-            nxt[var] = np.uint32(1 << value)
-            res, it, st = oracle.rac(n, d, scope, rel, nxt)  # plain recurrence, all constraints
-            out["steps"].append((level, var, value, it, st))
-            if st == oracle.OK and rec(level + 1, res):
-                return True
-            if out["exhausted"]:
-                return False
-        return False
-
-    rec(0, root)
-    return out
 
 
 @pytest.mark.parametrize("seed,n,d,p,t", [(1, 40, 8, 0.3, 0.35), (2, 60, 10, 0.5, 0.3),
