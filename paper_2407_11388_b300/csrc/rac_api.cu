@@ -586,7 +586,12 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
   if (!check_device(net)) return RAC_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t words = size_t(n_states) * net->n;
-  const size_t total = words + 2 * size_t(n_states);  // domains, iterations, status
+  // One launch of the bit-packed kernel writes its results straight into the
+  // pinned staging buffer at its end (posted writes, no separate copy out);
+  // the tensor-core kernel and calls of several launches copy them out.
+  const bool direct = !(flags & RAC_KERNEL_TENSOR) && n_states <= kMaxStatesPerLaunch;
+  // pinned staging: [input words][result words][iterations][status]
+  const size_t total = 2 * words + 2 * size_t(n_states);
   rac_status rc = RAC_OK;
   Workspace *w0 = get_workspace(net, s, std::min<int32_t>(n_states, kMaxStatesPerLaunch), 0, &rc);
   if (!w0) return rc;
@@ -600,24 +605,42 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
     cudaFreeHost(w0->host_pin);
     w0->host_dom = nullptr;
     w0->host_pin = nullptr;
+    w0->host_pin_dev = nullptr;
     w0->host_cap = 0;
+    void *dp = nullptr;
     if (cudaMalloc(&w0->host_dom, total * 4) != cudaSuccess ||
-        cudaMallocHost(&w0->host_pin, total * 4) != cudaSuccess) {
+        cudaMallocHost(&w0->host_pin, total * 4) != cudaSuccess ||
+        cudaHostGetDevicePointer(&dp, w0->host_pin, 0) != cudaSuccess) {
       cudaGetLastError();
       cudaFree(w0->host_dom);
+      cudaFreeHost(w0->host_pin);
       w0->host_dom = nullptr;
+      w0->host_pin = nullptr;
       set_error("out of memory for the host-path staging buffers");
       return RAC_ENOMEM;
     }
+    w0->host_pin_dev = static_cast<uint32_t *>(dp);
     w0->host_cap = total;
   }
   uint32_t *d_dom = w0->host_dom;
   int32_t *d_res = reinterpret_cast<int32_t *>(d_dom + words);
   uint32_t *pin = w0->host_pin;
-  // the copy in, the launches (state chunks) and the single copy out, on `q`
+  uint32_t *pin_res = pin + words;  // results: domains, then iterations and status
+  // the work of one call on `q`
   auto enqueue = [&](cudaStream_t q) -> rac_status {
     cudaError_t e = cudaMemcpyAsync(d_dom, pin, words * 4, cudaMemcpyHostToDevice, q);
     if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    if (direct) {
+      LaunchParams P = base_params(net, w0, n_states, max_sweeps, flags);
+      P.contiguous = 1;
+      P.dom_in = d_dom;
+      P.dom_out = d_dom;
+      P.iterations = d_res;
+      P.status = d_res + n_states;
+      P.host_out = w0->host_pin_dev + words;
+      return launch_for(P, flags, q);
+    }
+    // the launches (state chunks), one copy out
     const int32_t chunk = (flags & RAC_KERNEL_TENSOR) ? kTensorMaxStates : kMaxStatesPerLaunch;
     for (int32_t base = 0; base < n_states; base += chunk) {
       const int cnt = std::min<int32_t>(chunk, n_states - base);
@@ -630,12 +653,12 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
       const rac_status r = launch_for(P, flags, q);
       if (r != RAC_OK) return r;
     }
-    e = cudaMemcpyAsync(pin, d_dom, total * 4, cudaMemcpyDeviceToHost, q);
+    e = cudaMemcpyAsync(pin_res, d_dom, (words + 2 * size_t(n_states)) * 4,
+                        cudaMemcpyDeviceToHost, q);
     if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
     return RAC_OK;
   };
-  // the caller's buffers meet only host copies: the pinned staging is what
-  // the device copies read and write
+  // the caller's buffers meet only host copies
   std::memcpy(pin, dom_in, words * 4);
   const bool same = w0->graph_states == n_states && w0->graph_max_sweeps == max_sweeps &&
                     w0->graph_flags == flags;
@@ -678,9 +701,9 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
   const cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess && rc == RAC_OK) rc = cuda_fail(e, "cudaStreamSynchronize");
   if (rc == RAC_OK) {
-    std::memcpy(dom_out, pin, words * 4);
-    std::memcpy(iterations, pin + words, size_t(n_states) * 4);
-    std::memcpy(status, pin + words + n_states, size_t(n_states) * 4);
+    std::memcpy(dom_out, pin_res, words * 4);
+    std::memcpy(iterations, pin_res + words, size_t(n_states) * 4);
+    std::memcpy(status, pin_res + words + n_states, size_t(n_states) * 4);
   }
   return rc;
 }

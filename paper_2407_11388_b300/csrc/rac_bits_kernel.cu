@@ -1211,16 +1211,23 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
   }
 
   // Epilogue: results that ended in buffer B move to dom_out and B goes back
-  // to all ones.  The next launch on this workspace starts at the barrier
-  // slot after this launch's last one (see Sync).
+  // to all ones; with P.host_out the results are also written there (host
+  // memory: the caller's copy out).  The next launch on this workspace starts
+  // at the barrier slot after this launch's last one (see Sync).
   if (S.abort) S.failed = 1;
   __syncthreads();
   const bool failed = S.failed != 0u;
   if (!S.poisoned) {
     for (int64_t i = gtid; i < int64_t(B) * n; i += gstride) {
       const int s = int(i / n), x = int(i % n);
-      if (!failed && (S.st_info[s] & kInfoResB))
-        P.dom_out[state_offset(P, s) + x] = ld_dom(P.bufB + i);
+      const int64_t o = state_offset(P, s) + x;
+      if (!failed && (S.st_info[s] & kInfoResB)) {
+        const uint32_t v = ld_dom(P.bufB + i);
+        P.dom_out[o] = v;
+        if (P.host_out) P.host_out[o] = v;
+      } else if (P.host_out) {
+        P.host_out[o] = ld_dom(P.dom_out + o);
+      }
       P.bufB[i] = kFull;
     }
   }
@@ -1229,8 +1236,15 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
     for (int s = tid; s < B; s += blockDim.x) {
       const uint32_t info = S.st_info[s];
       const int idx = P.contiguous ? s : P.res_idx[s];
-      P.iterations[idx] = int32_t(info & kInfoSweepMask) ? int32_t(info & kInfoSweepMask) : k;
-      P.status[idx] = failed ? RAC_EBARRIER : info_status(info);
+      const int32_t its = int32_t(info & kInfoSweepMask) ? int32_t(info & kInfoSweepMask) : k;
+      const int32_t st = failed ? RAC_EBARRIER : info_status(info);
+      P.iterations[idx] = its;
+      P.status[idx] = st;
+      if (P.host_out) {
+        int32_t *res = reinterpret_cast<int32_t *>(P.host_out + int64_t(B) * n);
+        res[idx] = its;
+        res[B + idx] = st;
+      }
     }
   }
   if (failed && tid == 0) atomicOr(&P.sync->err, kErrCopyWait);  // poison (idempotent)

@@ -101,6 +101,9 @@ struct LaunchParams {
   uint32_t *bufB;            // n_states x n scratch words (all ones between launches)
   int32_t *iterations;
   int32_t *status;
+  // optional (contiguous launches): the results also written to host memory
+  // at the end -- n_states x n domain words, then iterations, then status
+  uint32_t *host_out;
   uint32_t *any;             // [3][flag_stride] some value removed in the sweep
   uint32_t *wipe;            // [3][flag_stride] some domain emptied in the sweep
   uint32_t *chg;             // [3][flag_stride][nb] variables that lost a value
@@ -212,6 +215,7 @@ struct Workspace {
   // cap, flags), captured on cap_stream and replayed on the caller's stream
   uint32_t *host_dom = nullptr;
   uint32_t *host_pin = nullptr;
+  uint32_t *host_pin_dev = nullptr;  // the device's address of host_pin
   size_t host_cap = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t host_graph = nullptr;
