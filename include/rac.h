@@ -251,10 +251,12 @@ RAC_API void rac_plan_destroy(rac_plan *plan);
  * back, and waits for `stream` before returning.  The caller's buffers (any
  * host memory) are copied with memcpy to and from a pinned staging buffer
  * that the library allocates per (network, stream) and frees in rac_destroy;
- * the device copies and the launches of one call form a CUDA graph, recorded
- * on the first call with a given (n_states, max_sweeps, flags) and replayed
- * by later calls with the same ones.  Calls on the same (network, stream)
- * must not overlap.
+ * the copy in, the launches and (calls of several launches, or the
+ * tensor-core kernel) the copy out form a CUDA graph, recorded on the first
+ * call with a given (n_states, max_sweeps, flags) and replayed by later calls
+ * with the same ones; a call of one bit-packed launch has the kernel write
+ * its results straight into the pinned buffer.  Calls on the same (network,
+ * stream) must not overlap.
  * Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA.
  */
 RAC_API rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint32_t *dom_in,
