@@ -44,3 +44,24 @@ def test_bounded_wait_runs_out_and_reports():
         good.synchronize()
         assert np.array_equal(from_dev(dout), want[0][0])
         assert int(it.item()) == want[1][0] and int(st.item()) == want[2][0]
+
+
+def test_bounded_wait_reported_through_the_host_entry_point():
+    """The host entry point returns the status the kernel writes into pinned
+    memory: a wait that runs out gives RAC_EBARRIER (also on the poisoned
+    workspace's next call), and another stream still gets the oracle's
+    result."""
+    T = torch()
+    n, d = 300, 12
+    net_np = racgen.random_network(9, 0, n, d, 0.5, 0.5)
+    doms = np.array([racgen.assignment_state(9, 0, s, n, d) for s in range(3)])
+    want = oracle_enforce(n, d, net_np.scope, net_np.rel, doms)
+    with rac.Network(n, d, net_np.scope, net_np.rel) as net:
+        bad_stream = T.cuda.Stream()
+        _, _, st = rac.enforce_host(net, doms, flags=rac.TEST_WITHHOLD_ARRIVAL, stream=bad_stream)
+        assert list(st) == [rac.EBARRIER] * 3
+        _, _, st = rac.enforce_host(net, doms, stream=bad_stream)
+        assert list(st) == [rac.EBARRIER] * 3
+        out, it, st = rac.enforce_host(net, doms, stream=T.cuda.Stream())
+        assert np.array_equal(out, want[0]) and list(it) == list(want[1])
+        assert list(st) == list(want[2])
