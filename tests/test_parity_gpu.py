@@ -116,6 +116,22 @@ def test_dense_2000_config():
                 oracle_enforce(2000, 32, net.scope, net.rel, doms, threads=32), "dense2000 states")
 
 
+@pytest.mark.parametrize("B,sample", [(32, None), (128, 24)])
+def test_n1000_d24_many_states_config(B, sample):
+    """n=1000, d=24, density 0.8, tightness 0.3 with 32 or 128 assignment
+    states in one launch (the benchmark's many-state launches): every state,
+    or an even sample of the 128, against the oracle, plain and with
+    Proposition 2."""
+    net_np = racgen.random_network(0, 0, 1000, 24, 0.8, 0.3)
+    doms = np.array([racgen.assignment_state(0, 0, s, 1000, 24) for s in range(B)])
+    pick = np.arange(B) if sample is None else np.linspace(0, B - 1, sample).astype(int)
+    ref = oracle_enforce(1000, 24, net_np.scope, net_np.rel, doms[pick], threads=32)
+    with rac.Network(1000, 24, net_np.scope, net_np.rel) as net:
+        for flags in (0, rac.INCREMENTAL):
+            out, its, sts = gpu_enforce(1000, 24, net_np.scope, net_np.rel, doms, flags, net=net)
+            assert_same((out[pick], its[pick], sts[pick]), ref, "B=%d flags %d" % (B, flags))
+
+
 def test_search_path_states():
     """States built the way backtrack search builds them (Algorithm 2):
     enforce, assign one more variable, enforce again -- the multi-sweep regime
