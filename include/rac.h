@@ -142,6 +142,26 @@ RAC_API rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons,
                               const uint32_t *rel_bits, uint32_t layout_flags,
                               rac_network **out);
 
+/*
+ * rac_create_network_u8 -- rac_create_network from the relation tensor's 0/1
+ * matrices instead of packed rows.
+ *
+ *  rel        HOST, n_cons x d x d uint8: rel[(c * d + a) * d + b] is
+ *             R_xy[a][b] for (x, y) = (scope[2c], scope[2c+1]), 1 = the pair
+ *             of values is allowed, 0 = it is not (the blocks of Algorithm 2's
+ *             `init` relation tensor Cons[x][y][a][b], one per constraint).
+ *
+ * Row a of each matrix is packed on the host into the word rac_create_network
+ * takes (bit b = R_xy[a][b]); the network, its layout and every result are
+ * then those of rac_create_network on the packed words.  The other arguments,
+ * ownership and errors are as there; an entry other than 0 or 1 is
+ * RAC_EINVAL (the message names the constraint), checked before anything is
+ * allocated on the device.
+ */
+RAC_API rac_status rac_create_network_u8(int32_t n_vars, int32_t d, int64_t n_cons,
+                                         const int32_t *scope, const uint8_t *rel,
+                                         uint32_t layout_flags, rac_network **out);
+
 /* rac_destroy -- free a network and all device memory it owns (NULL-safe).
  * The caller must make sure no enforcement on it is still running. */
 RAC_API void rac_destroy(rac_network *net);

@@ -35,7 +35,7 @@ TEST_WITHHOLD_ARRIVAL = 0x80000000  # failure-detection test hook (see include/r
 STATUS_NAMES = {OK: "ok", WIPEOUT: "wipeout", EINVAL: "einval", ENOMEM: "enomem",
                 ECUDA: "ecuda", ETIMEOUT: "etimeout", EBARRIER: "ebarrier", ENOTSUP: "enotsup"}
 
-ABI_FUNCTIONS = ("rac_create_network", "rac_destroy", "rac_enforce", "rac_enforce_batch",
+ABI_FUNCTIONS = ("rac_create_network", "rac_create_network_u8", "rac_destroy", "rac_enforce", "rac_enforce_batch",
                  "rac_enforce_host", "rac_enforce_noalloc", "rac_network_info", "rac_last_error",
                  "rac_plan_create", "rac_plan_enforce", "rac_plan_destroy", "rac_assign_enforce",
                  "rac_predictor_num_params", "rac_predictor_create", "rac_predictor_destroy",
@@ -74,6 +74,8 @@ def lib():
         vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
         L.rac_create_network.restype = i32
         L.rac_create_network.argtypes = [i32, i32, i64, vp, vp, u32, ctypes.POINTER(vp)]
+        L.rac_create_network_u8.restype = i32
+        L.rac_create_network_u8.argtypes = [i32, i32, i64, vp, vp, u32, ctypes.POINTER(vp)]
         L.rac_destroy.restype = None
         L.rac_destroy.argtypes = [vp]
         L.rac_enforce.restype = i32
@@ -157,15 +159,27 @@ def _stream(stream):
 class Network:
     """A constraint network resident on the current CUDA device.
 
-    scope: (m, 2) int32 host array; rel: (m, d) uint32 host array, bit b of
-    rel[c, a] = R_xy[a][b] for (x, y) = scope[c]."""
+    scope: (m, 2) int32 host array; rel: either (m, d) uint32 host array, bit
+    b of rel[c, a] = R_xy[a][b] for (x, y) = scope[c], or the 0/1 matrices
+    themselves, an (m, d, d) uint8 or bool array with rel[c, a, b] =
+    R_xy[a][b] (packed by the library: rac_create_network_u8)."""
 
     def __init__(self, n, d, scope, rel, layout=LAYOUT_BITS, rows=None):
         """rows: tile rows (a power of two); None takes the autotuned table's
         choice for this (d, density) if one is installed (tile_table.json),
         else the library default."""
         scope = np.ascontiguousarray(scope, dtype=np.int32).reshape(-1, 2)
-        rel = np.ascontiguousarray(rel, dtype=np.uint32).reshape(-1, d)
+        rel = np.asarray(rel)
+        if rel.ndim == 3:
+            if rel.dtype not in (np.uint8, np.bool_):
+                raise RacError(EINVAL, "0/1 relation matrices must be uint8 or bool")
+            rel = np.ascontiguousarray(rel.view(np.uint8) if rel.dtype == np.bool_ else rel)
+            create = lib().rac_create_network_u8
+            if rel.shape[1:] != (d, d):
+                raise RacError(EINVAL, "relation matrices must be d x d")
+        else:
+            rel = np.ascontiguousarray(rel, dtype=np.uint32).reshape(-1, d)
+            create = lib().rac_create_network
         if rel.shape[0] != scope.shape[0]:
             raise RacError(EINVAL, "scope and rel disagree on the number of constraints")
         if rows is None and not (int(layout) & 0xF00):
@@ -177,9 +191,9 @@ class Network:
                 raise RacError(EINVAL, "tile rows must be a power of two in [2, 32]")
             layout = int(layout) | LAYOUT_ROWS(rows.bit_length() - 1)
         h = ctypes.c_void_p()
-        _check(lib().rac_create_network(int(n), int(d), scope.shape[0], scope.ctypes.data,
-                                        rel.ctypes.data, int(layout), ctypes.byref(h)),
-               "rac_create_network")
+        _check(create(int(n), int(d), scope.shape[0], scope.ctypes.data, rel.ctypes.data,
+                      int(layout), ctypes.byref(h)),
+               create.__name__)
         self.handle = h.value
         self.n, self.d, self.m = int(n), int(d), int(scope.shape[0])
 

@@ -405,6 +405,48 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
   return RAC_OK;
 }
 
+rac_status rac_create_network_u8(int32_t n_vars, int32_t d, int64_t n_cons, const int32_t *scope,
+                                 const uint8_t *rel, uint32_t layout_flags, rac_network **out) {
+  set_error("");
+  if (!out) {
+    set_error("out is NULL");
+    return RAC_EINVAL;
+  }
+  *out = nullptr;
+  if (d < 1 || d > 32) {
+    set_error("d must be in [1, 32]");
+    return RAC_EINVAL;
+  }
+  if (n_cons < 0 || (n_cons > 0 && (!scope || !rel))) {
+    set_error("n_cons < 0 or NULL scope / rel");
+    return RAC_EINVAL;
+  }
+  // row a of constraint c becomes one word: bit b = R_xy[a][b]
+  std::vector<uint32_t> words;
+  try {
+    words.resize(size_t(n_cons) * size_t(d));
+  } catch (const std::bad_alloc &) {
+    set_error("out of host memory");
+    return RAC_ENOMEM;
+  }
+  const size_t dd = size_t(d);
+  for (size_t r = 0; r < words.size(); ++r) {
+    const uint8_t *row = rel + r * dd;
+    uint32_t w = 0u, bad = 0u;
+    for (size_t b = 0; b < dd; ++b) {
+      w |= uint32_t(row[b] & 1u) << b;
+      bad |= row[b] & ~1u;
+    }
+    if (bad) {
+      set_error("constraint " + std::to_string(r / dd) + " has a relation entry other than 0 or 1");
+      return RAC_EINVAL;
+    }
+    words[r] = w;
+  }
+  return rac_create_network(n_vars, d, n_cons, scope, n_cons > 0 ? words.data() : nullptr,
+                            layout_flags, out);
+}
+
 void rac_destroy(rac_network *net) {
   if (!net) return;
   for (auto &kv : net->ws) free_workspace(kv.second);

@@ -131,3 +131,54 @@ def test_tile_rows_too_large_rejected(L):
     for rows in (1, 3, 64):
         with pytest.raises(rac.RacError):
             rac.Network(4, 8, np.array([[0, 1]], np.int32), np.zeros((1, 8), np.uint32), rows=rows)
+
+
+def _create_u8(L, n, d, scope, mats, flags=1):
+    h = ctypes.c_void_p()
+    scope = np.ascontiguousarray(scope, np.int32)
+    mats = np.ascontiguousarray(mats, np.uint8)
+    rc = L.rac_create_network_u8(n, d, scope.shape[0], scope.ctypes.data, mats.ctypes.data, flags,
+                                 ctypes.byref(h))
+    return rc, h
+
+
+@pytest.mark.parametrize("case", ["entry_2", "entry_255", "d0", "d33", "null_rel", "null_out"])
+def test_create_u8_rejects(L, case):
+    """Entries other than 0/1 and bad shapes are refused on the host, before
+    any device allocation (so this runs without a GPU)."""
+    n, d = 4, 3
+    scope = np.array([[0, 1], [1, 2]], np.int32)
+    mats = np.ones((2, 3, 3), np.uint8)
+    if case == "entry_2":
+        mats[1, 2, 0] = 2
+    elif case == "entry_255":
+        mats[0, 0, 2] = 255
+    elif case == "d0":
+        d = 0
+    elif case == "d33":
+        d = 33
+    if case == "null_rel":
+        h = ctypes.c_void_p()
+        rc = L.rac_create_network_u8(n, d, 2, scope.ctypes.data, None, 1, ctypes.byref(h))
+    elif case == "null_out":
+        rc = L.rac_create_network_u8(n, d, 2, scope.ctypes.data, mats.ctypes.data, 1, None)
+        h = ctypes.c_void_p()
+    else:
+        rc, h = _create_u8(L, n, d, scope, mats)
+    assert rc == rac.EINVAL
+    assert h.value is None
+    msg = L.rac_last_error().decode()
+    assert msg != ""
+    if case.startswith("entry"):
+        assert "constraint %d" % (1 if case == "entry_2" else 0) in msg
+
+
+def test_python_binding_u8_checks(L):
+    scope = np.array([[0, 1]], np.int32)
+    with pytest.raises(rac.RacError):  # not d x d
+        rac.Network(3, 3, scope, np.ones((1, 3, 2), np.uint8))
+    with pytest.raises(rac.RacError):  # not 0/1 bytes or bools
+        rac.Network(3, 3, scope, np.ones((1, 3, 3), np.float32))
+    with pytest.raises(rac.RacError) as e:
+        rac.Network(3, 3, scope, np.full((1, 3, 3), 3, np.uint8))
+    assert e.value.code == rac.EINVAL

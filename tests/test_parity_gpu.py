@@ -6,8 +6,8 @@ import pytest
 import oracle
 import racgen
 import paper_2407_11388_b300 as rac
-from cases import (chain, chain_closed_form, full_word, golden_names, load_golden, random_tiny,
-                   width_cases)
+from cases import (chain, chain_closed_form, full_word, golden_names, load_golden, mixed_states,
+                   random_tiny, width_cases)
 from gpu_helpers import assert_same, from_dev, gpu_enforce, oracle_enforce, to_dev, torch
 
 pytestmark = pytest.mark.gpu
@@ -349,3 +349,33 @@ def test_wipe_split_over_slabs(B):
         stop = bool(flags & rac.STOP_ON_WIPEOUT)
         assert list(ref[1]) == [1 if stop else 3] * B and list(ref[2]) == [rac.WIPEOUT] * B
         assert_same(gpu_enforce(n, d, scope, rel, doms, flags), ref, "split wipe-out")
+
+
+@pytest.mark.parametrize("n,d,density,c,as_bool", [(40, 1, 0.5, 0.3, False), (70, 7, 0.6, 0.3, True),
+                                                   (300, 20, 0.3, 0.2, False),
+                                                   (90, 32, 0.8, 0.05, False)])
+def test_network_from_u8_matrices(n, d, density, c, as_bool):
+    """A network given as the relation tensor's 0/1 matrices
+    (rac_create_network_u8) gets the layout of the same network given as
+    packed rows, and the oracle's domains, sweep counts and status."""
+    rng = np.random.default_rng(7000 + d)
+    tight = min(0.95, (c / max(1.0, n * density)) ** (1.0 / d))
+    pairs = [(x, y) for x in range(n) for y in range(x + 1, n) if rng.random() < density]
+    # scopes in both orientations, as a caller may give them
+    scope = np.array([(y, x) if rng.random() < 0.5 else (x, y) for x, y in pairs],
+                     np.int32).reshape(-1, 2)
+    mats = (rng.random((len(pairs), d, d)) >= tight).astype(np.uint8)
+    rel = np.zeros((len(pairs), d), np.uint32)
+    for b in range(d):  # packed rows for the oracle: bit b of row a = R[a][b]
+        rel |= mats[:, :, b].astype(np.uint32) << np.uint32(b)
+    doms = mixed_states(rng, n, d)
+    net_u8 = rac.Network(n, d, scope, mats.astype(bool) if as_bool else mats)
+    net_w = rac.Network(n, d, scope, rel)
+    try:
+        assert net_u8.info() == net_w.info()
+        for flags in (0, rac.INCREMENTAL):
+            got = gpu_enforce(n, d, scope, rel, doms, flags, net=net_u8)
+            assert_same(got, oracle_enforce(n, d, scope, rel, doms, flags), "u8 %d %d" % (n, d))
+    finally:
+        net_u8.close()
+        net_w.close()
