@@ -958,6 +958,19 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
   const int64_t cgtid = int64_t(cta) * (kCW * 32) + ctid;
   const int64_t cgstride = int64_t(G) * (kCW * 32);
 
+  // Loads the first sweep waits on, issued before the set-up so that their
+  // latency (a cold miss after an idle spell) overlaps it: this CTA's first
+  // slab descriptors (producer lanes) and the workspace's barrier base and
+  // error word (thread 0; plain loads: the previous launch on this
+  // workspace ran on the same stream and has finished).
+  SlabDesc desc0 = {};
+  if (is_producer && lane < my_slabs) desc0 = N.slabs[cta + lane * G];
+  uint32_t base0 = 0u, err0 = 0u;
+  if (tid == 0) {
+    base0 = ld_dom(&P.sync->base);
+    err0 = ld_dom(&P.sync->err);
+  }
+
   if (tid == 0) {
     for (int i = 0; i < kStages; ++i) {
       mbar_init(&S.full[i], kGate > 0 ? 2 : 1);  // gated: the copy, then the decisions
@@ -1019,11 +1032,12 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
     }
     prod_it = __shfl_sync(kFull, prod_it, 0);
     // this CTA's slab descriptors (slabs cta, cta + G, ...)
-    for (int j = lane; j < my_slabs && j < kDescCache; j += 32) S.desc[j] = N.slabs[cta + j * G];
+    for (int j = lane; j < my_slabs && j < kDescCache; j += 32)
+      S.desc[j] = j < 32 ? desc0 : N.slabs[cta + j * G];
     __syncwarp();
   } else if (ctid == 0) {
-    S.base = ld_acquire(&P.sync->base);
-    S.poisoned = ld_acquire(&P.sync->err) != 0u ? 1u : 0u;
+    S.base = base0;
+    S.poisoned = err0 != 0u ? 1u : 0u;
   }
   __syncthreads();
   const uint32_t base = S.base;
