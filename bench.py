@@ -319,7 +319,7 @@ def cpu_baseline(W, budget_s=15.0):
         done += 1
         sweeps += it
         el = time.perf_counter() - t0
-        if el >= budget_s or done >= 1000:
+        if el >= budget_s or done >= 4000:
             break
     return {"value": done / el, "unit": "fixpoints/s", "cores": threads, "kind": "oracle",
             "sample": "%d whole fixpoints (%d sweeps) of this workload's items, %.1f s" % (
