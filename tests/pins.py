@@ -11,13 +11,16 @@ failure messages (empty = pinned).  Sources of truth:
     Sec. 3) and AC-3 (a different algorithm reaching the same set);
   * properties: the result is arc consistent, enforcement is idempotent,
     sweeps <= |D|+1 (Proposition 1), every sweep only removes, and the
-    incremental run removes the same values in every sweep (Proposition 2).
+    incremental run removes the same values in every sweep (Proposition 2);
+  * the paper's dense tensor form of a sweep (Sec. 4, Fig. 1, Algorithm 1),
+    restated in numpy: the same states and sweep counts while no domain is
+    empty.
 """
 import numpy as np
 
 import oracle
 from cases import (chain, chain_closed_form, full_word, golden_names, is_arc_consistent,
-                   load_golden, random_tiny)
+                   load_golden, random_tiny, tuned_tightness)
 
 
 def pin_golden(lib):
@@ -225,8 +228,79 @@ def pin_stop_and_cap(lib, seed=3):
     return fails
 
 
+def tensor_form(n, d, scope, rel, dom, stop_on_wipeout):
+    """One state enforced in the paper's dense tensor form (Sec. 4, Fig. 1,
+    Algorithm 1), in plain numpy:
+    - a constraint tensor of n x n blocks of d x d, holding R_xy on a
+      constrained pair, its transpose on (y, x), and all ones on an
+      unconstrained pair and on the diagonal;
+    - the support counts of every value, that tensor times the n x d domain
+      mask;
+    - each count clamped to {0, 1} and summed over y;
+    - (x, a) kept iff the sum reaches n.
+    The wipe-out test comes before the no-change test.  The input domains
+    must be non-empty.  Returns (domain words, sweeps, status)."""
+    cons = np.ones((n, n, d, d), dtype=np.int64)
+    bits = np.arange(d)
+    for c, (x, y) in enumerate(scope):
+        R = (np.asarray(rel[c], dtype=np.int64)[:, None] >> bits[None, :]) & 1  # R[a, b]
+        cons[x, y] = R
+        cons[y, x] = R.T
+    V = ((np.asarray(dom, dtype=np.int64)[:, None] >> bits[None, :]) & 1)  # V[x, a]
+    k = 0
+    while True:
+        k += 1
+        counts = np.einsum("xyab,yb->xya", cons, V)
+        support = np.minimum(counts, 1).sum(axis=1)  # over y, the diagonal included
+        Vn = V * (support == n)
+        empty = bool((Vn.sum(axis=1) == 0).any())
+        if stop_on_wipeout and empty:
+            status = oracle.WIPEOUT
+            break
+        if (Vn == V).all():
+            status = oracle.WIPEOUT if empty else oracle.OK
+            break
+        V = Vn
+    out = (Vn << bits[None, :]).sum(axis=1).astype(np.uint32)
+    return out, k, status
+
+
+def tensor_form_cases(seed, count):
+    """Small random networks with non-empty input domains, tightness near the
+    point where removals cascade."""
+    rng = np.random.default_rng(seed)
+    for _ in range(count):
+        n = int(rng.integers(2, 11))
+        d = int(rng.integers(1, 7))
+        density = float(rng.choice([0.3, 0.6, 1.0]))
+        tight = tuned_tightness(n, d, density, float(rng.choice([0.1, 0.3, 1.0])))
+        scope, rel, dom = random_tiny(rng, n, d, density, tight,
+                                      restrict=float(rng.choice([0.0, 0.3])))
+        dom[dom == 0] = 1
+        yield n, d, scope, rel, dom
+
+
+def pin_tensor_form(lib, seed=21, cases=400):
+    """Eq. 1 over the real constraints against the dense tensor form: while no
+    domain is empty an all-ones block supports every value (reading c5), so
+    in stop-on-wipeout mode the two agree on every state, sweep count and
+    status, and in the default mode on every input whose fixpoint has no
+    empty domain."""
+    fails = []
+    for i, (n, d, scope, rel, dom) in enumerate(tensor_form_cases(seed, cases)):
+        for stop in (True, False):
+            got = oracle.rac(n, d, scope, rel, dom, stop_on_wipeout=stop, lib=lib)
+            if not stop and got[2] != oracle.OK:
+                continue
+            want = tensor_form(n, d, scope, rel, dom, stop)
+            if not np.array_equal(got[0], want[0]) or tuple(got[1:]) != tuple(want[1:]):
+                fails.append("tensor form %d (stop %d): sweeps/status %s vs %s" % (
+                    i, stop, tuple(got[1:]), tuple(want[1:])))
+    return fails
+
+
 ALL_PINS = [pin_golden, pin_chain, pin_special_cases, pin_three_way, pin_invariants,
-            pin_incremental, pin_stop_and_cap]
+            pin_incremental, pin_stop_and_cap, pin_tensor_form]
 
 
 def run_all(lib, quick=False):
