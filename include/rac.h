@@ -33,7 +33,8 @@
  *    call on it reports RAC_EBARRIER without enforcing).
  *  - Functions return RAC_OK or a negative error code; on error nothing has
  *    been launched and rac_last_error() describes the cause.  No C++
- *    exception crosses this boundary.
+ *    exception crosses this boundary: a host allocation that fails inside
+ *    the library is RAC_ENOMEM, any other host-side exception RAC_EINVAL.
  *  - Device pointers are plain CUDA device addresses (for example the
  *    data_ptr() of a torch tensor on the same device).  `stream` is a
  *    cudaStream_t; NULL means the legacy default stream.  Work is enqueued on
@@ -135,8 +136,9 @@ typedef int32_t rac_status;
  *
  * The library keeps its own copy; the host arrays may be freed on return.
  * The call synchronises with the device (allocation and upload).
- * Errors: RAC_EINVAL (bad argument, duplicate pair, bit >= d set),
- * RAC_ENOMEM (host or device allocation failed), RAC_ECUDA.
+ * Errors: RAC_EINVAL (bad argument, duplicate pair, bit >= d set, more
+ * constraints than the n_vars (n_vars - 1) / 2 pairs), RAC_ENOMEM (host or
+ * device allocation failed), RAC_ECUDA.
  */
 RAC_API rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const int32_t *scope,
                               const uint32_t *rel_bits, uint32_t layout_flags,

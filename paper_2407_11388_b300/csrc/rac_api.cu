@@ -17,6 +17,12 @@ thread_local std::string g_last_error;
 }
 
 void set_error(const std::string &msg) { g_last_error = msg; }
+void set_error_nothrow(const char *msg) noexcept {
+  try {
+    g_last_error = msg;
+  } catch (...) {
+  }
+}
 
 rac_status cuda_fail(cudaError_t e, const char *what) {
   set_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -207,7 +213,7 @@ const char *rac_last_error(void) { return rac::g_last_error.c_str(); }
 
 rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const int32_t *scope,
                               const uint32_t *rel_bits, uint32_t layout_flags,
-                              rac_network **out) {
+                              rac_network **out) try {
   set_error("");
   if (!out) {
     set_error("out is NULL");
@@ -224,6 +230,10 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
   }
   if (n_cons < 0 || (n_cons > 0 && (!scope || !rel_bits))) {
     set_error("n_cons < 0 or NULL scope / rel_bits");
+    return RAC_EINVAL;
+  }
+  if (n_cons > int64_t(n_vars) * (n_vars - 1) / 2) {
+    set_error("more constraints than pairs of variables (each pair takes at most one)");
     return RAC_EINVAL;
   }
   if (layout_flags & ~(RAC_LAYOUT_BITS | RAC_LAYOUT_ROWS_MASK)) {
@@ -403,10 +413,10 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
     return fail(e, "upload of the slab features");
   *out = net;
   return RAC_OK;
-}
+} RAC_CATCH_STATUS
 
 rac_status rac_create_network_u8(int32_t n_vars, int32_t d, int64_t n_cons, const int32_t *scope,
-                                 const uint8_t *rel, uint32_t layout_flags, rac_network **out) {
+                                 const uint8_t *rel, uint32_t layout_flags, rac_network **out) try {
   set_error("");
   if (!out) {
     set_error("out is NULL");
@@ -419,6 +429,10 @@ rac_status rac_create_network_u8(int32_t n_vars, int32_t d, int64_t n_cons, cons
   }
   if (n_cons < 0 || (n_cons > 0 && (!scope || !rel))) {
     set_error("n_cons < 0 or NULL scope / rel");
+    return RAC_EINVAL;
+  }
+  if (n_vars < 1 || n_vars > 2000000 || n_cons > int64_t(n_vars) * (n_vars - 1) / 2) {
+    set_error("n_vars outside [1, 2000000] or more constraints than pairs of variables");
     return RAC_EINVAL;
   }
   // row a of constraint c becomes one word: bit b = R_xy[a][b]
@@ -445,9 +459,9 @@ rac_status rac_create_network_u8(int32_t n_vars, int32_t d, int64_t n_cons, cons
   }
   return rac_create_network(n_vars, d, n_cons, scope, n_cons > 0 ? words.data() : nullptr,
                             layout_flags, out);
-}
+} RAC_CATCH_STATUS
 
-void rac_destroy(rac_network *net) {
+void rac_destroy(rac_network *net) try {
   if (!net) return;
   for (auto &kv : net->ws) free_workspace(kv.second);
   net->ws.clear();
@@ -455,20 +469,20 @@ void rac_destroy(rac_network *net) {
   cudaFree(net->d_slabs);
   cudaFree(net->d_slab_feat);
   delete net;
-}
+} RAC_CATCH_VOID
 
-int32_t rac_network_info(const rac_network *net, int64_t *info, int32_t n_info) {
+int32_t rac_network_info(const rac_network *net, int64_t *info, int32_t n_info) try {
   if (!net || !info || n_info <= 0) return 0;
   const int64_t v[7] = {net->n, net->d, net->m, int64_t(net->rel_bytes), net->n_slabs,
                         net->rows_per_slab, net->dp};
   const int32_t k = std::min<int32_t>(n_info, 7);
   for (int32_t i = 0; i < k; ++i) info[i] = v[i];
   return k;
-}
+} RAC_CATCH_ZERO
 
 rac_status rac_enforce(const rac_network *net, const uint32_t *dom_in, uint32_t *dom_out,
                        int32_t *iterations, int32_t *status, int32_t max_sweeps, uint32_t flags,
-                       rac_stream_t stream) {
+                       rac_stream_t stream) try {
   set_error("");
   if (!net || !dom_in || !dom_out || !iterations || !status) {
     set_error("NULL argument");
@@ -490,11 +504,11 @@ rac_status rac_enforce(const rac_network *net, const uint32_t *dom_in, uint32_t 
   P.iterations = iterations;
   P.status = status;
   return launch_for(P, flags, s);
-}
+} RAC_CATCH_STATUS
 
 rac_status rac_assign_enforce(const rac_network *net, const uint32_t *dom_in, uint32_t *dom_out,
                               int32_t var, int32_t value, int32_t *iterations, int32_t *status,
-                              int32_t max_sweeps, uint32_t flags, rac_stream_t stream) {
+                              int32_t max_sweeps, uint32_t flags, rac_stream_t stream) try {
   set_error("");
   if (!net || !dom_in || !dom_out || !iterations || !status) {
     set_error("NULL argument");
@@ -526,13 +540,13 @@ rac_status rac_assign_enforce(const rac_network *net, const uint32_t *dom_in, ui
   P.seed_var = var;
   P.seed_keep = 1u << value;
   return launch_bits(P, s);
-}
+} RAC_CATCH_STATUS
 
 rac_status rac_enforce_batch(const rac_network *const *nets, int32_t n_nets, int32_t n_items,
                              const int32_t *item_net, const int64_t *item_dom_off,
                              const uint32_t *dom_in, uint32_t *dom_out, int32_t *iterations,
                              int32_t *status, int32_t max_sweeps, uint32_t flags,
-                             rac_stream_t stream) {
+                             rac_stream_t stream) try {
   set_error("");
   if (n_items < 0 || n_nets < 0) {
     set_error("negative count");
@@ -610,11 +624,11 @@ rac_status rac_enforce_batch(const rac_network *const *nets, int32_t n_nets, int
     }
   }
   return RAC_OK;
-}
+} RAC_CATCH_STATUS
 
 rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint32_t *dom_in,
                             uint32_t *dom_out, int32_t *iterations, int32_t *status,
-                            int32_t max_sweeps, uint32_t flags, rac_stream_t stream) {
+                            int32_t max_sweeps, uint32_t flags, rac_stream_t stream) try {
   set_error("");
   if (!net || !dom_in || !dom_out || !iterations || !status || n_states < 0) {
     set_error("NULL argument or negative state count");
@@ -748,13 +762,13 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
     std::memcpy(status, pin_res + words + n_states, size_t(n_states) * 4);
   }
   return rc;
-}
+} RAC_CATCH_STATUS
 
 rac_status rac_enforce_learned(const rac_network *net, int32_t n_states, const uint32_t *dom_in,
                                uint32_t *dom_out, int32_t *sweeps, int32_t *status,
                                int32_t max_sweeps, uint32_t flags, const rac_predictor *pred,
                                float threshold, int32_t min_scored, const rac_trace *trace,
-                               rac_stream_t stream) {
+                               rac_stream_t stream) try {
   set_error("");
   if (!net || n_states < 0) {
     set_error("NULL network or negative state count");
@@ -840,6 +854,6 @@ rac_status rac_enforce_learned(const rac_network *net, int32_t n_states, const u
     if (rc != RAC_OK) return rc;
   }
   return RAC_OK;
-}
+} RAC_CATCH_STATUS
 
 }  // extern "C"

@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <mutex>
+#include <new>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -256,6 +257,7 @@ struct LaunchCache {
 rac_status persistent_shape(LaunchCache &cache, const void *func, int threads, size_t smem,
                             const char *what, int *per_sm, int *sms);
 void set_error(const std::string &msg);
+void set_error_nothrow(const char *msg) noexcept;
 rac_status cuda_fail(cudaError_t e, const char *what);
 NetDev net_dev(const rac_network *net);
 // Launch the bit-packed kernel for P (grid sized by the callee).
@@ -274,3 +276,24 @@ rac_status enforce_batch_multi(const rac_network *const *nets, int32_t n_nets, i
                                int32_t *status, int32_t max_sweeps, uint32_t flags,
                                cudaStream_t s);
 }  // namespace rac
+
+// The extern "C" entry points are function-try-blocks that end in one of
+// these, so that no C++ exception (a failed host allocation inside a
+// std::vector or std::string, a length error on an absurd size) crosses the
+// C ABI: a status-returning call reports it as an error code.
+#define RAC_CATCH_STATUS                                        \
+  catch (const std::bad_alloc &) {                              \
+    rac::set_error_nothrow("out of host memory");               \
+    return RAC_ENOMEM;                                          \
+  }                                                             \
+  catch (...) {                                                 \
+    rac::set_error_nothrow("unexpected host-side exception");   \
+    return RAC_EINVAL;                                          \
+  }
+#define RAC_CATCH_ZERO \
+  catch (...) {        \
+    return 0;          \
+  }
+#define RAC_CATCH_VOID \
+  catch (...) {        \
+  }

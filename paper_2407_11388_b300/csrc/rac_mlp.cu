@@ -255,7 +255,7 @@ extern "C" {
 
 int32_t rac_predictor_num_params(void) { return kMlpParams; }
 
-rac_status rac_predictor_create(uint64_t seed, rac_predictor **out) {
+rac_status rac_predictor_create(uint64_t seed, rac_predictor **out) try {
   set_error("");
   if (!out) {
     set_error("out is NULL");
@@ -305,11 +305,11 @@ rac_status rac_predictor_create(uint64_t seed, rac_predictor **out) {
   }
   *out = p;
   return RAC_OK;
-}
+} RAC_CATCH_STATUS
 
 void rac_predictor_destroy(rac_predictor *p) { pred_free(p); }
 
-rac_status rac_predictor_set_weights(rac_predictor *p, const float *params) {
+rac_status rac_predictor_set_weights(rac_predictor *p, const float *params) try {
   set_error("");
   if (!p || !params) {
     set_error("NULL argument");
@@ -326,9 +326,9 @@ rac_status rac_predictor_set_weights(rac_predictor *p, const float *params) {
     e = cudaDeviceSynchronize();
   }
   return e == cudaSuccess ? RAC_OK : cuda_fail(e, "rac_predictor_set_weights");
-}
+} RAC_CATCH_STATUS
 
-rac_status rac_predictor_get_weights(const rac_predictor *p, float *params, int32_t bf16) {
+rac_status rac_predictor_get_weights(const rac_predictor *p, float *params, int32_t bf16) try {
   set_error("");
   if (!p || !params) {
     set_error("NULL argument");
@@ -344,10 +344,10 @@ rac_status rac_predictor_get_weights(const rac_predictor *p, float *params, int3
     for (int i = 0; e == cudaSuccess && i < kMlpParams; ++i) params[i] = __bfloat162float(h[i]);
   }
   return e == cudaSuccess ? RAC_OK : cuda_fail(e, "rac_predictor_get_weights");
-}
+} RAC_CATCH_STATUS
 
 rac_status rac_predictor_gradient(rac_predictor *p, const float *X, const float *Y, int64_t N,
-                                  float pos_weight, float *grad_out, float *loss_out) {
+                                  float pos_weight, float *grad_out, float *loss_out) try {
   set_error("");
   if (!p || !X || !Y || N <= 0 || !(pos_weight > 0.0f)) {
     set_error("NULL argument, empty batch or pos_weight <= 0");
@@ -364,11 +364,11 @@ rac_status rac_predictor_gradient(rac_predictor *p, const float *X, const float 
   if (grad_out) e = cudaMemcpy(grad_out, p->grad, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && loss_out) e = cudaMemcpy(loss_out, p->loss, sizeof(float), cudaMemcpyDeviceToHost);
   return e == cudaSuccess ? RAC_OK : cuda_fail(e, "copy of the gradient");
-}
+} RAC_CATCH_STATUS
 
 rac_status rac_predictor_train(rac_predictor *p, const float *X, const float *Y, int64_t N,
                                int32_t steps, int32_t batch, float lr, float pos_weight,
-                               uint64_t seed, float *loss_out) {
+                               uint64_t seed, float *loss_out) try {
   set_error("");
   if (!p || !X || !Y || N <= 0 || steps < 0 || batch <= 0 || !(lr > 0.0f) ||
       !(pos_weight > 0.0f)) {
@@ -399,10 +399,10 @@ rac_status rac_predictor_train(rac_predictor *p, const float *X, const float *Y,
     if (e != cudaSuccess) return cuda_fail(e, "copy of the loss");
   }
   return RAC_OK;
-}
+} RAC_CATCH_STATUS
 
 rac_status rac_predictor_predict(const rac_predictor *p, const float *X, int64_t N, float *Z,
-                                 int32_t tensor_cores) {
+                                 int32_t tensor_cores) try {
   set_error("");
   if (!p || N < 0 || (N > 0 && (!X || !Z))) {
     set_error("NULL argument or negative count");
@@ -417,6 +417,6 @@ rac_status rac_predictor_predict(const rac_predictor *p, const float *X, int64_t
     mlp_predict_scalar<<<unsigned((N + 127) / 128), 128>>>(p->w, X, N, Z);
   cudaError_t e = cudaDeviceSynchronize();
   return e == cudaSuccess ? RAC_OK : cuda_fail(e, "predictor inference");
-}
+} RAC_CATCH_STATUS
 
 }  // extern "C"

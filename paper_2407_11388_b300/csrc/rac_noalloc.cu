@@ -74,7 +74,7 @@ using namespace rac;
 extern "C" rac_status rac_enforce_noalloc(const rac_network *net, const uint32_t *dom_in,
                                           uint32_t *dom_out, int32_t *iterations,
                                           int32_t *status, int32_t max_sweeps, uint32_t flags,
-                                          rac_stream_t stream) {
+                                          rac_stream_t stream) try {
   set_error("");
   if (!net || !dom_in || !dom_out || !iterations || !status) {
     set_error("rac_enforce_noalloc: NULL argument");
@@ -132,4 +132,4 @@ extern "C" rac_status rac_enforce_noalloc(const rac_network *net, const uint32_t
   if (e == cudaSuccess) e = cudaMemsetAsync(P.bufB, 0xFF, size_t(net->n) * sizeof(uint32_t), s);
   if (e != cudaSuccess) return cuda_fail(e, "rac_enforce_noalloc: resetting the scratch array");
   return launch_bits(P, s);
-}
+} RAC_CATCH_STATUS

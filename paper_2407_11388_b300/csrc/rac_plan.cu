@@ -253,7 +253,7 @@ rac_status enforce_batch_multi(const rac_network *const *nets, int32_t n_nets, i
 extern "C" {
 
 rac_status rac_plan_create(const rac_network *const *nets, int32_t n_nets, int32_t n_items,
-                           const int32_t *item_net, const int64_t *item_dom_off, rac_plan **out) {
+                           const int32_t *item_net, const int64_t *item_dom_off, rac_plan **out) try {
   set_error("");
   if (!out) {
     set_error("out is NULL");
@@ -285,11 +285,11 @@ rac_status rac_plan_create(const rac_network *const *nets, int32_t n_nets, int32
   }
   *out = p;
   return RAC_OK;
-}
+} RAC_CATCH_STATUS
 
 rac_status rac_plan_enforce(rac_plan *plan, const uint32_t *dom_in, uint32_t *dom_out,
                             int32_t *iterations, int32_t *status, int32_t max_sweeps,
-                            uint32_t flags, rac_stream_t stream) {
+                            uint32_t flags, rac_stream_t stream) try {
   set_error("");
   if (!plan || (plan->total_states > 0 && (!dom_in || !dom_out || !iterations || !status))) {
     set_error("NULL argument");
@@ -306,7 +306,7 @@ rac_status rac_plan_enforce(rac_plan *plan, const uint32_t *dom_in, uint32_t *do
   }
   return plan_launch(plan, dom_in, dom_out, iterations, status, max_sweeps, flags,
                      reinterpret_cast<cudaStream_t>(stream));
-}
+} RAC_CATCH_STATUS
 
 void rac_plan_destroy(rac_plan *plan) { plan_free(plan); }
 

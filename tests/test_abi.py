@@ -182,3 +182,20 @@ def test_python_binding_u8_checks(L):
     with pytest.raises(rac.RacError) as e:
         rac.Network(3, 3, scope, np.full((1, 3, 3), 3, np.uint8))
     assert e.value.code == rac.EINVAL
+
+
+def test_more_constraints_than_pairs_rejected(L):
+    """Each unordered pair takes at most one constraint, so n_cons above
+    n(n-1)/2 is refused before anything is read or allocated; the same holds
+    for sizes no host could hold (no C++ exception crosses the ABI)."""
+    scope = np.zeros((1, 2), np.int32)
+    rel = np.zeros((1, 3), np.uint32)
+    mats = np.zeros((1, 3, 3), np.uint8)
+    for n_cons in (7, 1 << 40, (1 << 62) + 5):
+        h = ctypes.c_void_p()
+        assert L.rac_create_network(4, 3, n_cons, scope.ctypes.data, rel.ctypes.data, 1,
+                                    ctypes.byref(h)) == rac.EINVAL
+        assert h.value is None and "pairs" in L.rac_last_error().decode()
+        assert L.rac_create_network_u8(4, 3, n_cons, scope.ctypes.data, mats.ctypes.data, 1,
+                                       ctypes.byref(h)) == rac.EINVAL
+        assert h.value is None
