@@ -379,3 +379,50 @@ def test_network_from_u8_matrices(n, d, density, c, as_bool):
     finally:
         net_u8.close()
         net_w.close()
+
+
+_MAX_N_CASE = {}
+
+
+def _max_n_case():
+    """n_vars = 2,000,000, the largest network the library takes, with d = 8:
+    the chain x_0 < ... < x_7 on eight variables scattered over the whole
+    range (one value each at the fixpoint, after 8 sweeps), 50,000 random
+    loose constraints between far-apart blocks, and 2,000 more that touch the
+    chain's variables, so the removals spread from the chain over further
+    sweeps (9 in all, about 1,300 domains reduced).  The domains do not fit
+    in shared memory here, so the sweep reads them from global memory."""
+    if not _MAX_N_CASE:
+        n, d = 2_000_000, 8
+        rng = np.random.default_rng(77)
+        perm = rng.choice(n, size=8, replace=False)
+        s, r = chain(8, d)
+        cs = perm[s]
+        pairs = set((min(a, b), max(a, b)) for a, b in cs.tolist())
+        extra = []
+        while len(extra) < 50_000:
+            a, b = (int(v) for v in rng.integers(0, n, 2))
+            if a != b and (min(a, b), max(a, b)) not in pairs:
+                pairs.add((min(a, b), max(a, b)))
+                extra.append((a, b))
+        for i in range(2000):
+            a, b = int(perm[i % 8]), int(rng.integers(0, n))
+            if a != b and (min(a, b), max(a, b)) not in pairs:
+                pairs.add((min(a, b), max(a, b)))
+                extra.append((a, b))
+        bits = rng.random((len(extra), d, d)) >= 0.12
+        er = (bits * (1 << np.arange(d))[None, None, :]).sum(axis=2).astype(np.uint32)
+        scope = np.concatenate([cs.astype(np.int32), np.array(extra, np.int32)])
+        rel = np.concatenate([r, er])
+        dom = np.full(n, full_word(d), np.uint32)
+        ref = oracle_enforce(n, d, scope, rel, dom)
+        assert ref[1][0] >= 5 and np.count_nonzero(ref[0][0] != full_word(d)) > 100
+        _MAX_N_CASE.update(n=n, d=d, scope=scope, rel=rel, dom=dom, ref=ref)
+    return _MAX_N_CASE
+
+
+@pytest.mark.parametrize("flags", [0, rac.INCREMENTAL])
+def test_maximum_variable_count(flags):
+    c = _max_n_case()
+    got = gpu_enforce(c["n"], c["d"], c["scope"], c["rel"], c["dom"], flags)
+    assert_same(got, c["ref"], "n = 2,000,000, flags %d" % flags)
