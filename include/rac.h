@@ -288,21 +288,27 @@ RAC_API rac_status rac_enforce_host(const rac_network *net, int32_t n_states, co
 /*
  * rac_enforce_noalloc -- rac_enforce without any device allocation.  The
  * paper has no counterpart: this entry point exists for callers that cannot
- * call cudaMalloc while they enforce, such as code running during CUDA graph
- * capture, loops that cannot take the device-wide synchronisation of
- * cudaMalloc/cudaFree, or processes whose device memory belongs to another
- * allocator.
+ * call cudaMalloc while they enforce, such as processes whose device memory
+ * is entirely reserved by another allocator (a framework's caching pool), or
+ * latency-bound loops that cannot take the device-wide synchronisation that
+ * cudaMalloc/cudaFree may imply.
  *
- * Arguments, results and errors are those of rac_enforce.  The scratch space
- * is one static array inside the library (about 312 KiB on every device that
- * loads it, held until the process exits), so:
+ * Arguments, results and errors are those of rac_enforce with the bit-packed
+ * kernel; RAC_KERNEL_TENSOR is refused with RAC_ENOTSUP.  The scratch space
+ * is one static array inside the library (311,808 bytes, about 305 KiB, on
+ * every device that loads it, held until the process exits), so:
  *  - networks with more than RAC_NOALLOC_MAX_VARS variables are rejected with
  *    RAC_EINVAL and an explanatory rac_last_error();
  *  - all calls share the array: calls whose kernels overlap on the GPU (other
  *    streams, other host threads) race and give undefined results;
+ *  - every call resets the array on its stream first, sticky error word
+ *    included: a call whose bounded wait ran out (status RAC_EBARRIER) does
+ *    not poison later calls, unlike rac_enforce's per-stream workspace;
  *  - the first call on a device, with that device current, looks up the
- *    array's device address (and prepares the kernel launch); make that first
- *    call before starting any stream capture.
+ *    array's device address, and the first call for each relation width
+ *    (d rounded up to a multiple of 4) on a device sets that kernel's
+ *    launch attributes; make those first calls before starting any stream
+ *    capture.
  */
 #define RAC_NOALLOC_MAX_VARS 65536
 RAC_API rac_status rac_enforce_noalloc(const rac_network *net, const uint32_t *dom_in,

@@ -1,27 +1,31 @@
 // rac_enforce_noalloc: rac_enforce for callers that cannot allocate device
 // memory at call time.
 //
-// Some callers cannot call cudaMalloc when they enforce: code that runs while
-// a CUDA graph is being captured (an allocation is not a stream operation and
-// cannot be recorded), latency-bound loops that cannot absorb the device-wide
-// synchronisation cudaMalloc and cudaFree imply, and processes whose device
-// memory is entirely owned by another allocator.  This entry point takes its
-// scratch from one fixed array compiled into the library instead of from a
-// per-stream workspace, so it allocates nothing.
+// Some callers of this library cannot call cudaMalloc when they enforce:
+// processes whose device memory is entirely reserved by another allocator
+// (a framework's caching pool that holds the whole card, so a direct
+// cudaMalloc fails or fragments it), and latency-bound loops that cannot
+// absorb the device-wide synchronisation cudaMalloc and cudaFree may imply.
+// This entry point takes its scratch from one fixed array compiled into the
+// library instead of from a per-stream workspace, so it allocates nothing.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
-// library holds it (kScratchWords words, about 312 KiB) until the process
-// exits.  All calls share it and it keeps the previous call's contents, so
-// each call first resets, on its stream, what the kernel expects: the sync
-// words and flag slots to zero and the scratch domain buffer to all ones
-// (cudaMemsetAsync, which allocates nothing).  Two calls whose kernels
-// overlap on the GPU (different streams, or different host threads) race on
-// the array and give undefined results.
+// library holds it (kScratchWords words = 311,808 bytes, about 305 KiB) until
+// the process exits.  All calls share it and it keeps the previous call's
+// contents, so each call first resets, on its stream, what the kernel
+// expects: the sync words (including the sticky error word) and flag slots
+// to zero and the scratch domain buffer to all ones (cudaMemsetAsync, which
+// allocates nothing).  Because the error word is cleared too, a call whose
+// bounded wait ran out does not poison the next one, unlike the per-stream
+// workspace of rac_enforce.  Two calls whose kernels overlap on the GPU
+// (different streams, or different host threads) race on the array and give
+// undefined results.
 //
 // Host code must not use the array's name as a device address: in host code
 // it is a stand-in.  The first call on each device, with that device current,
 // looks the real address up with cudaGetSymbolAddress and keeps it; that
-// first call should come before any stream capture.
+// first call should come before any stream capture.  Only the bit-packed
+// kernel runs here (RAC_KERNEL_TENSOR is refused with RAC_ENOTSUP).
 #include <mutex>
 #include <string>
 
@@ -39,6 +43,7 @@ constexpr int kBufOffset = ((kSyncWords + kFlagWords + 63) / 64) * 64;
 constexpr int kScratchWords = kBufOffset + kNoallocMaxVars;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kScratchWords];
+static_assert(sizeof(g_noalloc_scratch) == 311808, "the documented size of the scratch array");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
@@ -79,6 +84,11 @@ extern "C" rac_status rac_enforce_noalloc(const rac_network *net, const uint32_t
   if (!net || !dom_in || !dom_out || !iterations || !status) {
     set_error("rac_enforce_noalloc: NULL argument");
     return RAC_EINVAL;
+  }
+  if (flags & RAC_KERNEL_TENSOR) {
+    set_error("rac_enforce_noalloc: only the bit-packed kernel runs without allocation "
+              "(RAC_KERNEL_TENSOR needs rac_enforce)");
+    return RAC_ENOTSUP;
   }
   if (flags & ~uint32_t(RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL | RAC_TEST_WITHHOLD_ARRIVAL)) {
     set_error("rac_enforce_noalloc: unknown flag");

@@ -1,18 +1,19 @@
 """rac_enforce_noalloc, the entry point for callers that cannot allocate
-device memory while they enforce (for example during CUDA graph capture): it
-must give exactly what rac_enforce gives, call after call, although every
-call reuses the same static scratch array (GPU).
+device memory while they enforce (a process whose device memory another
+allocator has reserved, or a loop that cannot take the synchronisation
+cudaMalloc may imply): it must give exactly what rac_enforce gives, call
+after call, although every call reuses the same static scratch array (GPU).
 
 This file is collected last so that a run stopping at the first failure has
 already run every other test."""
-import ctypes
+import time
 
 import numpy as np
 import pytest
 
 import racgen
 import paper_2407_11388_b300 as rac
-from gpu_helpers import from_dev, to_dev, torch
+from gpu_helpers import from_dev, oracle_enforce, to_dev, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -60,3 +61,38 @@ def test_noalloc_rejects_networks_above_its_limit():
                                    it.data_ptr(), 0, 0, None)
         assert rc == rac.EINVAL
         assert "65536" in rac.last_error()
+
+
+def test_noalloc_refuses_the_tensor_kernel():
+    n, d = 40, 8
+    net_np = racgen.random_network(3, 0, n, d, 0.5, 0.3)
+    T = torch()
+    with rac.Network(n, d, net_np.scope, net_np.rel) as net:
+        buf = to_dev(racgen.full_domain(n, d))
+        it = T.empty(1, dtype=T.int32, device="cuda:0")
+        rc = rac.lib().rac_enforce_noalloc(net.handle, buf.data_ptr(), buf.data_ptr(),
+                                           it.data_ptr(), it.data_ptr(), 0,
+                                           rac.KERNEL_TENSOR, None)
+        assert rc == rac.ENOTSUP
+        assert "bit-packed" in rac.last_error()
+
+
+def test_noalloc_wait_that_runs_out_does_not_poison_the_next_call():
+    """A bounded device wait made to run out (one CTA withholds its barrier
+    arrival under the test hook, 50 ms limit) gives RAC_EBARRIER; the next
+    call resets the shared array, error word included, and matches the
+    oracle."""
+    T = torch()
+    n, d = 300, 12
+    net_np = racgen.random_network(8, 0, n, d, 0.5, 0.5)
+    dom = racgen.assignment_state(8, 0, 1, n, d)
+    want = oracle_enforce(n, d, net_np.scope, net_np.rel, dom)
+    with rac.Network(n, d, net_np.scope, net_np.rel) as net:
+        t0 = time.perf_counter()
+        got = _via(rac.enforce_noalloc, net, dom, rac.TEST_WITHHOLD_ARRIVAL)
+        assert got[2] == rac.EBARRIER
+        assert time.perf_counter() - t0 < 1.5, "the wait limit under the test hook is 50 ms"
+        for _ in range(2):
+            out, it, st = _via(rac.enforce_noalloc, net, dom, 0)
+            assert np.array_equal(out, want[0][0])
+            assert it == want[1][0] and st == want[2][0]
