@@ -316,6 +316,36 @@ RAC_API rac_status rac_enforce_noalloc(const rac_network *net, const uint32_t *d
                                        int32_t max_sweeps, uint32_t flags, rac_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Partitioned sweep of one network over several ranks (one process per GPU).
+ *
+ * Eq. 1 (Sec. 3) computes every D^(k)[x] from D^(k-1) alone, and a sweep keeps
+ * (x,a) only if it has a support on EVERY constraint of C_x: an AND over the
+ * constraints.  So when the constraints are split over G ranks, rank g's one
+ * sweep of its share (rac_enforce on a network made of those constraints,
+ * max_sweeps = 1, input D^(k-1)) gives a partial next domain
+ * P_g = D^(k-1) AND (supports on its share), and D^(k) = AND_g P_g exactly.
+ * The ranks all-gather their partials (G x n_vars words) and each combines
+ * them with this call; the loop's decisions (some domain changed, some
+ * domain empty) come from the gathered words, identical on every rank, so
+ * no second collective is needed.
+ *
+ * rac_combine_partials -- dom_next[x] = dom_prev[x] AND partials[g][x] for
+ * g < n_parts; flags[0] = 1 iff some dom_next[x] != dom_prev[x], flags[1] =
+ * 1 iff some dom_next[x] == 0 (an empty domain), else 0.
+ *
+ *  partials    DEVICE, n_parts x n_vars words, part g at word g * n_vars (the
+ *              layout of an all-gather of the ranks' partials).
+ *  dom_prev    DEVICE, n_vars words: D^(k-1).
+ *  dom_next    DEVICE, n_vars words: receives D^(k).  dom_next == dom_prev is
+ *              allowed; no other overlap with either input is.
+ *  flags       DEVICE, 2 int32 (cleared and written on `stream`).
+ * Errors: RAC_EINVAL (n_parts < 1, n_vars < 0, a NULL pointer), RAC_ECUDA.
+ */
+RAC_API rac_status rac_combine_partials(int32_t n_parts, int32_t n_vars, const uint32_t *partials,
+                                        const uint32_t *dom_prev, uint32_t *dom_next,
+                                        int32_t *flags, rac_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Learned active-block gating.
  *
  * The paper gates sweeps exactly with Proposition 2 (Sec. 3): sweep k >= 2

@@ -41,7 +41,7 @@ ABI_FUNCTIONS = ("rac_create_network", "rac_create_network_u8", "rac_destroy", "
                  "rac_predictor_num_params", "rac_predictor_create", "rac_predictor_destroy",
                  "rac_predictor_set_weights", "rac_predictor_get_weights",
                  "rac_predictor_gradient", "rac_predictor_train", "rac_predictor_predict",
-                 "rac_enforce_learned")
+                 "rac_enforce_learned", "rac_combine_partials")
 NOALLOC_MAX_VARS = 65536
 PREDICTOR_FEATURES = 8
 PREDICTOR_PARAMS = 4801
@@ -94,6 +94,8 @@ def lib():
         L.rac_plan_destroy.argtypes = [vp]
         L.rac_assign_enforce.restype = i32
         L.rac_assign_enforce.argtypes = [vp, vp, vp, i32, i32, vp, vp, i32, u32, vp]
+        L.rac_combine_partials.restype = i32
+        L.rac_combine_partials.argtypes = [i32, i32, vp, vp, vp, vp, vp]
         L.rac_network_info.restype = i32
         L.rac_network_info.argtypes = [vp, ctypes.POINTER(i64), i32]
         L.rac_last_error.restype = ctypes.c_char_p
@@ -247,12 +249,26 @@ def enforce_noalloc(net, dom_in, dom_out, iterations, status, max_sweeps=0, flag
                     stream=None):
     """rac_enforce_noalloc: like enforce(), with the library's static scratch
     array instead of an allocated workspace, for callers that cannot allocate
-    device memory at call time (for example while a CUDA graph is being
-    captured).  At most NOALLOC_MAX_VARS variables; calls must not overlap on
-    the GPU; the first call on a device should precede any stream capture."""
+    device memory at call time (a process whose device memory another
+    allocator has reserved, a loop that cannot take the synchronisation
+    cudaMalloc may imply).  At most NOALLOC_MAX_VARS variables; calls must not
+    overlap on the GPU; the first call on a device should precede any stream
+    capture."""
     _check(lib().rac_enforce_noalloc(net.handle, _ptr(dom_in), _ptr(dom_out), _ptr(iterations),
                                      _ptr(status), int(max_sweeps), int(flags), _stream(stream)),
            "rac_enforce_noalloc")
+
+
+def combine_partials(partials, dom_prev, dom_next, flags, stream=None):
+    """rac_combine_partials: dom_next = dom_prev AND every row of partials
+    (n_parts, n_vars); flags[0] = some domain changed, flags[1] = some domain
+    empty (asynchronous on `stream`)."""
+    n_parts, n_vars = (int(v) for v in partials.shape)
+    if dom_prev.numel() != n_vars or dom_next.numel() != n_vars or flags.numel() < 2:
+        raise RacError(EINVAL, "combine_partials: sizes disagree")
+    _check(lib().rac_combine_partials(n_parts, n_vars, _ptr(partials), _ptr(dom_prev),
+                                      _ptr(dom_next), _ptr(flags), _stream(stream)),
+           "rac_combine_partials")
 
 
 def enforce_batch(nets, item_net, item_dom_off, dom_in, dom_out, iterations, status,
