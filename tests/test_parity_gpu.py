@@ -92,44 +92,45 @@ def test_small_random_csp_config(seed):
                     oracle_enforce(50, 10, net.scope, net.rel, doms[:1], flags), "seed %d" % seed)
 
 
-def test_dense_500_config():
+@pytest.mark.parametrize("seed", range(5))
+def test_dense_500_config(seed):
     """n=500, d=20, complete graph, tightness 0.35, full domains (the
-    single-state launch the benchmark times) plus assignment states."""
-    net = racgen.random_network(0, 0, 500, 20, 1.0, 0.35)
+    single-state launch the benchmark times) plus assignment states, seeds
+    0-4."""
+    net = racgen.random_network(seed, 0, 500, 20, 1.0, 0.35)
     full = racgen.full_domain(500, 20)
     assert_same(gpu_enforce(500, 20, net.scope, net.rel, full),
                 oracle_enforce(500, 20, net.scope, net.rel, full), "dense500 full")
-    doms = np.array([racgen.assignment_state(0, 0, s, 500, 20) for s in range(6)])
+    doms = np.array([racgen.assignment_state(seed, 0, s, 500, 20) for s in range(6)])
     assert_same(gpu_enforce(500, 20, net.scope, net.rel, doms, rac.INCREMENTAL, shuffle_seed=1),
                 oracle_enforce(500, 20, net.scope, net.rel, doms), "dense500 states")
 
 
-def test_dense_2000_config():
+@pytest.mark.parametrize("seed", range(5))
+def test_dense_2000_config(seed):
     """n=2000, d=32, density 0.9, tightness 0.3 (a 230 MB relation store),
-    full domains and two assignment states."""
-    net = racgen.random_network(0, 0, 2000, 32, 0.9, 0.3)
+    full domains and two assignment states, seeds 0-4."""
+    net = racgen.random_network(seed, 0, 2000, 32, 0.9, 0.3)
     full = racgen.full_domain(2000, 32)
     assert_same(gpu_enforce(2000, 32, net.scope, net.rel, full),
                 oracle_enforce(2000, 32, net.scope, net.rel, full, threads=32), "dense2000 full")
-    doms = np.array([racgen.assignment_state(0, 0, s, 2000, 32) for s in range(2)])
+    doms = np.array([racgen.assignment_state(seed, 0, s, 2000, 32) for s in range(2)])
     assert_same(gpu_enforce(2000, 32, net.scope, net.rel, doms, shuffle_seed=3),
                 oracle_enforce(2000, 32, net.scope, net.rel, doms, threads=32), "dense2000 states")
 
 
-@pytest.mark.parametrize("B,sample", [(32, None), (128, 24)])
-def test_n1000_d24_many_states_config(B, sample):
-    """n=1000, d=24, density 0.8, tightness 0.3 with 32 or 128 assignment
-    states in one launch (the benchmark's many-state launches): every state,
-    or an even sample of the 128, against the oracle, plain and with
-    Proposition 2."""
-    net_np = racgen.random_network(0, 0, 1000, 24, 0.8, 0.3)
-    doms = np.array([racgen.assignment_state(0, 0, s, 1000, 24) for s in range(B)])
-    pick = np.arange(B) if sample is None else np.linspace(0, B - 1, sample).astype(int)
-    ref = oracle_enforce(1000, 24, net_np.scope, net_np.rel, doms[pick], threads=32)
+@pytest.mark.parametrize("B,seed", [(32, 0), (32, 1), (32, 2), (32, 3), (32, 4), (128, 0)])
+def test_n1000_d24_many_states_config(B, seed):
+    """n=1000, d=24, density 0.8, tightness 0.3 with 32 assignment states
+    (seeds 0-4) or 128 (seed 0) in one launch (the benchmark's many-state
+    launches): every state against the oracle, plain and with Proposition 2."""
+    net_np = racgen.random_network(seed, 0, 1000, 24, 0.8, 0.3)
+    doms = np.array([racgen.assignment_state(seed, 0, s, 1000, 24) for s in range(B)])
+    ref = oracle_enforce(1000, 24, net_np.scope, net_np.rel, doms, threads=32)
     with rac.Network(1000, 24, net_np.scope, net_np.rel) as net:
         for flags in (0, rac.INCREMENTAL):
-            out, its, sts = gpu_enforce(1000, 24, net_np.scope, net_np.rel, doms, flags, net=net)
-            assert_same((out[pick], its[pick], sts[pick]), ref, "B=%d flags %d" % (B, flags))
+            got = gpu_enforce(1000, 24, net_np.scope, net_np.rel, doms, flags, net=net)
+            assert_same(got, ref, "B=%d seed %d flags %d" % (B, seed, flags))
 
 
 def test_search_path_states():
