@@ -8,6 +8,9 @@
 #include <string>
 #include <vector>
 
+#include <atomic>
+#include <chrono>
+
 #include "rac_internal.h"
 
 namespace rac {
@@ -646,8 +649,8 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
   // pinned staging buffer at its end (posted writes, no separate copy out);
   // the tensor-core kernel and calls of several launches copy them out.
   const bool direct = !(flags & RAC_KERNEL_TENSOR) && n_states <= kMaxStatesPerLaunch;
-  // pinned staging: [input words][result words][iterations][status]
-  const size_t total = 2 * words + 2 * size_t(n_states);
+  // pinned staging: [input words][result words][iterations][status][completion word]
+  const size_t total = 2 * words + 2 * size_t(n_states) + 1;
   rac_status rc = RAC_OK;
   Workspace *w0 = get_workspace(net, s, std::min<int32_t>(n_states, kMaxStatesPerLaunch), 0, &rc);
   if (!w0) return rc;
@@ -677,6 +680,9 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
     }
     w0->host_pin_dev = static_cast<uint32_t *>(dp);
     w0->host_cap = total;
+    // the completion word starts at the number of direct launches this
+    // workspace has completed (Sync::done_seq on the device)
+    w0->host_pin[total - 1] = w0->host_seq;
   }
   uint32_t *d_dom = w0->host_dom;
   int32_t *d_res = reinterpret_cast<int32_t *>(d_dom + words);
@@ -694,6 +700,7 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
       P.iterations = d_res;
       P.status = d_res + n_states;
       P.host_out = w0->host_pin_dev + words;
+      P.host_done = w0->host_pin_dev + (total - 1);
       return launch_for(P, flags, q);
     }
     // the launches (state chunks), one copy out
@@ -754,8 +761,31 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
       set_error("");
     }
   }
-  const cudaError_t e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess && rc == RAC_OK) rc = cuda_fail(e, "cudaStreamSynchronize");
+  // One direct launch: wait for its completion word in pinned memory (the
+  // last CTA writes it after every result is in host memory) instead of
+  // synchronising the stream; the kernel's exit may still be in flight, and
+  // later work on `stream` is ordered after it.  A word that does not come
+  // within the time limit (the launch failed) falls back to synchronising.
+  bool seen = false;
+  if (direct && rc == RAC_OK) {
+    const volatile uint32_t *done = w0->host_pin + (total - 1);
+    const uint32_t want = w0->host_seq + 1u;
+    const auto t0 = std::chrono::steady_clock::now();
+    const auto limit = std::chrono::nanoseconds(2 * wait_limit_for(flags) + 1000000000ull);
+    for (uint32_t i = 0;; ++i) {
+      if (*done == want) {
+        seen = true;
+        break;
+      }
+      if ((i & 255u) == 0u && std::chrono::steady_clock::now() - t0 > limit) break;
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+  }
+  if (!seen) {
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess && rc == RAC_OK) rc = cuda_fail(e, "cudaStreamSynchronize");
+  }
+  if (direct) w0->host_seq = *reinterpret_cast<volatile uint32_t *>(w0->host_pin + (total - 1));
   if (rc == RAC_OK) {
     std::memcpy(dom_out, pin_res, words * 4);
     std::memcpy(iterations, pin_res + words, size_t(n_states) * 4);

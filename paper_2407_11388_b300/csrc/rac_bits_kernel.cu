@@ -1261,6 +1261,21 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
       }
     }
   }
+  if (P.host_done) {
+    // the last CTA to finish its host writes publishes the completion
+    // number: the caller reads the results once it sees it
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence_system();
+      if (atomicAdd(&P.sync->done_cta, 1u) == uint32_t(G) - 1u) {
+        P.sync->done_cta = 0u;
+        const uint32_t seq = P.sync->done_seq + 1u;
+        P.sync->done_seq = seq;
+        __threadfence_system();
+        *reinterpret_cast<volatile uint32_t *>(P.host_done) = seq;
+      }
+    }
+  }
   if (failed && tid == 0) atomicOr(&P.sync->err, kErrCopyWait);  // poison (idempotent)
   // Drain copies still in flight (only after a failed wait or on a poisoned
   // workspace) before the CTA's shared memory goes away.

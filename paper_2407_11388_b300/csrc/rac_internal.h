@@ -78,6 +78,11 @@ struct Sync {
                               // a domain << 32 | CTAs that failed a wait << 48
   uint32_t base;
   uint32_t err;  // kErr* bits; sticky: a failed launch poisons the workspace
+  // host entry point: CTAs done writing their results into host memory in
+  // this launch (the last one resets it), and the number of such launches
+  // completed on the workspace (the last CTA publishes it to the host)
+  uint32_t done_cta;
+  uint32_t done_seq;
 };
 constexpr int kBarCountBits = 16;  // grids of at most 65535 CTAs
 
@@ -105,6 +110,10 @@ struct LaunchParams {
   // optional (contiguous launches): the results also written to host memory
   // at the end -- n_states x n domain words, then iterations, then status
   uint32_t *host_out;
+  // optional, with host_out: host word that receives Sync::done_seq once
+  // every CTA's results are in host memory (the caller waits on it instead
+  // of synchronising the stream)
+  uint32_t *host_done;
   uint32_t *any;             // [3][flag_stride] some value removed in the sweep
   uint32_t *wipe;            // [3][flag_stride] some domain emptied in the sweep
   uint32_t *chg;             // [3][flag_stride][nb] variables that lost a value
@@ -218,6 +227,7 @@ struct Workspace {
   uint32_t *host_pin = nullptr;
   uint32_t *host_pin_dev = nullptr;  // the device's address of host_pin
   size_t host_cap = 0;
+  uint32_t host_seq = 0;             // the last completion number seen in host_pin
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t host_graph = nullptr;
   int32_t graph_states = -1, graph_max_sweeps = 0;
