@@ -502,7 +502,8 @@ class Prepared:
             self.cfg = config_of(args.workload, spec, net_np, True)
         self.nets_np, self.items, self.offs, self.doms = nets_np, items, offs, doms
         self.B = len(items)
-        self.nets = [rac.Network(x.n, x.d, x.scope, x.rel) for x in nets_np]
+        per_launch = spec.get("states_per_net", spec.get("n_states", 1))
+        self.nets = [rac.Network(x.n, x.d, x.scope, x.rel, states=per_launch) for x in nets_np]
         self.flat = flat
         self.din = torch.from_numpy(np.ascontiguousarray(flat).view(np.int32)).to(dev)
         self.dout = torch.empty_like(self.din)

@@ -80,6 +80,14 @@ typedef int32_t rac_status;
  * count do not depend on it. */
 #define RAC_LAYOUT_ROWS(l) ((uint32_t)((l) + 1) << 8)
 #define RAC_LAYOUT_ROWS_MASK 0xF00u
+/* CTAs of the network's persistent launches (the bit-packed kernel):
+ * RAC_LAYOUT_MAX_CTAS(c), 1 <= c <= 65535, caps the grid at c.  Without it
+ * the grid is every resident CTA of the GPU, capped at the number of tiles:
+ * CTA c owns tiles c, c + G, ..., so a CTA beyond the tile count would only
+ * take part in the sweep barriers.  The result and the sweep count do not
+ * depend on it. */
+#define RAC_LAYOUT_MAX_CTAS(c) ((uint32_t)(c) << 16)
+#define RAC_LAYOUT_MAX_CTAS_MASK 0xFFFF0000u
 
 /* flags of the enforce calls */
 #define RAC_STOP_ON_WIPEOUT 0x1u /* end after the first sweep that leaves a domain

@@ -26,6 +26,11 @@ LAYOUT_BITS = 0x1
 def LAYOUT_ROWS(log2_rows):
     """layout flag: relation tiles of 2**log2_rows rows (RAC_LAYOUT_ROWS)."""
     return (int(log2_rows) + 1) << 8
+
+
+def LAYOUT_MAX_CTAS(ctas):
+    """layout flag: at most `ctas` CTAs per launch (RAC_LAYOUT_MAX_CTAS)."""
+    return int(ctas) << 16
 STOP_ON_WIPEOUT = 0x1
 INCREMENTAL = 0x2
 VERIFY_FULL = 0x4  # rac_enforce_learned: literal full verification sweep (see include/rac.h)
@@ -166,10 +171,14 @@ class Network:
     themselves, an (m, d, d) uint8 or bool array with rel[c, a, b] =
     R_xy[a][b] (packed by the library: rac_create_network_u8)."""
 
-    def __init__(self, n, d, scope, rel, layout=LAYOUT_BITS, rows=None):
-        """rows: tile rows (a power of two); None takes the autotuned table's
-        choice for this (d, density) if one is installed (tile_table.json),
-        else the library default."""
+    def __init__(self, n, d, scope, rel, layout=LAYOUT_BITS, rows=None, max_ctas=None,
+                 states=None):
+        """rows: tile rows (a power of two); max_ctas: grid cap of the
+        network's launches.  None takes the autotuned table's choice for
+        this (d, density, states per launch) if one is installed
+        (tile_table.json), else the library default; `states` is the number
+        of domain states the caller expects to enforce per launch (1 if
+        not given)."""
         scope = np.ascontiguousarray(scope, dtype=np.int32).reshape(-1, 2)
         rel = np.asarray(rel)
         if rel.ndim == 3:
@@ -184,9 +193,20 @@ class Network:
             create = lib().rac_create_network
         if rel.shape[0] != scope.shape[0]:
             raise RacError(EINVAL, "scope and rel disagree on the number of constraints")
-        if rows is None and not (int(layout) & 0xF00):
-            from .autotune import table_rows
-            rows = table_rows(int(d), scope.shape[0] / max(1.0, n * (n - 1) / 2.0))
+        if (rows is None and not (int(layout) & 0xF00)) or \
+                (max_ctas is None and not (int(layout) & 0xFFFF0000)):
+            from .autotune import table_choice
+            t_rows, t_ctas = table_choice(int(d), scope.shape[0] / max(1.0, n * (n - 1) / 2.0),
+                                          int(states or 1))
+            if rows is None and not (int(layout) & 0xF00):
+                rows = t_rows
+            if max_ctas is None and not (int(layout) & 0xFFFF0000):
+                max_ctas = t_ctas
+        if max_ctas is not None:
+            max_ctas = int(max_ctas)
+            if not 1 <= max_ctas <= 65535:
+                raise RacError(EINVAL, "max_ctas must be in [1, 65535]")
+            layout = int(layout) | LAYOUT_MAX_CTAS(max_ctas)
         if rows is not None:
             rows = int(rows)
             if rows < 2 or rows > 32 or rows & (rows - 1):

@@ -1,21 +1,26 @@
-"""Autotuned tile table of the relation layout.
+"""Autotuned launch table: tile rows and grid cap per (d, density, states).
 
 A network's relations are stored in tiles ("slabs") of 32 column variables by
 `rows` row variables of one block pair; the kernels stream one tile at a time
-through shared memory (rac_create_network, RAC_LAYOUT_ROWS).  Small tiles
-spread uneven networks more evenly over the CTAs of a batched launch and let
-Proposition 2 skip finer pieces; large tiles pay the per-tile overhead
-(stage hand-off, domain staging, pipeline latency) fewer times.  The best
-size depends on d, the density and the GPU, so it is measured:
+through shared memory (rac_create_network, RAC_LAYOUT_ROWS), and CTA c of a
+persistent launch owns tiles c, c + G, ...  (RAC_LAYOUT_MAX_CTAS caps G).
+Small tiles spread the work more evenly over the CTAs and let Proposition 2
+skip finer pieces; large tiles pay the per-tile overhead (stage hand-off,
+domain staging, pipeline latency) fewer times.  A smaller grid makes each
+sweep's grid barrier cheaper and leaves each CTA more tiles to overlap.  The
+best pair depends on d, the density, the number of states per launch and the
+GPU, so it is measured:
 
     python -m paper_2407_11388_b300.autotune [--out FILE] [--runs 20]
 
-times every admissible row count on seeded synthetic batches of each
-(d, density) bucket -- several networks with 64 assignment states each,
-enforced in one batched launch through a rac_plan, CUDA events, L2 flushed
-between runs -- and writes the fastest per bucket to a JSON table.
-Network() consults that table (tile_table.json next to this file) when no
-row count is given.
+For every (d, density, states) bucket it times every admissible row count
+and grid cap on seeded synthetic networks of the bucket (120, 360 and 700
+variables at the bucket's middle d and density, tightness 0.3, assignment
+states; one launch per network -- rac_enforce for one state, rac_enforce_batch
+for more -- CUDA events, L2 flushed before each launch, median of `runs`),
+and writes the fastest pair per bucket to a JSON table.  Network() consults
+that table (tile_table.json next to this file) for what its caller leaves
+open.
 """
 import argparse
 import json
@@ -26,6 +31,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 TABLE = os.path.join(HERE, "tile_table.json")
 D_BUCKETS = [(1, 8), (9, 16), (17, 24), (25, 32)]
 DENSITY_BUCKETS = [(0.0, 0.6), (0.6, 1.0)]
+STATE_BUCKETS = [(1, 1), (2, 16), (17, 1 << 30)]
+STATES_TIMED = {(1, 1): 1, (2, 16): 8, (17, 1 << 30): 32}
+CTA_CAPS = (None, 74, 37)  # every resident CTA (capped at the tile count), or fewer
 STAGE_BYTES = 32768  # relation bytes of one tile the kernels can stage
 
 _table = None
@@ -50,18 +58,28 @@ def load_table(path=TABLE):
     return _table
 
 
-def table_rows(d, density, path=TABLE):
-    """The tuned tile rows for this shape, or None (library default)."""
+def table_choice(d, density, states=1, path=TABLE):
+    """(rows, max_ctas) tuned for this shape; None for what the table does
+    not fix (the library default)."""
     for e in load_table(path).get("entries", []):
-        if e["d_lo"] <= d <= e["d_hi"] and e["dens_lo"] <= density <= e["dens_hi"]:
-            r = int(e["rows"])
-            return r if r in admissible_rows(d) else None
-    return None
+        if not (e["d_lo"] <= d <= e["d_hi"] and e["dens_lo"] <= density <= e["dens_hi"]):
+            continue
+        if not e.get("st_lo", 1) <= states <= e.get("st_hi", 1 << 30):
+            continue
+        r = int(e["rows"])
+        return (r if r in admissible_rows(d) else None), e.get("max_ctas")
+    return None, None
 
 
-def _bucket_batch(d_lo, d_hi, dens_lo, dens_hi, seed, states):
+def table_rows(d, density, states=1, path=TABLE):
+    """The tuned tile rows for this shape, or None (library default)."""
+    return table_choice(d, density, states, path)[0]
+
+
+def _bucket_networks(d_lo, d_hi, dens_lo, dens_hi, seed, states):
     """Seeded representatives of a bucket: networks of 120, 360 and 700
-    variables at the bucket's middle d and density, tightness 0.3."""
+    variables at the bucket's middle d and density, tightness 0.3, with
+    `states` assignment states each."""
     import racgen
     d = (d_lo + d_hi + 1) // 2
     dens = 0.5 * (dens_lo + dens_hi)
@@ -73,59 +91,70 @@ def _bucket_batch(d_lo, d_hi, dens_lo, dens_hi, seed, states):
     return d, dens, nets
 
 
-def time_rows(nets, rows, runs):
-    """Median time (ms) of one batched enforcement of all states of all
-    networks with tiles of `rows` rows."""
+def time_choice(nets, rows, max_ctas, runs):
+    """Median over runs of the summed time (ms) of one launch per network
+    (all of its states) with this tile height and grid cap."""
     import numpy as np
     import torch
-    from . import Network, Plan
-    handles = [Network(x.n, x.d, x.scope, x.rel, rows=rows) for x, _ in nets]
-    items, offs, flat, pos = [], [], [], 0
-    for i, (x, doms) in enumerate(nets):
-        for dom in doms:
-            items.append(i)
-            offs.append(pos)
-            flat.append(dom)
-            pos += x.n
-    flat = np.concatenate(flat).astype(np.uint32)
-    din = torch.from_numpy(flat.view(np.int32)).cuda()
-    dout = torch.empty_like(din)
-    it = torch.empty(len(items), dtype=torch.int32, device="cuda")
-    st = torch.empty_like(it)
-    plan = Plan(handles, np.array(items, np.int32), np.array(offs, np.int64))
+    from . import Network, enforce, enforce_batch
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
-    ts = []
-    for r in range(runs + 3):
-        flush.fill_(r)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        plan.enforce(din, dout, it, st)
-        b.record()
-        torch.cuda.synchronize()
-        if r >= 3:
-            ts.append(a.elapsed_time(b))
-    plan.close()
-    for h in handles:
-        h.close()
-    return float(np.median(ts))
+    total = 0.0
+    for x, doms in nets:
+        with Network(x.n, x.d, x.scope, x.rel, rows=rows,
+                     max_ctas=max_ctas if max_ctas is not None else 65535) as h:
+            B = len(doms)
+            din = torch.from_numpy(np.concatenate(doms).astype(np.uint32).view(np.int32)).cuda()
+            dout = torch.empty_like(din)
+            it = torch.empty(B, dtype=torch.int32, device="cuda")
+            st = torch.empty_like(it)
+            items = np.zeros(B, np.int32)
+            offs = np.arange(B, dtype=np.int64) * x.n
+
+            def launch():
+                if B == 1:
+                    enforce(h, din, dout, it, st)
+                else:
+                    enforce_batch([h], items, offs, din, dout, it, st)
+
+            ts = []
+            for r in range(runs + 3):
+                flush.fill_(r)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                launch()
+                b.record()
+                torch.cuda.synchronize()
+                if r >= 3:
+                    ts.append(a.elapsed_time(b))
+            total += float(np.median(ts))
+    return total
 
 
-def tune(runs=20, states=64, seed=7, out=TABLE, log=print):
+def tune(runs=20, seed=7, out=TABLE, log=print):
     import torch
     entries = []
-    for d_lo, d_hi in D_BUCKETS:
-        for dens_lo, dens_hi in DENSITY_BUCKETS:
-            d, dens, nets = _bucket_batch(d_lo, d_hi, dens_lo, dens_hi, seed, states)
-            times = {r: time_rows(nets, r, runs) for r in admissible_rows(d)}
-            best = min(times, key=times.get)
-            log("d %2d-%2d density %.1f-%.1f: %s -> rows %d" % (
-                d_lo, d_hi, dens_lo, dens_hi,
-                " ".join("%d:%.3fms" % (r, t) for r, t in sorted(times.items())), best))
-            entries.append({"d_lo": d_lo, "d_hi": d_hi, "dens_lo": dens_lo, "dens_hi": dens_hi,
-                            "rows": best, "ms": {str(r): round(t, 4) for r, t in times.items()}})
-    table = {"version": 1, "device": torch.cuda.get_device_name(0), "states": states,
+    for st_lo, st_hi in STATE_BUCKETS:
+        states = STATES_TIMED[(st_lo, st_hi)]
+        for d_lo, d_hi in D_BUCKETS:
+            for dens_lo, dens_hi in DENSITY_BUCKETS:
+                d, dens, nets = _bucket_networks(d_lo, d_hi, dens_lo, dens_hi, seed, states)
+                times = {(r, c): time_choice(nets, r, c, runs)
+                         for r in admissible_rows(d) for c in CTA_CAPS}
+                best = min(times, key=times.get)
+                default = times[(max(admissible_rows(d)), None)]
+                log("states %d d %2d-%2d density %.1f-%.1f: best rows %d ctas %s (%.3f ms; "
+                    "library default %.3f ms)" % (states, d_lo, d_hi, dens_lo, dens_hi, best[0],
+                                                  best[1], times[best], default))
+                entries.append({"d_lo": d_lo, "d_hi": d_hi, "dens_lo": dens_lo,
+                                "dens_hi": dens_hi, "st_lo": st_lo, "st_hi": st_hi,
+                                "rows": best[0], "max_ctas": best[1],
+                                "ms": {"%d/%s" % (r, c if c is not None else "all"): round(t, 4)
+                                       for (r, c), t in times.items()}})
+    table = {"version": 2, "device": torch.cuda.get_device_name(0),
+             "states_timed": {"%d-%d" % k: v for k, v in STATES_TIMED.items()},
              "runs": runs, "seed": seed, "created": time.strftime("%Y-%m-%d %H:%M:%S"),
+             "key": "ms: 'rows/grid cap' -> summed median launch time of the three networks",
              "entries": entries}
     with open(out, "w") as f:
         json.dump(table, f, indent=1)
@@ -138,8 +167,7 @@ if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=TABLE)
     ap.add_argument("--runs", type=int, default=20)
-    ap.add_argument("--states", type=int, default=64)
     a = ap.parse_args()
     import sys
     sys.path.insert(0, os.path.dirname(HERE))
-    tune(a.runs, a.states, out=a.out)
+    tune(a.runs, out=a.out)

@@ -71,6 +71,7 @@ NetDev net_dev(const rac_network *net) {
   N.nb = net->nb;
   N.rows_per_slab = net->rows_per_slab;
   N.n_slabs = int32_t(net->n_slabs);
+  N.max_ctas = net->max_ctas;
   N.rel = static_cast<const uint4 *>(net->d_rel);
   N.slabs = net->d_slabs;
   N.slab_feat = net->d_slab_feat;
@@ -239,7 +240,7 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
     set_error("more constraints than pairs of variables (each pair takes at most one)");
     return RAC_EINVAL;
   }
-  if (layout_flags & ~(RAC_LAYOUT_BITS | RAC_LAYOUT_ROWS_MASK)) {
+  if (layout_flags & ~(RAC_LAYOUT_BITS | RAC_LAYOUT_ROWS_MASK | RAC_LAYOUT_MAX_CTAS_MASK)) {
     set_error("unknown layout flag");
     return RAC_EINVAL;
   }
@@ -388,6 +389,7 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
   net->q = q;
   net->nb = nb;
   net->rows_per_slab = rows;
+  net->max_ctas = int32_t(layout_flags >> 16);
   net->m = n_cons;
   net->n_slabs = int64_t(slabs.size());
   net->first.assign(slabs.begin(), slabs.begin() + std::min<size_t>(slabs.size(), kMaxFirst));

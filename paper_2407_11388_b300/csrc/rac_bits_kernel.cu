@@ -34,6 +34,8 @@
 
 #include <cstdio>
 
+#include <algorithm>
+
 #include "rac_device.cuh"
 #include "rac_internal.h"
 #include "rac_mlp.cuh"
@@ -1295,7 +1297,11 @@ rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
                                    threads_for(kVar), smem, "bit-packed kernel set-up", &per_sm,
                                    &sms);
   if (rc != RAC_OK) return rc;
-  const int grid = per_sm * sms;
+  // every resident CTA, but no more than the tiles (a CTA without a tile
+  // would only join the sweep barriers) nor the network's cap
+  int grid = per_sm * sms;
+  grid = std::min(grid, std::max(1, P.net.n_slabs));
+  if (P.net.max_ctas > 0) grid = std::min(grid, P.net.max_ctas);
   cudaError_t e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(grid));

@@ -60,6 +60,7 @@ constexpr int kDomWords = 5040;   // domain words a CTA keeps in shared memory p
 
 struct NetDev {
   int32_t n, d, dp, q, nb, rows_per_slab, n_slabs;
+  int32_t max_ctas;  // > 0: grid cap of the network's launches (RAC_LAYOUT_MAX_CTAS)
   const uint4 *rel;
   const SlabDesc *slabs;
   const float2 *slab_feat;  // per slab: (tightness, density), the predictor's f3 and f4
@@ -242,6 +243,7 @@ struct Workspace {
 
 struct rac_network {
   int32_t n = 0, d = 0, dp = 0, q = 0, nb = 0, rows_per_slab = 0;
+  int32_t max_ctas = 0;  // RAC_LAYOUT_MAX_CTAS, 0: none
   int64_t m = 0;
   int64_t n_slabs = 0;
   size_t rel_bytes = 0;
