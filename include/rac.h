@@ -278,15 +278,20 @@ RAC_API void rac_plan_destroy(rac_plan *plan);
  * rac_enforce_host -- rac_enforce on HOST buffers: copies the n_states
  * states (n_states x n_vars words, state s at word s*n_vars) to the device,
  * enforces them as one batch on `net`, copies domains, iterations and status
- * back, and waits for `stream` before returning.  The caller's buffers (any
- * host memory) are copied with memcpy to and from a pinned staging buffer
- * that the library allocates per (network, stream) and frees in rac_destroy;
- * the copy in, the launches and (calls of several launches, or the
- * tensor-core kernel) the copy out form a CUDA graph, recorded on the first
- * call with a given (n_states, max_sweeps, flags) and replayed by later calls
- * with the same ones; a call of one bit-packed launch has the kernel write
- * its results straight into the pinned buffer.  Calls on the same (network,
- * stream) must not overlap.
+ * back, and returns once they are in the caller's buffers.  The caller's
+ * buffers (any host memory) are copied with memcpy to and from a pinned
+ * staging buffer that the library allocates per (network, stream) and frees
+ * in rac_destroy; the copy in, the launches and (calls of several launches,
+ * or the tensor-core kernel) the copy out form a CUDA graph, recorded on the
+ * first call with a given (n_states, max_sweeps, flags) and replayed by later
+ * calls with the same ones.  A call of one bit-packed launch has the kernel
+ * write its results straight into the pinned buffer, and its last CTA then
+ * writes a completion number there: the call waits for that number instead
+ * of synchronising `stream` (the kernel's exit may still be in flight when it
+ * returns; later work on `stream` is ordered after it), and synchronises
+ * `stream` only if the number does not come within the wait limit.  Other
+ * calls synchronise `stream`.  Calls on the same (network, stream) must not
+ * overlap.
  * Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA.
  */
 RAC_API rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint32_t *dom_in,

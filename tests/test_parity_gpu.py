@@ -427,3 +427,35 @@ def test_maximum_variable_count(flags):
     c = _max_n_case()
     got = gpu_enforce(c["n"], c["d"], c["scope"], c["rel"], c["dom"], flags)
     assert_same(got, c["ref"], "n = 2,000,000, flags %d" % flags)
+
+
+@pytest.mark.parametrize("ctas", [1, 2, 7, 37, 65535])
+def test_grid_cap_does_not_change_results(ctas):
+    """RAC_LAYOUT_MAX_CTAS: a CTA then owns many tiles (one CTA: all of them)
+    and the grid barrier joins fewer CTAs; domains, sweep counts and statuses
+    stay the oracle's, one state and many, plain and with Proposition 2 and
+    stop-on-wipeout, and through the no-allocation and host entry points."""
+    n, d = 400, 16
+    net_np = racgen.random_network(31, 0, n, d, 0.3, 0.58)
+    doms = np.array([racgen.assignment_state(31, 0, s, n, d) for s in range(9)])
+    with rac.Network(n, d, net_np.scope, net_np.rel, max_ctas=ctas) as net:
+        for flags in (0, rac.INCREMENTAL, rac.STOP_ON_WIPEOUT):
+            want = oracle_enforce(n, d, net_np.scope, net_np.rel, doms, flags)
+            assert_same(gpu_enforce(n, d, net_np.scope, net_np.rel, doms, flags, net=net), want,
+                        "cap %d flags %d" % (ctas, flags))
+            assert_same(gpu_enforce(n, d, net_np.scope, net_np.rel, doms[:1], flags, net=net),
+                        tuple(a[:1] for a in want), "cap %d flags %d one state" % (ctas, flags))
+        assert max(want[1]) >= 3
+        out, it, st = rac.enforce_host(net, doms)
+        want = oracle_enforce(n, d, net_np.scope, net_np.rel, doms)
+        assert np.array_equal(out, want[0]) and list(it) == list(want[1])
+        assert list(st) == list(want[2])
+        T = torch()
+        din = to_dev(doms[0])
+        dout = T.empty_like(din)
+        its = T.empty(1, dtype=T.int32, device="cuda:0")
+        sts = T.empty(1, dtype=T.int32, device="cuda:0")
+        rac.enforce_noalloc(net, din, dout, its, sts)
+        T.cuda.synchronize()
+        assert np.array_equal(from_dev(dout), want[0][0])
+        assert (int(its.item()), int(sts.item())) == (want[1][0], want[2][0])
