@@ -445,7 +445,8 @@ def test_grid_cap_does_not_change_results(ctas):
                         "cap %d flags %d" % (ctas, flags))
             assert_same(gpu_enforce(n, d, net_np.scope, net_np.rel, doms[:1], flags, net=net),
                         tuple(a[:1] for a in want), "cap %d flags %d one state" % (ctas, flags))
-        assert max(want[1]) >= 3
+            if flags == 0:
+                assert max(want[1]) >= 3  # removals cascade over several sweeps
         out, it, st = rac.enforce_host(net, doms)
         want = oracle_enforce(n, d, net_np.scope, net_np.rel, doms)
         assert np.array_equal(out, want[0]) and list(it) == list(want[1])
