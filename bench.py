@@ -503,7 +503,8 @@ class Prepared:
         self.nets_np, self.items, self.offs, self.doms = nets_np, items, offs, doms
         self.B = len(items)
         per_launch = spec.get("states_per_net", spec.get("n_states", 1))
-        self.nets = [rac.Network(x.n, x.d, x.scope, x.rel, states=per_launch) for x in nets_np]
+        self.nets = [rac.Network(x.n, x.d, x.scope, x.rel, states=per_launch,
+                                 plan=len(nets_np) > 1) for x in nets_np]
         self.flat = flat
         self.din = torch.from_numpy(np.ascontiguousarray(flat).view(np.int32)).to(dev)
         self.dout = torch.empty_like(self.din)

@@ -172,13 +172,14 @@ class Network:
     R_xy[a][b] (packed by the library: rac_create_network_u8)."""
 
     def __init__(self, n, d, scope, rel, layout=LAYOUT_BITS, rows=None, max_ctas=None,
-                 states=None):
+                 states=None, plan=False):
         """rows: tile rows (a power of two); max_ctas: grid cap of the
         network's launches.  None takes the autotuned table's choice for
         this (d, density, states per launch) if one is installed
         (tile_table.json), else the library default; `states` is the number
         of domain states the caller expects to enforce per launch (1 if
-        not given)."""
+        not given), `plan` whether the network is to be enforced with others
+        in multi-network plans."""
         scope = np.ascontiguousarray(scope, dtype=np.int32).reshape(-1, 2)
         rel = np.asarray(rel)
         if rel.ndim == 3:
@@ -197,7 +198,7 @@ class Network:
                 (max_ctas is None and not (int(layout) & 0xFFFF0000)):
             from .autotune import table_choice
             t_rows, t_ctas = table_choice(int(d), scope.shape[0] / max(1.0, n * (n - 1) / 2.0),
-                                          int(states or 1))
+                                          int(states or 1), kind="plan" if plan else "single")
             if rows is None and not (int(layout) & 0xF00):
                 rows = t_rows
             if max_ctas is None and not (int(layout) & 0xFFFF0000):

@@ -18,9 +18,10 @@ and grid cap on seeded synthetic networks of the bucket (120, 360 and 700
 variables at the bucket's middle d and density, tightness 0.3, assignment
 states; one launch per network -- rac_enforce for one state, rac_enforce_batch
 for more -- CUDA events, L2 flushed before each launch, median of `runs`),
-and writes the fastest pair per bucket to a JSON table.  Network() consults
-that table (tile_table.json next to this file) for what its caller leaves
-open.
+and, for networks enforced together, every row count of one multi-network
+plan launch of the three networks with 64 states each; it writes the
+fastest choice per bucket to a JSON table.  Network() consults that table
+(tile_table.json next to this file) for what its caller leaves open.
 """
 import argparse
 import json
@@ -33,6 +34,7 @@ D_BUCKETS = [(1, 8), (9, 16), (17, 24), (25, 32)]
 DENSITY_BUCKETS = [(0.0, 0.6), (0.6, 1.0)]
 STATE_BUCKETS = [(1, 1), (2, 16), (17, 1 << 30)]
 STATES_TIMED = {(1, 1): 1, (2, 16): 8, (17, 1 << 30): 32}
+PLAN_STATES = 64  # states per network in the multi-network plans timed
 CTA_CAPS = (None, 74, 37)  # every resident CTA (capped at the tile count), or fewer
 STAGE_BYTES = 32768  # relation bytes of one tile the kernels can stage
 
@@ -58,10 +60,13 @@ def load_table(path=TABLE):
     return _table
 
 
-def table_choice(d, density, states=1, path=TABLE):
+def table_choice(d, density, states=1, path=TABLE, kind="single"):
     """(rows, max_ctas) tuned for this shape; None for what the table does
-    not fix (the library default)."""
+    not fix (the library default).  kind: "single" for a network enforced in
+    launches of its own, "plan" for one enforced in multi-network plans."""
     for e in load_table(path).get("entries", []):
+        if e.get("kind", "single") != kind:
+            continue
         if not (e["d_lo"] <= d <= e["d_hi"] and e["dens_lo"] <= density <= e["dens_hi"]):
             continue
         if not e.get("st_lo", 1) <= states <= e.get("st_hi", 1 << 30):
@@ -71,9 +76,9 @@ def table_choice(d, density, states=1, path=TABLE):
     return None, None
 
 
-def table_rows(d, density, states=1, path=TABLE):
+def table_rows(d, density, states=1, path=TABLE, kind="single"):
     """The tuned tile rows for this shape, or None (library default)."""
-    return table_choice(d, density, states, path)[0]
+    return table_choice(d, density, states, path, kind)[0]
 
 
 def _bucket_networks(d_lo, d_hi, dens_lo, dens_hi, seed, states):
@@ -131,6 +136,44 @@ def time_choice(nets, rows, max_ctas, runs):
     return total
 
 
+def time_plan(nets, rows, runs):
+    """Median time (ms) of one multi-network plan launch of all states of all
+    networks with tiles of `rows` rows (the batched kernel)."""
+    import numpy as np
+    import torch
+    from . import Network, Plan
+    handles = [Network(x.n, x.d, x.scope, x.rel, rows=rows, max_ctas=65535) for x, _ in nets]
+    items, offs, flat, pos = [], [], [], 0
+    for i, (x, doms) in enumerate(nets):
+        for dom in doms:
+            items.append(i)
+            offs.append(pos)
+            flat.append(dom)
+            pos += x.n
+    flat = np.concatenate(flat).astype(np.uint32)
+    din = torch.from_numpy(flat.view(np.int32)).cuda()
+    dout = torch.empty_like(din)
+    it = torch.empty(len(items), dtype=torch.int32, device="cuda")
+    st = torch.empty_like(it)
+    plan = Plan(handles, np.array(items, np.int32), np.array(offs, np.int64))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
+    ts = []
+    for r in range(runs + 3):
+        flush.fill_(r)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.enforce(din, dout, it, st)
+        b.record()
+        torch.cuda.synchronize()
+        if r >= 3:
+            ts.append(a.elapsed_time(b))
+    plan.close()
+    for h in handles:
+        h.close()
+    return float(np.median(ts))
+
+
 def tune(runs=20, seed=7, out=TABLE, log=print):
     import torch
     entries = []
@@ -151,6 +194,20 @@ def tune(runs=20, seed=7, out=TABLE, log=print):
                                 "rows": best[0], "max_ctas": best[1],
                                 "ms": {"%d/%s" % (r, c if c is not None else "all"): round(t, 4)
                                        for (r, c), t in times.items()}})
+    # networks enforced together in multi-network plans (the batched kernel:
+    # its grid is every resident CTA, so only the tile rows are tuned)
+    for d_lo, d_hi in D_BUCKETS:
+        for dens_lo, dens_hi in DENSITY_BUCKETS:
+            d, dens, nets = _bucket_networks(d_lo, d_hi, dens_lo, dens_hi, seed, PLAN_STATES)
+            times = {r: time_plan(nets, r, runs) for r in admissible_rows(d)}
+            best = min(times, key=times.get)
+            log("plan, %d states each: d %2d-%2d density %.1f-%.1f: best rows %d (%.3f ms; "
+                "library default %.3f ms)" % (PLAN_STATES, d_lo, d_hi, dens_lo, dens_hi, best,
+                                              times[best], times[max(admissible_rows(d))]))
+            entries.append({"kind": "plan", "d_lo": d_lo, "d_hi": d_hi, "dens_lo": dens_lo,
+                            "dens_hi": dens_hi, "st_lo": 1, "st_hi": 1 << 30, "rows": best,
+                            "max_ctas": None,
+                            "ms": {str(r): round(t, 4) for r, t in times.items()}})
     table = {"version": 2, "device": torch.cuda.get_device_name(0),
              "states_timed": {"%d-%d" % k: v for k, v in STATES_TIMED.items()},
              "runs": runs, "seed": seed, "created": time.strftime("%Y-%m-%d %H:%M:%S"),

@@ -731,15 +731,16 @@ __device__ void produce_sweep(Smem &S, const LaunchParams &P, unsigned char *rin
                               int slot_r, int slot_c, int cta, int G, int my_slabs,
                               uint32_t &prod_it, int lane) {
   const NetDev &N = P.net;
-  if (cta == 0 && lane == 0) P.sync->bar[slot_c] = 0ull;  // last used two sweeps (or a launch) ago
+  if (cta == 0 && lane == 0) {  // last used two sweeps (or a launch) ago
+    P.sync->bar[slot_c] = 0ull;
+    P.sync->claim[slot_c] = 0u;
+  }
   // (learned gating: every slab while some state is in its full phase)
   const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2 && !(P.mlp && S.load_all);
   const uint32_t *cu = P.chgU + int64_t(slot_r) * N.nb;
   bool ok = true;  // lane 0's wait outcomes
-  // lane 0: the copy of this CTA's slab j into the next ring stage
-  auto issue = [&](int j) {
-    const int sl = cta + j * G;
-    const SlabDesc sd = j < kDescCache ? S.desc[j] : N.slabs[sl];
+  // lane 0: the copy of slab sl (descriptor sd) into the next ring stage
+  auto issue_sd = [&](int sl, const SlabDesc &sd) {
     const int stg = prod_it % kStages;
     const uint32_t par = (prod_it / kStages) & 1u;
     if (!mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err, P.wait_limit_ns)) return false;
@@ -753,16 +754,45 @@ __device__ void produce_sweep(Smem &S, const LaunchParams &P, unsigned char *rin
     ++prod_it;
     return true;
   };
+  // lane 0: this CTA's slab j (slab cta + j G)
+  auto issue = [&](int j) {
+    const int sl = cta + j * G;
+    return issue_sd(sl, j < kDescCache ? S.desc[j] : N.slabs[sl]);
+  };
+  // a plain sweep of the ungated variants claims the slabs beyond each
+  // CTA's first kStaticSlabs dynamically (the gated variants and the seeded
+  // first sweep keep the static split: pending flags and the seed filter are
+  // per owner)
+  const bool dyn = kGate == 0 && !(k == 1 && P.seed_var >= 0);
   if (!incr) {
     if (lane != 0) return;
+    const int n_static = dyn ? (my_slabs < kStaticSlabs ? my_slabs : kStaticSlabs) : my_slabs;
     // in sweep 1 the first slab may already be on its way
-    for (int j = (k == 1 && prod_it == 1) ? 1 : 0; j < my_slabs; ++j) {
+    for (int j = (k == 1 && prod_it == 1) ? 1 : 0; j < n_static; ++j) {
       if (k == 1 && P.seed_var >= 0) {
         const SlabDesc sd = j < kDescCache ? S.desc[j] : N.slabs[cta + j * G];
         if (!slab_touches_seed(P, sd.ij & 0xFFFFu, sd.ij >> 16, sd.rows & 0xFFu, sd.rows >> 8))
           continue;  // sweep 1 of an assignment: only constraints on the assigned variable
       }
       if (!(ok = issue(j))) break;
+    }
+    if (dyn && ok && int64_t(kStaticSlabs) * G < int64_t(N.n_slabs)) {
+      // slabs [kStaticSlabs G, n_slabs), kClaimBatch at a time; the next
+      // batch is claimed before this one's copies wait for free stages
+      uint32_t *ctr = &P.sync->claim[(slot_r + 1) % 3];  // this sweep's slot
+      const int first_dyn = kStaticSlabs * G;
+      int lo = first_dyn + int(atomicAdd(ctr, uint32_t(kClaimBatch)));
+      while (ok && lo < N.n_slabs) {
+        SlabDesc sd[kClaimBatch];
+#pragma unroll
+        for (int i = 0; i < kClaimBatch; ++i)
+          if (lo + i < N.n_slabs) sd[i] = N.slabs[lo + i];
+        const int next = first_dyn + int(atomicAdd(ctr, uint32_t(kClaimBatch)));
+#pragma unroll
+        for (int i = 0; i < kClaimBatch; ++i)
+          if (ok && lo + i < N.n_slabs) ok = issue_sd(lo + i, sd[i]);
+        lo = next;
+      }
     }
   } else {
     for (int j0 = 0; j0 < my_slabs; j0 += 32) {

@@ -54,6 +54,12 @@ constexpr int kStageBytes = kSlabRelBytes + 256;     // + header (at most 32 row
 // next round's phase parity while the current round is still filling, and a
 // parity test cannot tell those two phases apart.
 constexpr int kStages = 6;
+// A plain sweep streams each CTA's first kStaticSlabs slabs (cta, cta + G,
+// ...) from its own descriptor list, then claims the rest from a grid-wide
+// counter in batches of kClaimBatch, so that CTAs whose slabs are quicker
+// take more and the sweep's last CTA ends about one batch after the others.
+constexpr int kStaticSlabs = kStages;
+constexpr int kClaimBatch = 2;
 constexpr int kMaxStatesPerLaunch = 1024;
 constexpr int kDescCache = 200;   // slab descriptors a CTA keeps in shared memory
 constexpr int kDomWords = 5040;   // domain words a CTA keeps in shared memory per sweep
@@ -84,6 +90,9 @@ struct Sync {
   // completed on the workspace (the last CTA publishes it to the host)
   uint32_t done_cta;
   uint32_t done_seq;
+  // dynamic slab claims of a plain sweep (slot as bar): slabs beyond the
+  // first kStaticSlabs per CTA go to whichever producer asks first
+  uint32_t claim[3];
 };
 constexpr int kBarCountBits = 16;  // grids of at most 65535 CTAs
 

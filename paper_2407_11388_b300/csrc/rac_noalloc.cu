@@ -44,6 +44,7 @@ constexpr int kScratchWords = kBufOffset + kNoallocMaxVars;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kScratchWords];
 static_assert(sizeof(g_noalloc_scratch) == 311808, "the documented size of the scratch array");
+static_assert(sizeof(Sync) <= kSyncWords * sizeof(uint32_t), "the sync words fit their slot");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;

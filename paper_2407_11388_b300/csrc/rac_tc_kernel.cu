@@ -421,7 +421,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
       const int slot_c = int((base + k + 1) % 3);
       if (is_producer) {
         if (lane == 0) {
-          if (cta == 0) P.sync->bar[slot_c] = 0ull;
+          if (cta == 0) {  // the slot of the next sweep (the bit-packed kernel's claims too)
+            P.sync->bar[slot_c] = 0ull;
+            P.sync->claim[slot_c] = 0u;
+          }
           const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
           const uint32_t *cu = P.chgU + int64_t(slot_r) * N.nb;
           bool ok = true;

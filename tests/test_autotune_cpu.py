@@ -36,3 +36,14 @@ def test_older_table_and_rows_that_do_not_fit(tmp_path):
     assert autotune.table_choice(8, 0.5, 64, path) == (32, None)
     assert autotune.admissible_rows(32) == [2, 4, 8]
     assert autotune.admissible_rows(8) == [2, 4, 8, 16, 32]
+
+
+def test_plan_entries_are_looked_up_apart(tmp_path):
+    path = _write(tmp_path, [
+        {"kind": "plan", "d_lo": 1, "d_hi": 8, "dens_lo": 0.0, "dens_hi": 1.0, "rows": 32},
+        {"d_lo": 1, "d_hi": 8, "dens_lo": 0.0, "dens_hi": 1.0, "st_lo": 2, "st_hi": 1 << 30,
+         "rows": 8, "max_ctas": None},
+    ])
+    assert autotune.table_choice(6, 0.5, 64, path, kind="plan") == (32, None)
+    assert autotune.table_choice(6, 0.5, 64, path) == (8, None)
+    assert autotune.table_choice(6, 0.5, 1, path) == (None, None)
