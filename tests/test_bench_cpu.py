@@ -35,9 +35,9 @@ def test_comment_edits_keep_the_hash(monkeypatch, tmp_path):
 def test_traffic_needs_the_recorded_hash(monkeypatch):
     data = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     ent = data["dense_n500_d20"]
-    monkeypatch.setattr(bench, "source_hash", lambda: ent["source_hash"])
+    monkeypatch.setattr(bench, "source_hash", lambda kernel=None: ent["source_hash"])
     assert bench.traffic_from_profiles("dense_n500_d20") == ent["dram_bytes_per_launch"]
-    monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)
+    monkeypatch.setattr(bench, "source_hash", lambda kernel=None: "0" * 16)
     assert bench.traffic_from_profiles("dense_n500_d20") is None
     assert bench.traffic_from_profiles("no_such_workload") is None
 
