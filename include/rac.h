@@ -285,12 +285,12 @@ RAC_API void rac_plan_destroy(rac_plan *plan);
  * or the tensor-core kernel) the copy out form a CUDA graph, recorded on the
  * first call with a given (n_states, max_sweeps, flags) and replayed by later
  * calls with the same ones.  A call of one bit-packed launch has the kernel
- * write its results straight into the pinned buffer, and its last CTA then
- * writes a completion number there: the call waits for that number instead
- * of synchronising `stream` (the kernel's exit may still be in flight when it
- * returns; later work on `stream` is ordered after it), and synchronises
- * `stream` only if the number does not come within the wait limit.  Other
- * calls synchronise `stream`.  Calls on the same (network, stream) must not
+ * write its results straight into the pinned buffer; with at most three
+ * states its last CTA then writes a completion number there, and the call
+ * waits for that number instead of synchronising `stream` (the kernel's exit
+ * may still be in flight when it returns; later work on `stream` is ordered
+ * after it), synchronising `stream` only if the number does not come within
+ * the wait limit.  Other calls synchronise `stream`.  Calls on the same (network, stream) must not
  * overlap.
  * Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA.
  */

@@ -702,7 +702,7 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
       P.iterations = d_res;
       P.status = d_res + n_states;
       P.host_out = w0->host_pin_dev + words;
-      P.host_done = w0->host_pin_dev + (total - 1);
+      if (n_states < 4) P.host_done = w0->host_pin_dev + (total - 1);
       return launch_for(P, flags, q);
     }
     // the launches (state chunks), one copy out
@@ -769,7 +769,8 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
   // later work on `stream` is ordered after it.  A word that does not come
   // within the time limit (the launch failed) falls back to synchronising.
   bool seen = false;
-  if (direct && rc == RAC_OK) {
+  const bool done_word = direct && n_states < 4;  // the launches that publish one
+  if (done_word && rc == RAC_OK) {
     const volatile uint32_t *done = w0->host_pin + (total - 1);
     const uint32_t want = w0->host_seq + 1u;
     const auto t0 = std::chrono::steady_clock::now();
@@ -787,7 +788,8 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
     const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess && rc == RAC_OK) rc = cuda_fail(e, "cudaStreamSynchronize");
   }
-  if (direct) w0->host_seq = *reinterpret_cast<volatile uint32_t *>(w0->host_pin + (total - 1));
+  if (done_word)
+    w0->host_seq = *reinterpret_cast<volatile uint32_t *>(w0->host_pin + (total - 1));
   if (rc == RAC_OK) {
     std::memcpy(dom_out, pin_res, words * 4);
     std::memcpy(iterations, pin_res + words, size_t(n_states) * 4);

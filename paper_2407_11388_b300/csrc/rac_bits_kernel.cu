@@ -726,7 +726,7 @@ __device__ __forceinline__ bool slab_streamed(const LaunchParams &P, const SlabD
 // lane 0 alone.  kGate: the learned variants, where the producer also
 // arrives on the stage's `issued` barrier once the slab is set (the stage's
 // scorer warp gives the full barrier's second arrival).
-template <int kGate>
+template <int kGate, bool kDyn>
 __device__ void produce_sweep(Smem &S, const LaunchParams &P, unsigned char *ring, int k,
                               int slot_r, int slot_c, int cta, int G, int my_slabs,
                               uint32_t &prod_it, int lane) {
@@ -759,11 +759,15 @@ __device__ void produce_sweep(Smem &S, const LaunchParams &P, unsigned char *rin
     const int sl = cta + j * G;
     return issue_sd(sl, j < kDescCache ? S.desc[j] : N.slabs[sl]);
   };
-  // a plain sweep of the ungated variants claims the slabs beyond each
-  // CTA's first kStaticSlabs dynamically (the gated variants and the seeded
-  // first sweep keep the static split: pending flags and the seed filter are
-  // per owner)
-  const bool dyn = kGate == 0 && !(k == 1 && P.seed_var >= 0);
+  // a plain sweep of the one-to-three-state variant claims the slabs beyond
+  // each CTA's first kStaticSlabs dynamically.  The gated variants and the
+  // seeded first sweep keep the static split (pending flags and the seed
+  // filter are per owner), and so does the many-state variant: there the
+  // two slabs of a claimed batch (neighbours in one tile, the same column
+  // block) sent their removals and change marks to the same words from two
+  // consumer groups at once, and the launch got slower (595 -> 674 us for
+  // n=1000, d=24 with 32 states)
+  const bool dyn = kDyn && kGate == 0 && !(k == 1 && P.seed_var >= 0);
   if (!incr) {
     if (lane != 0) return;
     const int n_static = dyn ? (my_slabs < kStaticSlabs ? my_slabs : kStaticSlabs) : my_slabs;
@@ -967,8 +971,11 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
 // gating and/or trace records) whose producer warp scores up to 16 or up to
 // 32 states at a time (one or two MMA M tiles).  Separate kernels keep each
 // one's instruction footprint small: a launch after an L2 flush fetches its
-// code from HBM.
-template <int Q, int kVar>
+// code from HBM.  kDone: the instance the host entry point launches, which
+// publishes a completion number to host memory at its end (P.host_done); a
+// separate instance keeps that code out of every other launch, where it had
+// cost 1-5% of the time.
+template <int Q, int kVar, bool kDone>
 __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const LaunchParams P) {
   constexpr int kGate = kVar >= kVarGated1 ? 1 : 0;
   constexpr int kGW = group_warps(kVar), kCW = consumer_warps(kVar);
@@ -1088,7 +1095,8 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
           score_sweep<kVar - kVarGated1 + 1>(S, P, k, slot_r, warp - kCW - 1, sc_it,
                                              lane);
       } else if (is_producer) {
-        produce_sweep<kGate>(S, P, ring, k, slot_r, slot_c, cta, G, my_slabs, prod_it, lane);
+        produce_sweep<kGate, kVar == kVarFew>(S, P, ring, k, slot_r, slot_c, cta, G, my_slabs,
+                                              prod_it, lane);
       } else {
         const int64_t stride = P.flag_stride;
         // this sweep's domains D_{k-1} into shared memory
@@ -1293,7 +1301,7 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
       }
     }
   }
-  if (P.host_done) {
+  if constexpr (kDone) {
     // the last CTA to finish its host writes publishes the completion
     // number: the caller reads the results once it sees it
     __syncthreads();
@@ -1318,12 +1326,13 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
   }
 }
 
-template <int Q, int kVar>
+template <int Q, int kVar, bool kDone>
 rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
   static LaunchCache cache;
   const size_t smem = size_t(kStages) * kStageBytes + sizeof(Smem);
   int per_sm = 0, sms = 0;
-  rac_status rc = persistent_shape(cache, reinterpret_cast<const void *>(rac_bits_kernel<Q, kVar>),
+  rac_status rc = persistent_shape(cache,
+                                   reinterpret_cast<const void *>(rac_bits_kernel<Q, kVar, kDone>),
                                    threads_for(kVar), smem, "bit-packed kernel set-up", &per_sm,
                                    &sms);
   if (rc != RAC_OK) return rc;
@@ -1343,22 +1352,22 @@ rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, rac_bits_kernel<Q, kVar>, P);
+  e = cudaLaunchKernelEx(&cfg, rac_bits_kernel<Q, kVar, kDone>, P);
   if (e != cudaSuccess) return cuda_fail(e, "launch of the bit-packed kernel");
   return RAC_OK;
 }
 
-template <int kVar>
+template <int kVar, bool kDone>
 rac_status launch_width(const LaunchParams &P, cudaStream_t stream) {
   switch (P.net.q) {
-    case 1: return launch_q<1, kVar>(P, stream);
-    case 2: return launch_q<2, kVar>(P, stream);
-    case 3: return launch_q<3, kVar>(P, stream);
-    case 4: return launch_q<4, kVar>(P, stream);
-    case 5: return launch_q<5, kVar>(P, stream);
-    case 6: return launch_q<6, kVar>(P, stream);
-    case 7: return launch_q<7, kVar>(P, stream);
-    case 8: return launch_q<8, kVar>(P, stream);
+    case 1: return launch_q<1, kVar, kDone>(P, stream);
+    case 2: return launch_q<2, kVar, kDone>(P, stream);
+    case 3: return launch_q<3, kVar, kDone>(P, stream);
+    case 4: return launch_q<4, kVar, kDone>(P, stream);
+    case 5: return launch_q<5, kVar, kDone>(P, stream);
+    case 6: return launch_q<6, kVar, kDone>(P, stream);
+    case 7: return launch_q<7, kVar, kDone>(P, stream);
+    case 8: return launch_q<8, kVar, kDone>(P, stream);
     default: set_error("unsupported relation width"); return RAC_EINVAL;
   }
 }
@@ -1367,12 +1376,19 @@ rac_status launch_width(const LaunchParams &P, cudaStream_t stream) {
 
 rac_status launch_bits(const LaunchParams &P, cudaStream_t stream) {
   const bool gate = P.mlp != nullptr || P.tr_count != nullptr || P.tr_evals != nullptr;
-  if (!gate) return P.n_states < 4 ? launch_width<kVarFew>(P, stream)
-                                   : launch_width<kVarMany>(P, stream);
+  if (P.host_done) {  // the host entry point's one-to-three-state launch
+    if (gate || P.n_states >= 4) {
+      set_error("a completion word is published by the one-to-three-state launch only");
+      return RAC_EINVAL;
+    }
+    return launch_width<kVarFew, true>(P, stream);
+  }
+  if (!gate) return P.n_states < 4 ? launch_width<kVarFew, false>(P, stream)
+                                   : launch_width<kVarMany, false>(P, stream);
   // the producer warp scores 32 states at a time (lane = state): one MMA M
   // tile covers them while there are at most 16
-  return P.n_states <= 16 ? launch_width<kVarGated1>(P, stream)
-                          : launch_width<kVarGated2>(P, stream);
+  return P.n_states <= 16 ? launch_width<kVarGated1, false>(P, stream)
+                          : launch_width<kVarGated2, false>(P, stream);
 }
 
 }  // namespace rac
