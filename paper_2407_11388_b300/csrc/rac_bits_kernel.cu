@@ -10,7 +10,9 @@
 // iff it keeps a support on every constraint of C_x (Algorithm 1
 // `tensorRevise`: the sum over the constraints must equal their number).
 //
-// Mapping: a CTA owns every G-th relation slab.  A producer warp streams
+// Mapping: a CTA owns every G-th relation slab (in a plain sweep of one to
+// three states only its first kStaticSlabs of them; the rest go to whichever
+// CTA claims them first from a grid-wide counter).  A producer warp streams
 // slabs into a shared-memory ring with bulk copies (cp.async.bulk, completion
 // on mbarriers); three consumer groups of four warps (five in the many-state
 // variant) take alternate stages.  A lane holds one relation (the pair (x,
