@@ -71,6 +71,14 @@ typedef int32_t rac_status;
 
 /* layout_flags of rac_create_network */
 #define RAC_LAYOUT_BITS 0x1u /* bit-packed relation slabs (always built) */
+/* The tensor-core kernel's operand store (RAC_KERNEL_TENSOR), built on the
+ * device at creation: every relation expanded to E4M3 0/1 bytes (1.0 = 0x38)
+ * in the MMA's shared-memory tile layout, 8 KiB per MMA job (a slab's forward
+ * jobs: 8 relations of one column, a row each of their 32 values; its
+ * reverse jobs: 8 relations of one row, transposed), about 64 x 8 KiB per 8
+ * slab rows (1.1 GB for n = 1000).  Without it the first RAC_KERNEL_TENSOR
+ * call on the network builds it (an allocation and a wait on its stream). */
+#define RAC_LAYOUT_FP8 0x2u
 /* Rows of the relation tiles ("slabs": 32 column variables x `rows` row
  * variables of one block pair, read as one unit): RAC_LAYOUT_ROWS(l) asks
  * for 2^l rows, 1 <= l <= 5 (a tile's header of 2 x rows words keeps the

@@ -72,6 +72,8 @@ NetDev net_dev(const rac_network *net) {
   N.rows_per_slab = net->rows_per_slab;
   N.n_slabs = int32_t(net->n_slabs);
   N.max_ctas = net->max_ctas;
+  N.fp8 = net->d_fp8;
+  N.fp8_jobs = net->fp8_jobs;
   N.rel = static_cast<const uint4 *>(net->d_rel);
   N.slabs = net->d_slabs;
   N.slab_feat = net->d_slab_feat;
@@ -199,6 +201,12 @@ rac_status launch_for(const LaunchParams &P, uint32_t flags, cudaStream_t s) {
   return (flags & RAC_KERNEL_TENSOR) ? launch_tc(P, s) : launch_bits(P, s);
 }
 
+// The tensor-core kernel reads the network's FP8 operand store: build it
+// (once) before the launch parameters are taken from the network.
+rac_status prepare_for(const rac_network *net, uint32_t flags, cudaStream_t s) {
+  return (flags & RAC_KERNEL_TENSOR) ? ensure_fp8(net, s) : RAC_OK;
+}
+
 // Largest power of two rows (<= 32) whose slab fits one ring stage.
 int rows_per_slab_for(int dp) {
   int rows = 32;
@@ -240,7 +248,8 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
     set_error("more constraints than pairs of variables (each pair takes at most one)");
     return RAC_EINVAL;
   }
-  if (layout_flags & ~(RAC_LAYOUT_BITS | RAC_LAYOUT_ROWS_MASK | RAC_LAYOUT_MAX_CTAS_MASK)) {
+  if (layout_flags &
+      ~(RAC_LAYOUT_BITS | RAC_LAYOUT_FP8 | RAC_LAYOUT_ROWS_MASK | RAC_LAYOUT_MAX_CTAS_MASK)) {
     set_error("unknown layout flag");
     return RAC_EINVAL;
   }
@@ -390,6 +399,7 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
   net->nb = nb;
   net->rows_per_slab = rows;
   net->max_ctas = int32_t(layout_flags >> 16);
+  net->fp8_jobs = fp8_jobs_for(rows);
   net->m = n_cons;
   net->n_slabs = int64_t(slabs.size());
   net->first.assign(slabs.begin(), slabs.begin() + std::min<size_t>(slabs.size(), kMaxFirst));
@@ -416,6 +426,15 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
   if ((e = upload(reinterpret_cast<void **>(&net->d_slab_feat), slab_feat.data(),
                   slab_feat.size() * sizeof(float2))) != cudaSuccess)
     return fail(e, "upload of the slab features");
+  if (layout_flags & RAC_LAYOUT_FP8) {
+    const rac_status rc = ensure_fp8(net, nullptr);
+    if (rc != RAC_OK) {
+      const std::string msg = rac_last_error();
+      rac_destroy(net);
+      set_error(msg);
+      return rc;
+    }
+  }
   *out = net;
   return RAC_OK;
 } RAC_CATCH_STATUS
@@ -470,6 +489,7 @@ void rac_destroy(rac_network *net) try {
   if (!net) return;
   for (auto &kv : net->ws) free_workspace(kv.second);
   net->ws.clear();
+  cudaFree(net->d_fp8);
   cudaFree(net->d_rel);
   cudaFree(net->d_slabs);
   cudaFree(net->d_slab_feat);
@@ -499,7 +519,8 @@ rac_status rac_enforce(const rac_network *net, const uint32_t *dom_in, uint32_t 
   }
   if (!check_device(net)) return RAC_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  rac_status rc = RAC_OK;
+  rac_status rc = prepare_for(net, flags, s);
+  if (rc != RAC_OK) return rc;
   Workspace *w = get_workspace(net, s, 1, 0, &rc);
   if (!w) return rc;
   LaunchParams P = base_params(net, w, 1, max_sweeps, flags);
@@ -597,6 +618,10 @@ rac_status rac_enforce_batch(const rac_network *const *nets, int32_t n_nets, int
   std::vector<int32_t> idx;
   for (int32_t k = 0; k < n_nets; ++k) {
     const std::vector<int32_t> &g = groups[size_t(k)];
+    if (!g.empty()) {
+      const rac_status rc = prepare_for(nets[k], flags, s);
+      if (rc != RAC_OK) return rc;
+    }
     for (size_t base = 0; base < g.size(); base += chunk) {
       const int cnt = int(std::min<size_t>(chunk, g.size() - base));
       rac_status rc = RAC_OK;
@@ -653,7 +678,8 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
   const bool direct = !(flags & RAC_KERNEL_TENSOR) && n_states <= kMaxStatesPerLaunch;
   // pinned staging: [input words][result words][iterations][status][completion word]
   const size_t total = 2 * words + 2 * size_t(n_states) + 1;
-  rac_status rc = RAC_OK;
+  rac_status rc = prepare_for(net, flags, s);
+  if (rc != RAC_OK) return rc;
   Workspace *w0 = get_workspace(net, s, std::min<int32_t>(n_states, kMaxStatesPerLaunch), 0, &rc);
   if (!w0) return rc;
   if (w0->host_cap < total) {

@@ -67,6 +67,10 @@ constexpr int kDomWords = 5040;   // domain words a CTA keeps in shared memory p
 struct NetDev {
   int32_t n, d, dp, q, nb, rows_per_slab, n_slabs;
   int32_t max_ctas;  // > 0: grid cap of the network's launches (RAC_LAYOUT_MAX_CTAS)
+  // FP8 operand store of the tensor-core kernel (RAC_LAYOUT_FP8; null until
+  // built): fp8_jobs MMA operand tiles of kFp8TileBytes per slab, slab-major
+  const uint8_t *fp8;
+  int32_t fp8_jobs;
   const uint4 *rel;
   const SlabDesc *slabs;
   const float2 *slab_feat;  // per slab: (tightness, density), the predictor's f3 and f4
@@ -253,6 +257,11 @@ struct Workspace {
 struct rac_network {
   int32_t n = 0, d = 0, dp = 0, q = 0, nb = 0, rows_per_slab = 0;
   int32_t max_ctas = 0;  // RAC_LAYOUT_MAX_CTAS, 0: none
+  // the tensor-core kernel's FP8 operand store (RAC_LAYOUT_FP8, or built by
+  // the first RAC_KERNEL_TENSOR call under mu)
+  mutable uint8_t *d_fp8 = nullptr;
+  mutable size_t fp8_bytes = 0;
+  int32_t fp8_jobs = 0;
   int64_t m = 0;
   int64_t n_slabs = 0;
   size_t rel_bytes = 0;
@@ -261,7 +270,7 @@ struct rac_network {
   rac::SlabDesc *d_slabs = nullptr;
   float2 *d_slab_feat = nullptr;      // per slab: tightness, density
   std::vector<rac::SlabDesc> first;  // host copy of the first kMaxFirst descriptors
-  std::mutex mu;
+  mutable std::mutex mu;
   std::unordered_map<cudaStream_t, rac::Workspace *> ws;
 };
 
@@ -283,9 +292,18 @@ rac_status cuda_fail(cudaError_t e, const char *what);
 NetDev net_dev(const rac_network *net);
 // Launch the bit-packed kernel for P (grid sized by the callee).
 rac_status launch_bits(const LaunchParams &P, cudaStream_t stream);
-// Launch the tensor-core kernel for P (at most 128 states).
+// Launch the tensor-core kernel for P (at most 128 states; P.net.fp8 set).
 rac_status launch_tc(const LaunchParams &P, cudaStream_t stream);
 constexpr int kTensorMaxStates = 128;
+// The tensor-core kernel's operand tiles: 256 rows (8 relations x 32 values)
+// of 32 one-byte E4M3 entries (K = 32 values), 8 KiB each.
+constexpr int kFp8TileBytes = 8192;
+// MMA jobs of a slab of `rows` rows: a forward job per (8-row group, column),
+// a reverse job per (row, 8-column group).
+inline int fp8_jobs_for(int rows) { return 32 * ((rows + 7) / 8) + 4 * rows; }
+// Builds net's FP8 operand store if it has none yet (thread-safe; the first
+// call allocates and expands the bit-packed store on `stream` and waits).
+rac_status ensure_fp8(const rac_network *net, cudaStream_t stream);
 const uint4 *predictor_pack(const rac_predictor *p);  // fragment-packed weights
 int predictor_device(const rac_predictor *p);
 Workspace *get_workspace(const rac_network *net, cudaStream_t stream, int n_states, int n_items,

@@ -6,9 +6,9 @@
 // For every relation R_xy of a slab and every state s the counts are
 //   forward  Sup_xy[a](s) = sum_b R[a][b] D_s[y][b]     (Fig. 1)
 //   reverse  Sup_yx[b](s) = sum_a R[a][b] D_s[x][a]
-// computed as GEMMs with M = 128 states, K = 32 values and N = 256 =
-// 8 relations x 32 rows: a forward MMA per (column y, group of 8 rows) takes
-// D_s[y] as A and the 8 relations R_{x,y} as B; a reverse MMA per (row x,
+// computed as MMAs with M = 128 states, K = 32 values and N = 256 = 8
+// relations x 32 rows: a forward job per (group of 8 rows, column y) takes
+// D_s[y] as A and the 8 relations R_{x,y} as B; a reverse job per (row x,
 // group of 8 columns) takes D_s[x] as A and the 8 transposed relations as B.
 // Counts are exact in FP32 (at most 32).  The epilogue reads the accumulator
 // lanes (one state per lane), clamps every count to {0,1} (only Sup > 0
@@ -16,12 +16,29 @@
 // into one word and ANDs it over the row's or column's constraints; the
 // removals then follow kernel (a) (atomicAnd into the next domain buffer).
 //
-// Operand tiles are built in shared memory from the bit-packed slab (the
-// reverse direction transposes each relation with 32 warp ballots) in the
-// canonical K-major layout without swizzle (8-row x 16-byte core matrices,
-// 128 B apart along K, 256 B apart along M/N).  Operand buffers and
-// accumulators are double-buffered: while MMA i runs, the warps build the
-// operands of MMA i+1 and run the epilogue of MMA i-1.
+// The B operands are the network's FP8 operand store (RAC_LAYOUT_FP8: every
+// job's tile expanded once, on the device, in the MMA's shared-memory layout),
+// brought in by bulk copies.  A slab's jobs run through a pipeline of warps
+// that wait on mbarriers only (no CTA-wide barrier per MMA):
+//   warps 0-7    epilogue: TMEM lane quarter warp % 4 (32 states), half of
+//                each job's 8 relations (warp / 4); they keep a slab's AND
+//                masks in registers and make its removals;
+//   warps 8-11   A tiles: the states' domain word of the job's column (or
+//                row) expanded to E4M3 bytes, 32 states each;
+//   warp 12      B tiles: one bulk copy of 8 KiB per job;
+//   warp 13      MMA issuer: waits for the job's A and B tiles and a free
+//                accumulator, issues the MMA, and commits its completion to
+//                the A and B stages it frees and to the accumulator's full
+//                barrier;
+//   warp 14      helps stage the slab's domain words;
+//   warp 15      streams the bit-packed slabs (their headers name the
+//                relations present) into a small ring, as in kernel (a).
+// Operand rings of four stages and two accumulators of 256 columns keep the
+// roles apart by up to four jobs.
+#include <algorithm>
+#include <mutex>
+#include <string>
+
 #include "rac_device.cuh"
 #include "rac_internal.h"
 
@@ -30,15 +47,22 @@ namespace {
 
 using namespace dev;
 
-constexpr int kTcConsumerWarps = 12;  // 3 per TMEM lane quarter
+// warp roles (see the file comment)
+constexpr int kTcEpiWarps = 8;
+constexpr int kTcAWarp0 = 8, kTcAWarps = 4;
+constexpr int kTcBWarp = 12;
+constexpr int kTcMmaWarp = 13;
+constexpr int kTcConsumerWarps = 15;  // warps 0-14; warp 15 streams the bit-packed slabs
 constexpr int kTcThreads = (kTcConsumerWarps + 1) * 32;
-constexpr int kTcStages = 4;
-constexpr int kTcMaxStates = 128;     // M of the MMA
-constexpr int kTcN = 256;             // N of the MMA: 8 relations x 32 rows
-constexpr uint32_t kTmemCols = 512;   // two accumulators of 256 columns
+constexpr int kTcStages = 3;    // bit-packed slab ring
+constexpr int kTcOpStages = 4;  // A and B operand rings
+constexpr int kTcMaxStates = 128;  // M of the MMA
+constexpr int kTcN = 256;          // N of the MMA: 8 relations x 32 rows
+constexpr uint32_t kTmemCols = 512;  // two accumulators of 256 columns
 constexpr int kATileBytes = kTcMaxStates * 32;  // 4 KB
-constexpr int kBTileBytes = kTcN * 32;          // 8 KB
-constexpr int kTcDomWords = 64;                 // per state: 32 columns + up to 32 rows
+constexpr int kBTileBytes = kFp8TileBytes;      // 8 KB
+static_assert(kBTileBytes == kTcN * 32, "a B tile is N rows of 32 bytes");
+constexpr int kTcDomWords = 64;  // per state: 32 columns + up to 32 rows
 
 struct TcStage {
   int32_t sl;
@@ -46,15 +70,18 @@ struct TcStage {
 };
 
 struct TcSmem {
-  uint8_t a_tile[2][kATileBytes];
-  uint8_t b_tile[2][kBTileBytes];
+  uint8_t a_tile[kTcOpStages][kATileBytes];
+  uint8_t b_tile[kTcOpStages][kBTileBytes];
   uint32_t dom[kTcMaxStates][kTcDomWords];  // staged D_{k-1} words of the slab
   uint64_t full[kTcStages];
   uint64_t empty[kTcStages];
-  uint64_t mma_done[2];
+  uint64_t a_full[kTcOpStages], a_empty[kTcOpStages];
+  uint64_t b_full[kTcOpStages], b_empty[kTcOpStages];
+  uint64_t acc_full[2], acc_empty[2];
   TcStage stage[kTcStages];
   uint32_t stage_ok[kTcStages];
   uint32_t tmem_base;
+  uint32_t mma_issued, b_issued;
   uint32_t base, poisoned, abort, failed, all_done;
   uint32_t any_total, wipe_total, cta_any, cta_wipe;
   uint32_t st_info[kTcMaxStates];
@@ -62,6 +89,7 @@ struct TcSmem {
 };
 static_assert(size_t(kTcStages) * kStageBytes + sizeof(TcSmem) + 1024 <= 232448,
               "shared memory of the tensor-core kernel exceeds 227 KB");
+static_assert((size_t(kTcStages) * kStageBytes) % 128 == 0, "operand tiles 128-byte aligned");
 
 constexpr uint32_t kInfoSweepMask = 0xFFFFFFu;
 constexpr uint32_t kInfoResB = 1u << 24;
@@ -129,13 +157,6 @@ __device__ __forceinline__ uint32_t tile_off(uint32_t row, uint32_t k) {
 __device__ __forceinline__ uint32_t expand4(uint32_t nib) {
   return ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
 }
-// Row word w (bit k = 1) -> the 32 bytes of one tile row.
-__device__ __forceinline__ void put_row(uint8_t *tile, uint32_t row, uint32_t w) {
-#pragma unroll
-  for (int q = 0; q < 8; ++q)
-    *reinterpret_cast<uint32_t *>(tile + tile_off(row, 4u * q)) = expand4((w >> (4 * q)) & 0xFu);
-}
-
 struct TcView {
   const uint32_t *C;
   uint32_t *T;
@@ -182,21 +203,88 @@ __device__ __forceinline__ uint32_t rel_row(const uint32_t *hdr, const uint32_t 
   return relw[(base_chunk + uint32_t(a >> 2) * cnt + t) * 4u + uint32_t(a & 3)];
 }
 
-// The whole slab for every running state: 2 * ceil(nrows/8) * 32 MMAs.
+// The FP8 operand store: word w of tile (slab sl, job idx), job order as in
+// tc_consume (forward jobs g * 32 + j, then reverse jobs 32 rg + g nrows + r).
+__global__ void __launch_bounds__(256) rac_fp8_build_kernel(const NetDev N, uint8_t *out) {
+  const int64_t total = int64_t(N.n_slabs) * N.fp8_jobs * (kFp8TileBytes / 4);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const int64_t t = i / (kFp8TileBytes / 4);
+    const int w = int(i % (kFp8TileBytes / 4));
+    const int sl = int(t / N.fp8_jobs), idx = int(t % N.fp8_jobs);
+    const SlabDesc sd = N.slabs[sl];
+    const uint32_t *hdr = reinterpret_cast<const uint32_t *>(N.rel + sd.rel_off16);
+    const uint32_t nrows = sd.rows >> 8;
+    const uint32_t *relw = hdr + 2 * nrows;
+    const int rg = int(nrows + 7) / 8;
+    const int row = w >> 3, qq = w & 7;
+    uint32_t nib = 0u;
+    if (idx < 32 * rg) {  // forward: rows (r, a) of R_{x_r, y_j}, K = b
+      const int j = idx & 31, g = idx >> 5;
+      const int r = 8 * g + (row >> 5), a = row & 31;
+      if (r < int(nrows) && ((hdr[r] >> j) & 1u)) {
+        const uint32_t t_rank = __popc(hdr[r] & ((1u << j) - 1u));
+        nib = (rel_row(hdr, relw, nrows, N.q, r, t_rank, a) >> (4 * qq)) & 0xFu;
+      }
+    } else {  // reverse: rows (j, b) of R_{x_r, y_j} transposed, K = a
+      const int ridx = idx - 32 * rg;
+      const int r = ridx % int(nrows), g = ridx / int(nrows);
+      const int j = 8 * g + (row >> 5), b = row & 31;
+      if ((hdr[r] >> j) & 1u) {
+        const uint32_t t_rank = __popc(hdr[r] & ((1u << j) - 1u));
+#pragma unroll
+        for (int i2 = 0; i2 < 4; ++i2)
+          nib |= ((rel_row(hdr, relw, nrows, N.q, r, t_rank, 4 * qq + i2) >> b) & 1u) << i2;
+      }
+    }
+    *reinterpret_cast<uint32_t *>(out + t * kFp8TileBytes + tile_off(uint32_t(row), 4u * qq)) =
+        expand4(nib);
+  }
+}
+
+// The CTA's abort flag, set by any role whose wait ran out (read through
+// volatile: another warp may set it while this one loops).
+__device__ __forceinline__ bool aborted(const TcSmem &S) {
+  return *reinterpret_cast<const volatile uint32_t *>(&S.abort) != 0u;
+}
+
+// One lane waits (bounded) on an mbarrier phase for its warp; the warp
+// follows the outcome.  A wait that runs out aborts the CTA's launch.
+__device__ __forceinline__ bool warp_wait(TcSmem &S, const LaunchParams &P, uint64_t *bar,
+                                          uint32_t parity, int lane) {
+  uint32_t ok = 1u;
+  if (lane == 0) {
+    if (aborted(S) || !mbar_wait(bar, parity, &P.sync->err, P.wait_limit_ns)) {
+      ok = 0u;
+      S.abort = 1u;
+    }
+  }
+  return __shfl_sync(kFull, ok, 0) != 0u;
+}
+
+// Packs the 32 counts of one relation row (one state per lane) into a word:
+// bit a set iff count a > 0 (the listing's clamp).  FP32 counts are >= 0, so
+// a count is positive iff its bits are not all zero.
+__device__ __forceinline__ uint32_t pack_positive(const uint32_t (&v)[32]) {
+  uint32_t m = 0u;
+#pragma unroll
+  for (int a = 0; a < 32; ++a) m |= (v[a] != 0u ? 1u : 0u) << a;
+  return m;
+}
+
+// The whole slab for every running state: 32 rg forward jobs and 4 nrows
+// reverse jobs, each through the A / B / MMA / epilogue pipeline.  jc counts
+// the CTA's jobs so far (the same in every role: ring stages and phases).
 __device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char *stage,
                            const TcStage &si, int k, int slot_w, int warp, int lane,
-                           uint32_t &mma_count) {
+                           uint32_t &jc) {
   const NetDev &N = P.net;
-  const int n = N.n, q = N.q, B = P.n_states;
+  const int n = N.n, B = P.n_states;
   const uint32_t I = si.ij & 0xFFFFu, J = si.ij >> 16;
   const uint32_t row0 = si.rows & 0xFFu, nrows = si.rows >> 8;
   const uint32_t *hdr = reinterpret_cast<const uint32_t *>(stage);
-  const uint32_t *relw = hdr + 2 * nrows;
   const int ct = warp * 32 + lane;  // consumer thread
-  const int nct = kTcConsumerWarps * 32;
-  const int quarter = warp & 3, part = warp >> 2;  // TMEM lanes 32*quarter.., column part
-  const int s = quarter * 32 + lane;               // this thread's state in the epilogue
-  const bool s_ok = s < B && !(S.st_info[s] & kInfoSweepMask);
+  constexpr int nct = kTcConsumerWarps * 32;
 
   // stage this slab's domain words of every state: [0,32) columns, [32,..) rows
   for (int i = ct; i < B * kTcDomWords; i += nct) {
@@ -214,143 +302,153 @@ __device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char
   }
   named_bar(kConsumersBar, nct);
 
-  const int rgroups = int(nrows + 7) / 8;
-  const int n_mma = 32 * rgroups + int(nrows) * 4;  // forward (column, row group), reverse (row, column group)
-  // this thread's AND accumulators: rows r with (r % 8) % 3 == part, columns j
-  // with (j % 8) % 3 == part (12 of each at most)
-  uint32_t facc[12], racc[12];
+  const int rg = int(nrows + 7) / 8;
+  const int n_jobs = 32 * rg + 4 * int(nrows);
+  if (warp >= kTcAWarp0 && warp < kTcAWarp0 + kTcAWarps) {
+    // A tiles: state s's word of the job's column (forward) or row (reverse)
+    const int s = (warp - kTcAWarp0) * 32 + lane;
+    for (int idx = 0; idx < n_jobs; ++idx) {
+      const uint32_t c = jc + uint32_t(idx);
+      const int st = int(c % kTcOpStages);
+      if (!warp_wait(S, P, &S.a_empty[st], ((c / kTcOpStages) & 1u) ^ 1u, lane)) break;
+      const int word = idx < 32 * rg ? (idx & 31) : 32 + (idx - 32 * rg) % int(nrows);
+      const uint32_t w = s < B ? S.dom[s][word] : 0u;
+      uint8_t *At = S.a_tile[st];
 #pragma unroll
-  for (int i = 0; i < 12; ++i) {
-    facc[i] = kFull;
-    racc[i] = kFull;
-  }
-
-  auto build = [&](int idx, int buf) {
-    uint8_t *At = S.a_tile[buf];
-    uint8_t *Bt = S.b_tile[buf];
-    if (idx < 32 * rgroups) {  // forward: column j, rows 8g..8g+7
-      const int j = idx / rgroups, g = idx % rgroups;
-      for (int i = ct; i < kTcMaxStates * 8; i += nct) {  // A: D_s[y_j] bits
-        const int st = i >> 3, qq = i & 7;
-        const uint32_t w = st < B ? S.dom[st][j] : 0u;
-        *reinterpret_cast<uint32_t *>(At + tile_off(st, 4 * qq)) = expand4((w >> (4 * qq)) & 0xFu);
-      }
-      for (int i = ct; i < kTcN * 8; i += nct) {  // B: rows (r, a) of R_{x_r, y_j}
-        const int row = i >> 3, qq = i & 7;
-        const int r = 8 * g + (row >> 5), a = row & 31;
-        uint32_t w = 0u;
-        if (r < int(nrows)) {
-          const uint32_t pm = hdr[r];
-          if ((pm >> j) & 1u) w = rel_row(hdr, relw, nrows, q, r, __popc(pm & ((1u << j) - 1u)), a);
-        }
-        *reinterpret_cast<uint32_t *>(Bt + tile_off(row, 4 * qq)) = expand4((w >> (4 * qq)) & 0xFu);
-      }
-    } else {  // reverse: row r, columns 8g..8g+7
-      const int ridx = idx - 32 * rgroups;
-      const int r = ridx / 4, g = ridx % 4;
-      for (int i = ct; i < kTcMaxStates * 8; i += nct) {  // A: D_s[x_r] bits
-        const int st = i >> 3, qq = i & 7;
-        const uint32_t w = st < B ? S.dom[st][32 + r] : 0u;
-        *reinterpret_cast<uint32_t *>(At + tile_off(st, 4 * qq)) = expand4((w >> (4 * qq)) & 0xFu);
-      }
-      // B: rows (j, b) = column b of R_{x_r, y_j}: one warp transposes one relation
-      const uint32_t pm = hdr[r];
-      for (int jj = warp; jj < 8; jj += kTcConsumerWarps) {
-        const int j = 8 * g + jj;
-        const bool present = (pm >> j) & 1u;
-        const uint32_t t = __popc(pm & ((1u << j) - 1u));
-        const uint32_t mine = present ? rel_row(hdr, relw, nrows, q, r, t, lane) : 0u;
-        uint32_t col = 0u;
-#pragma unroll 8
-        for (int b = 0; b < 32; ++b) {
-          const uint32_t m = __ballot_sync(kFull, (mine >> b) & 1u);
-          if (lane == b) col = m;
-        }
-        put_row(Bt, uint32_t(jj * 32 + lane), col);
-      }
-    }
-  };
-
-  auto epilogue = [&](int idx, int buf) {
-    const uint32_t acc = S.tmem_base + uint32_t(buf) * 256u + (uint32_t(quarter * 32) << 16);
-    if (idx < 32 * rgroups) {
-      const int j = idx / rgroups, g = idx % rgroups;
-      for (int rr = part; rr < 8; rr += 3) {
-        const int r = 8 * g + rr;
-        uint32_t v[32];
-        tmem_ld32(acc + uint32_t(rr * 32), v);  // all lanes of the warp, even idle states
-        if (r >= int(nrows) || !s_ok || !((hdr[r] >> j) & 1u)) continue;
-        uint32_t m = 0u;
-#pragma unroll
-        for (int a = 0; a < 32; ++a) m |= (__uint_as_float(v[a]) > 0.5f ? 1u : 0u) << a;
-        facc[(r / 8) * 3 + (r % 8) / 3] &= m;
-      }
-    } else {
-      const int ridx = idx - 32 * rgroups;
-      const int r = ridx / 4, g = ridx % 4;
-      for (int jj = part; jj < 8; jj += 3) {
-        const int j = 8 * g + jj;
-        uint32_t v[32];
-        tmem_ld32(acc + uint32_t(jj * 32), v);
-        if (!s_ok || !((hdr[r] >> j) & 1u)) continue;
-        uint32_t m = 0u;
-#pragma unroll
-        for (int b = 0; b < 32; ++b) m |= (__uint_as_float(v[b]) > 0.5f ? 1u : 0u) << b;
-        racc[(j / 8) * 3 + (j % 8) / 3] &= m;
-      }
-    }
-  };
-
-  // MMA number g (counted over the whole launch) uses operand buffer and
-  // accumulator g & 1; it is the (g >> 1)-th use of that buffer, so its
-  // completion is the phase of parity (g >> 1) & 1 of mma_done[g & 1].
-  const bool leader = ct == 0;
-  for (int idx = 0; idx <= n_mma; ++idx) {
-    const uint32_t g = mma_count + uint32_t(idx);
-    const int buf = int(g & 1u);
-    if (idx < n_mma) {
-      build(idx, buf);  // buffer last read by MMA g-2, whose completion was awaited
+      for (int qq = 0; qq < 8; ++qq)
+        *reinterpret_cast<uint32_t *>(At + tile_off(uint32_t(s), 4u * qq)) =
+            expand4((w >> (4 * qq)) & 0xFu);
       fence_async_smem();
-      tc_fence_before();
-      named_bar(kConsumersBar, nct);
-      tc_fence_after();
-      if (leader) {
-        umma_f8(S.tmem_base + uint32_t(buf) * 256u, umma_desc(S.a_tile[buf]),
-                umma_desc(S.b_tile[buf]));
-        umma_commit(&S.mma_done[buf]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.a_full[st]);
+    }
+  } else if (warp == kTcBWarp) {
+    // B tiles: the job's 8 KiB of the FP8 operand store
+    if (lane == 0) {
+      const uint8_t *tiles = N.fp8 + size_t(si.sl) * size_t(N.fp8_jobs) * kFp8TileBytes;
+      for (int idx = 0; idx < n_jobs; ++idx) {
+        const uint32_t c = jc + uint32_t(idx);
+        const int st = int(c % kTcOpStages);
+        if (aborted(S) || !mbar_wait(&S.b_empty[st], ((c / kTcOpStages) & 1u) ^ 1u,
+                                     &P.sync->err, P.wait_limit_ns)) {
+          S.abort = 1u;
+          break;
+        }
+        mbar_arrive_expect_tx(&S.b_full[st], kBTileBytes);
+        bulk_copy_g2s(S.b_tile[st], tiles + size_t(idx) * kFp8TileBytes, kBTileBytes,
+                      &S.b_full[st]);
+        S.b_issued = c + 1u;
       }
     }
-    if (idx >= 1) {
-      const uint32_t gp = g - 1u;
-      const int pb = int(gp & 1u);
-      const bool ok = mbar_wait(&S.mma_done[pb], (gp >> 1) & 1u, &P.sync->err, P.wait_limit_ns);
-      if (!ok) S.abort = 1;
-      tc_fence_after();
-      epilogue(idx - 1, pb);
-      tc_fence_before();
-      named_bar(kConsumersBar, nct);  // accumulator pb free for MMA g+1
+  } else if (warp == kTcMmaWarp) {
+    if (lane == 0) {
+      for (int idx = 0; idx < n_jobs; ++idx) {
+        const uint32_t c = jc + uint32_t(idx);
+        const int st = int(c % kTcOpStages);
+        const uint32_t par = (c / kTcOpStages) & 1u;
+        const int ab = int(c & 1u);
+        if (aborted(S) || !mbar_wait(&S.a_full[st], par, &P.sync->err, P.wait_limit_ns) ||
+            !mbar_wait(&S.b_full[st], par, &P.sync->err, P.wait_limit_ns) ||
+            !mbar_wait(&S.acc_empty[ab], ((c >> 1) & 1u) ^ 1u, &P.sync->err, P.wait_limit_ns)) {
+          S.abort = 1u;
+          break;
+        }
+        tc_fence_after();
+        umma_f8(S.tmem_base + uint32_t(ab) * 256u, umma_desc(S.a_tile[st]),
+                umma_desc(S.b_tile[st]));
+        umma_commit(&S.a_empty[st]);
+        umma_commit(&S.b_empty[st]);
+        umma_commit(&S.acc_full[ab]);
+        S.mma_issued = c + 1u;
+      }
+    }
+  } else if (warp < kTcEpiWarps) {
+    const int quarter = warp & 3, half = warp >> 2;
+    const int s = quarter * 32 + lane;  // this thread's state
+    const bool s_ok = s < B && !(S.st_info[s] & kInfoSweepMask);
+    const uint32_t tq = S.tmem_base + (uint32_t(quarter * 32) << 16);
+    // AND masks of this half's rows (forward) and columns (reverse):
+    // facc[4 g + i] for row 8 g + 4 half + i, racc[4 g + i] for column 8 g + 4 half + i
+    uint32_t facc[16], racc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      facc[i] = kFull;
+      racc[i] = kFull;
+    }
+    bool ok = true;
+    int idx = 0;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {  // forward jobs g * 32 + j
+      if (g >= rg) break;
+      for (int j = 0; j < 32; ++j, ++idx) {
+        const uint32_t c = jc + uint32_t(idx);
+        const int ab = int(c & 1u);
+        if (!ok || !(ok = warp_wait(S, P, &S.acc_full[ab], (c >> 1) & 1u, lane))) continue;
+        tc_fence_after();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int rr = 4 * half + i, r = 8 * g + rr;
+          if (r < int(nrows) && ((hdr[r] >> j) & 1u)) {  // warp-uniform
+            uint32_t v[32];
+            tmem_ld32(tq + uint32_t(ab) * 256u + uint32_t(rr * 32), v);
+            facc[4 * g + i] &= pack_positive(v);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.acc_empty[ab]);
+      }
+    }
+    idx = 32 * rg;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {  // reverse jobs 32 rg + g nrows + r
+      for (int r = 0; r < int(nrows); ++r, ++idx) {
+        const uint32_t c = jc + uint32_t(idx);
+        const int ab = int(c & 1u);
+        if (!ok || !(ok = warp_wait(S, P, &S.acc_full[ab], (c >> 1) & 1u, lane))) continue;
+        tc_fence_after();
+        const uint32_t pm = hdr[r];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int jj = 4 * half + i, j = 8 * g + jj;
+          if ((pm >> j) & 1u) {  // warp-uniform
+            uint32_t v[32];
+            tmem_ld32(tq + uint32_t(ab) * 256u + uint32_t(jj * 32), v);
+            racc[4 * g + i] &= pack_positive(v);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.acc_empty[ab]);
+      }
+    }
+    // removals of this thread's state: this half's rows and columns
+    if (ok && s_ok) {
+      uint32_t *T = tc_view(P, s, k).T;
+      uint32_t colmask = 0u;  // columns with at least one constraint in the slab
+      for (int r = 0; r < int(nrows); ++r) colmask |= hdr[r];
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = 8 * g + 4 * half + i;
+          if (r < int(nrows) && hdr[r] != 0u) {
+            const uint32_t Dx = S.dom[s][32 + r];
+            const uint32_t keep = facc[4 * g + i] & Dx;
+            if (keep != Dx)
+              tc_remove(S, P, s, slot_w, T, uint32_t(int(I) * 32 + int(row0) + r), keep);
+          }
+          const int j = 8 * g + 4 * half + i;
+          if ((colmask >> j) & 1u) {
+            const uint32_t Dy = S.dom[s][j];
+            const uint32_t keep = racc[4 * g + i] & Dy;
+            if (keep != Dy) tc_remove(S, P, s, slot_w, T, uint32_t(int(J) * 32 + j), keep);
+          }
+        }
+      }
     }
   }
-  mma_count += uint32_t(n_mma);
-
-  // removals of this thread's state, rows and columns
-  if (s_ok) {
-    uint32_t *T = tc_view(P, s, k).T;
-    for (int r = 0; r < int(nrows); ++r) {
-      if ((r % 8) % 3 != part || hdr[r] == 0u) continue;
-      const uint32_t Dx = S.dom[s][32 + r];
-      const uint32_t keep = facc[(r / 8) * 3 + (r % 8) / 3] & Dx;
-      if (keep != Dx) tc_remove(S, P, s, slot_w, T, uint32_t(int(I) * 32 + int(row0) + r), keep);
-    }
-    uint32_t colmask = 0u;  // columns with at least one constraint in the slab
-    for (int r = 0; r < int(nrows); ++r) colmask |= hdr[r];
-    for (int j = 0; j < 32; ++j) {
-      if ((j % 8) % 3 != part || !((colmask >> j) & 1u)) continue;
-      const uint32_t Dy = S.dom[s][j];
-      const uint32_t keep = racc[(j / 8) * 3 + (j % 8) / 3] & Dy;
-      if (keep != Dy) tc_remove(S, P, s, slot_w, T, uint32_t(int(J) * 32 + j), keep);
-    }
-  }
+  jc += uint32_t(n_jobs);
   named_bar(kConsumersBar, nct);  // S.dom free for the next slab
 }
 
@@ -382,9 +480,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
       mbar_init(&S.full[i], 1);
       mbar_init(&S.empty[i], kTcConsumerWarps);
     }
-    mbar_init(&S.mma_done[0], 1);
-    mbar_init(&S.mma_done[1], 1);
+    for (int i = 0; i < kTcOpStages; ++i) {
+      mbar_init(&S.a_full[i], kTcAWarps);
+      mbar_init(&S.a_empty[i], 1);
+      mbar_init(&S.b_full[i], 1);
+      mbar_init(&S.b_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&S.acc_full[i], 1);
+      mbar_init(&S.acc_empty[i], kTcEpiWarps);
+    }
     fence_mbar_init();
+    S.mma_issued = 0;
+    S.b_issued = 0;
     S.abort = 0;
     S.failed = 0;
     S.all_done = 0;
@@ -400,7 +508,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
   __syncthreads();
   tc_fence_after();
   const uint32_t base = S.base;
-  uint32_t ring_it = 0, prod_it = 0, mma_count = 0;
+  uint32_t ring_it = 0, prod_it = 0, jc = 0;
   int k = 0;
   if (S.poisoned) {
     S.failed = 1;
@@ -504,8 +612,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
           __syncwarp();
           const TcStage si = S.stage[stg];
           if (si.sl >= 0)
-            tc_consume(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_w, warp, lane,
-                       mma_count);
+            tc_consume(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_w, warp, lane, jc);
           __syncwarp();
           if (lane == 0) mbar_arrive(&S.empty[stg]);
           ++ring_it;
@@ -619,12 +726,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
     for (uint32_t j = first; j < prod_it; ++j)
       mbar_wait(&S.full[j % kTcStages], (j / kTcStages) & 1u, &P.sync->err, P.wait_limit_ns);
   }
-  // no MMA may still write the accumulators when they are released
-  if (tid == 0 && mma_count > 0) {
-    for (uint32_t b = 0; b < 2; ++b) {
-      const uint32_t uses = (mma_count + 1u - b) / 2u;  // MMAs issued on buffer b
-      if (uses) mbar_wait(&S.mma_done[b], (uses - 1u) & 1u, &P.sync->err, P.wait_limit_ns);
+  // no MMA may still write the accumulators, and no operand copy may still
+  // be in flight, when they are released: wait for the last ones issued (the
+  // phases of a normal run are complete already)
+  if (tid == 0) {
+    const uint32_t mi = S.mma_issued, bi = S.b_issued;
+    if (mi > 0) {
+      const uint32_t c = mi - 1u;
+      mbar_wait(&S.acc_full[c & 1u], (c >> 1) & 1u, &P.sync->err, P.wait_limit_ns);
     }
+    const uint32_t first = bi > uint32_t(kTcOpStages) ? bi - kTcOpStages : 0u;
+    for (uint32_t c = first; c < bi; ++c)
+      mbar_wait(&S.b_full[c % kTcOpStages], (c / kTcOpStages) & 1u, &P.sync->err,
+                P.wait_limit_ns);
   }
   tc_fence_before();
   __syncthreads();
@@ -642,6 +756,10 @@ rac_status launch_tc(const LaunchParams &P, cudaStream_t stream) {
   const size_t smem = size_t(kTcStages) * kStageBytes + sizeof(TcSmem);
   if (P.n_states > kTcMaxStates) {
     set_error("the tensor-core kernel takes at most 128 states per launch");
+    return RAC_EINVAL;
+  }
+  if (!P.net.fp8 || P.net.fp8_jobs != fp8_jobs_for(P.net.rows_per_slab)) {
+    set_error("the network's FP8 operand store is missing");
     return RAC_EINVAL;
   }
   int per_sm = 0, sms = 0;
@@ -666,6 +784,41 @@ rac_status launch_tc(const LaunchParams &P, cudaStream_t stream) {
   cfg.numAttrs = 1;
   e = cudaLaunchKernelEx(&cfg, rac_tc_kernel, P);
   if (e != cudaSuccess) return cuda_fail(e, "launch of the tensor-core kernel");
+  return RAC_OK;
+}
+
+rac_status ensure_fp8(const rac_network *net, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lock(net->mu);
+  if (net->d_fp8) return RAC_OK;
+  const size_t tiles = size_t(net->n_slabs) * size_t(net->fp8_jobs);
+  const size_t bytes = tiles * size_t(kFp8TileBytes);
+  if (bytes > (size_t(64) << 30)) {
+    set_error("the FP8 operand store of this network would take " +
+              std::to_string(bytes >> 30) + " GiB (at most 64)");
+    return RAC_ENOTSUP;
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("out of device memory for the FP8 operand store (" + std::to_string(bytes) +
+              " bytes)");
+    return RAC_ENOMEM;
+  }
+  if (tiles > 0) {
+    NetDev N = net_dev(net);
+    const int64_t words = int64_t(tiles) * (kFp8TileBytes / 4);
+    const int64_t blocks = std::min<int64_t>((words + 255) / 256, int64_t(1) << 20);
+    rac_fp8_build_kernel<<<unsigned(blocks), 256, 0, stream>>>(N, static_cast<uint8_t *>(p));
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+      cudaFree(p);
+      return cuda_fail(e, "building the FP8 operand store");
+    }
+  }
+  net->d_fp8 = static_cast<uint8_t *>(p);
+  net->fp8_bytes = bytes;
   return RAC_OK;
 }
 

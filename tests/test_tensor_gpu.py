@@ -70,3 +70,21 @@ def test_tensor_dense_500():
                                                     for s in range(7)])
     assert_same(gpu_enforce(500, 20, net.scope, net.rel, doms, TC, shuffle_seed=5),
                 oracle_enforce(500, 20, net.scope, net.rel, doms), "dense500 tensor")
+
+
+def test_fp8_store_built_at_creation():
+    """RAC_LAYOUT_FP8 builds the FP8 operand store when the network is
+    created; the tensor-core kernel then reads it (the other tests build it
+    on their first tensor-core call)."""
+    n, d = 300, 24
+    net_np = racgen.random_network(5, 0, n, d, 0.7, 0.55)
+    doms = np.array([racgen.assignment_state(5, 0, s, n, d) for s in range(40)])
+    ref = oracle_enforce(n, d, net_np.scope, net_np.rel, doms)
+    with rac.Network(n, d, net_np.scope, net_np.rel,
+                     layout=rac.LAYOUT_BITS | rac.LAYOUT_FP8) as net:
+        for flags in (TC, TC | rac.INCREMENTAL, TC | rac.STOP_ON_WIPEOUT):
+            want = ref if flags == TC or flags == TC | rac.INCREMENTAL else \
+                oracle_enforce(n, d, net_np.scope, net_np.rel, doms, rac.STOP_ON_WIPEOUT)
+            assert_same(gpu_enforce(n, d, net_np.scope, net_np.rel, doms, flags, net=net), want,
+                        "flags %d" % flags)
+    assert ref[1].max() >= 3
