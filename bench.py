@@ -636,6 +636,25 @@ def compare_learned(W, args, stream, flush, per_step_s, world):
     return res
 
 
+def tensor_roofline(W, its, per_step_s, kernel):
+    """The tensor-core kernel's algorithmic MMA work -- per state and sweep,
+    every relation's forward and reverse counts, 2 x d x d multiply-adds
+    each (4 d^2 flops) -- over the launch's CUDA-event time, against the
+    dense FP8 peak measured on this machine (profiles/fp8_peak.json)."""
+    flops = sum(4.0 * W.nets_np[int(W.items[j])].m * W.nets_np[int(W.items[j])].d ** 2 * int(its[j])
+                for j in range(W.B))
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "profiles", "fp8_peak.json")))
+                     ["fp8_e4m3_tflops_burst"])
+        src = "measured (profiles/fp8_peak.json: cuBLASLt E4M3 GEMM)"
+    except (OSError, ValueError, KeyError):
+        peak, src = 4500.0, "nominal dense FP8"
+    achieved = flops / per_step_s / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": src, "kernel": kernel,
+            "alg_flops_per_launch": flops}
+
+
 def issue_roofline(wl, per_step_s, torch, dev, peaks, kernel):
     """Warp instructions per launch (ncu smsp__inst_executed.sum, recorded on
     the kernel's current sources) over the live CUDA-event time of a launch,
@@ -751,6 +770,27 @@ def run_ours(args):
                  "how": "one single-state rac_enforce launch per item (kernel (a)), same items",
                  "speedup_of_this_form": (world * B / per_step_s) / (world * B / t_plain)}
 
+    # the tensor-core kernel against kernel (a) on the same states (one
+    # batched launch each, the same flags otherwise)
+    kernel_a = None
+    if args.flags & 0x10:
+        fl_a = args.flags & ~0x10
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        W.step(fl_a, stream)
+        torch.cuda.synchronize()
+        reps, t_a = max(3, min(20, K)), 0.0
+        for _ in range(reps):
+            flush()
+            e0.record(stream)
+            W.step(fl_a, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_a += e0.elapsed_time(e1) / 1000.0
+        t_a = max_over_ranks(t_a) / reps
+        kernel_a = {"ms_per_step": t_a * 1000.0, "value": world * B / t_a, "unit": "fixpoints/s",
+                    "how": "kernel (a) (bit-packed) on the same states, same launch shape",
+                    "tensor_speedup_over_it": t_a / per_step_s}
+
     # end to end through the host entry point (copies inside the timed region)
     e2e = None
     if not args.no_e2e and len(W.nets) == 1 and W.pred is None:
@@ -816,14 +856,19 @@ def run_ours(args):
     achieved = alg_bytes_per_launch / per_step_s / 1e9
     traffic = traffic_from_profiles(args.workload)
     clocks = clk.summary()
-    kernel = "rac_batch_kernel" if W.plan is not None else "rac_bits_kernel"
+    kernel = "rac_batch_kernel" if W.plan is not None else (
+        "rac_tc_kernel" if args.flags & 0x10 else "rac_bits_kernel")
 
     hbm_line = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,
                 "peak_source": "measured" if peaks else "fallback",
                 "kernel": kernel, "alg_bytes_per_launch": alg_bytes_per_launch}
     roof = hbm_line
-    if B > 1:
+    if args.flags & 0x10:
+        # the tensor-core kernel: its MMAs against the measured FP8 peak
+        roof = tensor_roofline(W, its, per_step_s, kernel="rac_tc_kernel")
+        roof["hbm"] = hbm_line
+    elif B > 1:
         # many states: the per-state support tests bound the launch, not the
         # one read of the store per sweep; the binding roofline is the SM
         # issue rate (one warp instruction per cycle per scheduler)
@@ -844,6 +889,8 @@ def run_ours(args):
             "e2e": e2e}
     if plain is not None:
         line["plain_gpu_rac"] = plain
+    if kernel_a is not None:
+        line["kernel_a_same_states"] = kernel_a
     if learned_cmp is not None:
         line["learned"] = learned_cmp
         line["learned"]["training"] = W.train_info

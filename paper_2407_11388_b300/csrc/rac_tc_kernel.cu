@@ -33,8 +33,9 @@
 //   warp 14      helps stage the slab's domain words;
 //   warp 15      streams the bit-packed slabs (their headers name the
 //                relations present) into a small ring, as in kernel (a).
-// Operand rings of four stages and two accumulators of 256 columns keep the
-// roles apart by up to four jobs.
+// An A ring of four stages, a B ring of eight (64 KiB of copies in flight)
+// and two accumulators of 256 columns let the roles run apart by several
+// jobs.
 #include <algorithm>
 #include <mutex>
 #include <string>
@@ -54,8 +55,9 @@ constexpr int kTcBWarp = 12;
 constexpr int kTcMmaWarp = 13;
 constexpr int kTcConsumerWarps = 15;  // warps 0-14; warp 15 streams the bit-packed slabs
 constexpr int kTcThreads = (kTcConsumerWarps + 1) * 32;
-constexpr int kTcStages = 3;    // bit-packed slab ring
-constexpr int kTcOpStages = 4;  // A and B operand rings
+constexpr int kTcStages = 2;   // bit-packed slab ring
+constexpr int kTcAStages = 4;  // A operand ring (built on chip)
+constexpr int kTcBStages = 8;  // B operand ring (8 KiB copies in flight from HBM)
 constexpr int kTcMaxStates = 128;  // M of the MMA
 constexpr int kTcN = 256;          // N of the MMA: 8 relations x 32 rows
 constexpr uint32_t kTmemCols = 512;  // two accumulators of 256 columns
@@ -70,13 +72,13 @@ struct TcStage {
 };
 
 struct TcSmem {
-  uint8_t a_tile[kTcOpStages][kATileBytes];
-  uint8_t b_tile[kTcOpStages][kBTileBytes];
+  uint8_t a_tile[kTcAStages][kATileBytes];
+  uint8_t b_tile[kTcBStages][kBTileBytes];
   uint32_t dom[kTcMaxStates][kTcDomWords];  // staged D_{k-1} words of the slab
   uint64_t full[kTcStages];
   uint64_t empty[kTcStages];
-  uint64_t a_full[kTcOpStages], a_empty[kTcOpStages];
-  uint64_t b_full[kTcOpStages], b_empty[kTcOpStages];
+  uint64_t a_full[kTcAStages], a_empty[kTcAStages];
+  uint64_t b_full[kTcBStages], b_empty[kTcBStages];
   uint64_t acc_full[2], acc_empty[2];
   TcStage stage[kTcStages];
   uint32_t stage_ok[kTcStages];
@@ -309,8 +311,8 @@ __device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char
     const int s = (warp - kTcAWarp0) * 32 + lane;
     for (int idx = 0; idx < n_jobs; ++idx) {
       const uint32_t c = jc + uint32_t(idx);
-      const int st = int(c % kTcOpStages);
-      if (!warp_wait(S, P, &S.a_empty[st], ((c / kTcOpStages) & 1u) ^ 1u, lane)) break;
+      const int st = int(c % kTcAStages);
+      if (!warp_wait(S, P, &S.a_empty[st], ((c / kTcAStages) & 1u) ^ 1u, lane)) break;
       const int word = idx < 32 * rg ? (idx & 31) : 32 + (idx - 32 * rg) % int(nrows);
       const uint32_t w = s < B ? S.dom[s][word] : 0u;
       uint8_t *At = S.a_tile[st];
@@ -328,8 +330,8 @@ __device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char
       const uint8_t *tiles = N.fp8 + size_t(si.sl) * size_t(N.fp8_jobs) * kFp8TileBytes;
       for (int idx = 0; idx < n_jobs; ++idx) {
         const uint32_t c = jc + uint32_t(idx);
-        const int st = int(c % kTcOpStages);
-        if (aborted(S) || !mbar_wait(&S.b_empty[st], ((c / kTcOpStages) & 1u) ^ 1u,
+        const int st = int(c % kTcBStages);
+        if (aborted(S) || !mbar_wait(&S.b_empty[st], ((c / kTcBStages) & 1u) ^ 1u,
                                      &P.sync->err, P.wait_limit_ns)) {
           S.abort = 1u;
           break;
@@ -344,20 +346,20 @@ __device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char
     if (lane == 0) {
       for (int idx = 0; idx < n_jobs; ++idx) {
         const uint32_t c = jc + uint32_t(idx);
-        const int st = int(c % kTcOpStages);
-        const uint32_t par = (c / kTcOpStages) & 1u;
+        const int sa = int(c % kTcAStages), sb = int(c % kTcBStages);
         const int ab = int(c & 1u);
-        if (aborted(S) || !mbar_wait(&S.a_full[st], par, &P.sync->err, P.wait_limit_ns) ||
-            !mbar_wait(&S.b_full[st], par, &P.sync->err, P.wait_limit_ns) ||
+        if (aborted(S) ||
+            !mbar_wait(&S.a_full[sa], (c / kTcAStages) & 1u, &P.sync->err, P.wait_limit_ns) ||
+            !mbar_wait(&S.b_full[sb], (c / kTcBStages) & 1u, &P.sync->err, P.wait_limit_ns) ||
             !mbar_wait(&S.acc_empty[ab], ((c >> 1) & 1u) ^ 1u, &P.sync->err, P.wait_limit_ns)) {
           S.abort = 1u;
           break;
         }
         tc_fence_after();
-        umma_f8(S.tmem_base + uint32_t(ab) * 256u, umma_desc(S.a_tile[st]),
-                umma_desc(S.b_tile[st]));
-        umma_commit(&S.a_empty[st]);
-        umma_commit(&S.b_empty[st]);
+        umma_f8(S.tmem_base + uint32_t(ab) * 256u, umma_desc(S.a_tile[sa]),
+                umma_desc(S.b_tile[sb]));
+        umma_commit(&S.a_empty[sa]);
+        umma_commit(&S.b_empty[sb]);
         umma_commit(&S.acc_full[ab]);
         S.mma_issued = c + 1u;
       }
@@ -366,6 +368,8 @@ __device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char
     const int quarter = warp & 3, half = warp >> 2;
     const int s = quarter * 32 + lane;  // this thread's state
     const bool s_ok = s < B && !(S.st_info[s] & kInfoSweepMask);
+    // a quarter without running states only keeps the accumulators moving
+    const bool live = __any_sync(kFull, s_ok);
     const uint32_t tq = S.tmem_base + (uint32_t(quarter * 32) << 16);
     // AND masks of this half's rows (forward) and columns (reverse):
     // facc[4 g + i] for row 8 g + 4 half + i, racc[4 g + i] for column 8 g + 4 half + i
@@ -388,7 +392,7 @@ __device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int rr = 4 * half + i, r = 8 * g + rr;
-          if (r < int(nrows) && ((hdr[r] >> j) & 1u)) {  // warp-uniform
+          if (live && r < int(nrows) && ((hdr[r] >> j) & 1u)) {  // warp-uniform
             uint32_t v[32];
             tmem_ld32(tq + uint32_t(ab) * 256u + uint32_t(rr * 32), v);
             facc[4 * g + i] &= pack_positive(v);
@@ -411,7 +415,7 @@ __device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int jj = 4 * half + i, j = 8 * g + jj;
-          if ((pm >> j) & 1u) {  // warp-uniform
+          if (live && ((pm >> j) & 1u)) {  // warp-uniform
             uint32_t v[32];
             tmem_ld32(tq + uint32_t(ab) * 256u + uint32_t(jj * 32), v);
             racc[4 * g + i] &= pack_positive(v);
@@ -480,9 +484,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
       mbar_init(&S.full[i], 1);
       mbar_init(&S.empty[i], kTcConsumerWarps);
     }
-    for (int i = 0; i < kTcOpStages; ++i) {
+    for (int i = 0; i < kTcAStages; ++i) {
       mbar_init(&S.a_full[i], kTcAWarps);
       mbar_init(&S.a_empty[i], 1);
+    }
+    for (int i = 0; i < kTcBStages; ++i) {
       mbar_init(&S.b_full[i], 1);
       mbar_init(&S.b_empty[i], 1);
     }
@@ -735,9 +741,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
       const uint32_t c = mi - 1u;
       mbar_wait(&S.acc_full[c & 1u], (c >> 1) & 1u, &P.sync->err, P.wait_limit_ns);
     }
-    const uint32_t first = bi > uint32_t(kTcOpStages) ? bi - kTcOpStages : 0u;
+    const uint32_t first = bi > uint32_t(kTcBStages) ? bi - kTcBStages : 0u;
     for (uint32_t c = first; c < bi; ++c)
-      mbar_wait(&S.b_full[c % kTcOpStages], (c / kTcOpStages) & 1u, &P.sync->err,
+      mbar_wait(&S.b_full[c % kTcBStages], (c / kTcBStages) & 1u, &P.sync->err,
                 P.wait_limit_ns);
   }
   tc_fence_before();
