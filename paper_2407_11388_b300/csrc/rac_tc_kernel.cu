@@ -20,19 +20,21 @@
 // job's tile expanded once, on the device, in the MMA's shared-memory layout),
 // brought in by bulk copies.  A slab's jobs run through a pipeline of warps
 // that wait on mbarriers only (no CTA-wide barrier per MMA):
-//   warps 0-7    epilogue: TMEM lane quarter warp % 4 (32 states), half of
-//                each job's 8 relations (warp / 4); they keep a slab's AND
-//                masks in registers and make its removals;
-//   warps 8-11   A tiles: the states' domain word of the job's column (or
+//   warps 0-15   epilogue: TMEM lane quarter warp % 4 (32 states), a
+//                quarter of each job's 8 relations (warp / 4); they keep a
+//                slab's AND masks in registers and make its removals;
+//   warps 16-19  A tiles: the states' domain word of the job's column (or
 //                row) expanded to E4M3 bytes, 32 states each;
-//   warp 12      B tiles: one bulk copy of 8 KiB per job;
-//   warp 13      MMA issuer: waits for the job's A and B tiles and a free
+//   warp 20      B tiles: one bulk copy of 8 KiB per job;
+//   warp 21      MMA issuer: waits for the job's A and B tiles and a free
 //                accumulator, issues the MMA, and commits its completion to
 //                the A and B stages it frees and to the accumulator's full
 //                barrier;
-//   warp 14      helps stage the slab's domain words;
-//   warp 15      streams the bit-packed slabs (their headers name the
+//   warp 22      helps stage the slab's domain words;
+//   warp 23      streams the bit-packed slabs (their headers name the
 //                relations present) into a small ring, as in kernel (a).
+// Four epilogue warps per quarter keep several tensor-memory loads in
+// flight on each SM sub-partition.
 // An A ring of four stages, a B ring of eight (64 KiB of copies in flight)
 // and two accumulators of 256 columns let the roles run apart by several
 // jobs.
@@ -49,11 +51,14 @@ namespace {
 using namespace dev;
 
 // warp roles (see the file comment)
-constexpr int kTcEpiWarps = 8;
-constexpr int kTcAWarp0 = 8, kTcAWarps = 4;
-constexpr int kTcBWarp = 12;
-constexpr int kTcMmaWarp = 13;
-constexpr int kTcConsumerWarps = 15;  // warps 0-14; warp 15 streams the bit-packed slabs
+constexpr int kTcEpiParts = 4;                   // epilogue warps per TMEM lane quarter
+constexpr int kTcEpiWarps = 4 * kTcEpiParts;      // warps 0-15
+constexpr int kRelPerPart = 8 / kTcEpiParts;      // a job's relations per epilogue warp
+constexpr int kTcAWarp0 = kTcEpiWarps, kTcAWarps = 4;  // warps 16-19
+constexpr int kTcBWarp = kTcAWarp0 + kTcAWarps;        // warp 20
+constexpr int kTcMmaWarp = kTcBWarp + 1;               // warp 21
+constexpr int kTcConsumerWarps = kTcMmaWarp + 2;  // warps 0-22 (22 helps stage the domains);
+                                                  // warp 23 streams the bit-packed slabs
 constexpr int kTcThreads = (kTcConsumerWarps + 1) * 32;
 constexpr int kTcStages = 2;   // bit-packed slab ring
 constexpr int kTcAStages = 4;  // A operand ring (built on chip)
@@ -365,17 +370,19 @@ __device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char
       }
     }
   } else if (warp < kTcEpiWarps) {
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3, part = warp >> 2;
     const int s = quarter * 32 + lane;  // this thread's state
     const bool s_ok = s < B && !(S.st_info[s] & kInfoSweepMask);
     // a quarter without running states only keeps the accumulators moving
     const bool live = __any_sync(kFull, s_ok);
     const uint32_t tq = S.tmem_base + (uint32_t(quarter * 32) << 16);
-    // AND masks of this half's rows (forward) and columns (reverse):
-    // facc[4 g + i] for row 8 g + 4 half + i, racc[4 g + i] for column 8 g + 4 half + i
-    uint32_t facc[16], racc[16];
+    // AND masks of this part's rows (forward) and columns (reverse): with
+    // R = kRelPerPart, facc[R g + i] for row 8 g + R part + i and racc[R g + i]
+    // for column 8 g + R part + i
+    constexpr int R = kRelPerPart;
+    uint32_t facc[4 * R], racc[4 * R];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < 4 * R; ++i) {
       facc[i] = kFull;
       racc[i] = kFull;
     }
@@ -390,12 +397,12 @@ __device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char
         if (!ok || !(ok = warp_wait(S, P, &S.acc_full[ab], (c >> 1) & 1u, lane))) continue;
         tc_fence_after();
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int rr = 4 * half + i, r = 8 * g + rr;
+        for (int i = 0; i < R; ++i) {
+          const int rr = R * part + i, r = 8 * g + rr;
           if (live && r < int(nrows) && ((hdr[r] >> j) & 1u)) {  // warp-uniform
             uint32_t v[32];
             tmem_ld32(tq + uint32_t(ab) * 256u + uint32_t(rr * 32), v);
-            facc[4 * g + i] &= pack_positive(v);
+            facc[R * g + i] &= pack_positive(v);
           }
         }
         tc_fence_before();
@@ -413,12 +420,12 @@ __device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char
         tc_fence_after();
         const uint32_t pm = hdr[r];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int jj = 4 * half + i, j = 8 * g + jj;
+        for (int i = 0; i < R; ++i) {
+          const int jj = R * part + i, j = 8 * g + jj;
           if (live && ((pm >> j) & 1u)) {  // warp-uniform
             uint32_t v[32];
             tmem_ld32(tq + uint32_t(ab) * 256u + uint32_t(jj * 32), v);
-            racc[4 * g + i] &= pack_positive(v);
+            racc[R * g + i] &= pack_positive(v);
           }
         }
         tc_fence_before();
@@ -426,7 +433,7 @@ __device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char
         if (lane == 0) mbar_arrive(&S.acc_empty[ab]);
       }
     }
-    // removals of this thread's state: this half's rows and columns
+    // removals of this thread's state: this part's rows and columns
     if (ok && s_ok) {
       uint32_t *T = tc_view(P, s, k).T;
       uint32_t colmask = 0u;  // columns with at least one constraint in the slab
@@ -434,18 +441,18 @@ __device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int r = 8 * g + 4 * half + i;
+        for (int i = 0; i < R; ++i) {
+          const int r = 8 * g + R * part + i;
           if (r < int(nrows) && hdr[r] != 0u) {
             const uint32_t Dx = S.dom[s][32 + r];
-            const uint32_t keep = facc[4 * g + i] & Dx;
+            const uint32_t keep = facc[R * g + i] & Dx;
             if (keep != Dx)
               tc_remove(S, P, s, slot_w, T, uint32_t(int(I) * 32 + int(row0) + r), keep);
           }
-          const int j = 8 * g + 4 * half + i;
+          const int j = 8 * g + R * part + i;
           if ((colmask >> j) & 1u) {
             const uint32_t Dy = S.dom[s][j];
-            const uint32_t keep = racc[4 * g + i] & Dy;
+            const uint32_t keep = racc[R * g + i] & Dy;
             if (keep != Dy) tc_remove(S, P, s, slot_w, T, uint32_t(int(J) * 32 + j), keep);
           }
         }
