@@ -115,9 +115,14 @@ typedef int32_t rac_status;
 #define RAC_KERNEL_TENSOR 0x10u  /* evaluate the support counts with the tensor-core
                                     kernel (tcgen05 FP8 GEMMs, FP32 accumulation in
                                     tensor memory) instead of the bit-packed kernel:
-                                    rac_enforce and single-network rac_enforce_batch
-                                    only, at most 128 states per launch (larger
-                                    batches are split).  Results are identical. */
+                                    rac_enforce, single-network rac_enforce_batch
+                                    and rac_enforce_host only, at most 128 states
+                                    per launch (larger batches are split).  It
+                                    reads the network's FP8 operand store
+                                    (RAC_LAYOUT_FP8), which the first such call
+                                    builds if the network has none: make that
+                                    call outside any stream capture.  Results
+                                    are identical. */
 #define RAC_TEST_WITHHOLD_ARRIVAL 0x80000000u
                                  /* test hook for failure detection: one CTA
                                     withholds its first grid-barrier arrival,
