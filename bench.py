@@ -440,6 +440,9 @@ def run_reference_search(args, spec):
     print(json.dumps(line), flush=True)
 
 
+# untimed steps right before the timed ones (after the clock sampler starts)
+RESUME_STEPS = 10
+
 # a slab's 32-state group is scored only with at least this many gated
 # candidates (fewer are evaluated unscored: measured faster on B300)
 LEARNED_MIN_SCORED = 28
@@ -724,6 +727,11 @@ def run_ours(args):
     gc.collect()
     gc.disable()
     with ClockSampler(local) as clk:
+        # the sampler's start-up leaves the GPU idle for a while: a few more
+        # untimed steps bring its clock back up before the timed ones
+        for _ in range(RESUME_STEPS):
+            W.step(args.flags, stream)
+            flush()
         w0 = time.perf_counter()
         for i in range(K):
             starts[i].record(stream)
@@ -810,7 +818,7 @@ def run_ours(args):
 
         for _ in range(20):
             host_step()
-        Ke = max(10, min(K, 500))
+        Ke = max(100, min(K, 500))  # host calls: at least 100 even in a short run
         if pg:
             pg.barrier()
         gc.collect()
@@ -875,7 +883,7 @@ def run_ours(args):
         roof = issue_roofline(args.workload, per_step_s, torch, dev, peaks, kernel)
         roof["hbm"] = hbm_line
     line = {"metric": METRIC, "value": value, "unit": "fixpoints/s", "n_gpus": world,
-            "steps": K, "warmup": warm, "ms_per_step": per_step_s * 1000.0,
+            "steps": K, "warmup": warm + RESUME_STEPS, "ms_per_step": per_step_s * 1000.0,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic (seeded random binary CSP, generated in-process)",
             "config": W.cfg,
