@@ -660,7 +660,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
                                         (uint64_t(S.cta_wipe ? 1u : 0u) << (2 * kBarCountBits)) |
                                         (uint64_t(S.failed ? 1u : 0u) << (3 * kBarCountBits));
         __threadfence();
-        unsigned long long v = atomicAdd(w, mine) + mine;
+        // test hook: CTA 0 withholds its arrivals, so every wait runs out
+        const bool withhold = (P.flags & RAC_TEST_WITHHOLD_ARRIVAL) && cta == 0;
+        unsigned long long v = withhold ? 0ull : atomicAdd(w, mine) + mine;
         const uint64_t t0 = global_timer();
         while ((v & kMask) < uint64_t(G)) {
           if (ld_acquire(&P.sync->err) != 0u) {

@@ -65,3 +65,33 @@ def test_bounded_wait_reported_through_the_host_entry_point():
         out, it, st = rac.enforce_host(net, doms, stream=T.cuda.Stream())
         assert np.array_equal(out, want[0]) and list(it) == list(want[1])
         assert list(st) == list(want[2])
+
+
+def test_bounded_wait_runs_out_in_the_tensor_core_kernel():
+    """The tensor-core kernel's grid barrier takes the same hook: a wait that
+    runs out gives RAC_EBARRIER within the short limit, the workspace stays
+    poisoned, and another stream's workspace still enforces correctly."""
+    T = torch()
+    n, d = 200, 16
+    net_np = racgen.random_network(10, 0, n, d, 0.5, 0.5)
+    doms = np.array([racgen.assignment_state(10, 0, s, n, d) for s in range(5)])
+    want = oracle_enforce(n, d, net_np.scope, net_np.rel, doms)
+    TC = rac.KERNEL_TENSOR
+    with rac.Network(n, d, net_np.scope, net_np.rel) as net:
+        din = to_dev(doms.reshape(-1))
+        dout = T.empty_like(din)
+        it = T.full((5,), -7, dtype=T.int32, device="cuda:0")
+        st = T.full((5,), -7, dtype=T.int32, device="cuda:0")
+        items, offs = np.zeros(5, np.int32), np.arange(5, dtype=np.int64) * n
+        bad = T.cuda.Stream()
+        t0 = time.perf_counter()
+        rac.enforce_batch([net], items, offs, din, dout, it, st,
+                          flags=TC | rac.TEST_WITHHOLD_ARRIVAL, stream=bad)
+        bad.synchronize()
+        assert time.perf_counter() - t0 < 1.5, "the wait limit under the test hook is 50 ms"
+        assert list(st.cpu().numpy()) == [rac.EBARRIER] * 5
+        good = T.cuda.Stream()
+        rac.enforce_batch([net], items, offs, din, dout, it, st, flags=TC, stream=good)
+        good.synchronize()
+        assert np.array_equal(from_dev(dout).reshape(5, n), want[0])
+        assert list(it.cpu().numpy()) == list(want[1]) and list(st.cpu().numpy()) == list(want[2])
