@@ -5,9 +5,10 @@
 order, and after each `assign` enforce with only that variable changed
 (`tensorAC(Vars, [idx])`, rac_assign_enforce), descending while no domain is
 empty and backtracking otherwise.  The states of the levels stay on the
-device; the host reads a state back only to apply the variable-ordering
-heuristic, which the paper leaves open (here: smallest domain of size > 1,
-lowest index first).  Every assignment's sweep count is recorded: it is the
+device; after each enforcement one read brings the child state, its sweep
+count and its status back together (the variable-ordering heuristic, which
+the paper leaves open, needs the state: smallest domain of size > 1, lowest
+index first).  Every assignment's sweep count is recorded: it is the
 quantity Table 1 reports as #Recurrence.
 """
 from dataclasses import dataclass, field
@@ -33,7 +34,7 @@ class SearchResult:
 def choose_variable(dom):
     """Smallest domain of size > 1, lowest index; None when all are singletons."""
     words = np.ascontiguousarray(dom, dtype=np.uint32)
-    sizes = np.unpackbits(words.view(np.uint8)).reshape(-1, 32).sum(1)
+    sizes = np.bitwise_count(words)
     open_vars = np.flatnonzero(sizes > 1)
     if open_vars.size == 0:
         return None
@@ -49,18 +50,22 @@ def dfs(net, dom0, max_nodes=10_000, stream=None, flags=0, hook=None):
     dev = torch.device("cuda", torch.cuda.current_device())
     n = net.n
     res = SearchResult()
-    levels = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(n + 1)]
-    it = torch.empty(1, dtype=torch.int32, device=dev)
-    st = torch.empty(1, dtype=torch.int32, device=dev)
-    levels[0].copy_(torch.from_numpy(np.ascontiguousarray(dom0, dtype=np.uint32).view(np.int32)))
-    enforce(net, levels[0], levels[0], it, st, flags=flags, stream=stream)
-    res.root_iterations = int(it.item())
-    res.root_status = int(st.item())
+    # a level's buffer: its n domain words, then the sweep count and status of
+    # the enforcement that produced it, so that one read brings all three back
+    bufs = [torch.empty(n + 2, dtype=torch.int32, device=dev) for _ in range(n + 1)]
+    levels = [b[:n] for b in bufs]
+    bufs[0][:n].copy_(torch.from_numpy(np.ascontiguousarray(dom0, dtype=np.uint32).view(np.int32)))
+    enforce(net, levels[0], levels[0], bufs[0][n:n + 1], bufs[0][n + 1:], flags=flags,
+            stream=stream)
+    host = bufs[0].cpu().numpy()
+    res.root_iterations = int(host[n])
+    res.root_status = int(host[n + 1])
     if res.root_status != OK:
         return res
+    doms = {0: host[:n].view(np.uint32)}
 
     def rec(level):
-        dom = levels[level].cpu().numpy().view(np.uint32)
+        dom = doms[level]
         var = choose_variable(dom)
         if var is None:
             res.solution = dom.copy()
@@ -74,11 +79,14 @@ def dfs(net, dom0, max_nodes=10_000, stream=None, flags=0, hook=None):
             res.nodes += 1
             if hook:
                 hook("before")
-            assign_enforce(net, levels[level], levels[level + 1], var, value, it, st,
-                           flags=flags, stream=stream)
+            nxt = bufs[level + 1]
+            assign_enforce(net, levels[level], levels[level + 1], var, value, nxt[n:n + 1],
+                           nxt[n + 1:], flags=flags, stream=stream)
             if hook:
                 hook("after")
-            iters, status = int(it.item()), int(st.item())
+            host = nxt.cpu().numpy()  # the child state, its sweep count and status
+            iters, status = int(host[n]), int(host[n + 1])
+            doms[level + 1] = host[:n].view(np.uint32)
             res.steps.append((level, var, value, iters, status))
             if status == OK and rec(level + 1):
                 return True
