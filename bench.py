@@ -997,16 +997,18 @@ def run_search(args):
         raise SystemExit("the search ended after %d assignments: no step to time" % res.nodes)
     dev_s = sum(a.elapsed_time(b) for a, b in events[W:]) / 1000.0
     per_step_s = max_over_ranks(dev_s / len(timed))
-    # end to end: the same search from the host domains, no flushes, wall clock
+    # end to end: the same search from the host domains through the
+    # library's own search loop (rac_search), no flushes, wall clock
     gc.collect()
     gc.disable()
     t0 = time.perf_counter()
-    res2 = dfs(net, racgen_full(x), max_nodes=W + K, stream=stream, flags=args.flags)
+    res2 = rac.search(net, racgen_full(x), max_nodes=W + K, flags=args.flags, stream=stream)
     wall = time.perf_counter() - t0
     gc.enable()
-    wall_per_step = max_over_ranks(wall / max(1, res2.nodes))
-    if res2.steps != res.steps:
-        raise SystemExit("the untimed search took other steps than the timed one")
+    wall_per_step = max_over_ranks(wall / max(1, res2["nodes"]))
+    if [tuple(int(v) for v in r) for r in res2["steps"]] != \
+            [tuple(int(v) for v in r) for r in res.steps]:
+        raise SystemExit("the library's search took other steps than the timed one")
     peaks = measured_peaks()
     hbm_peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6400.0
     alg = _search_alg_bytes(x, timed) / len(timed)
@@ -1033,10 +1035,11 @@ def run_search(args):
             "clocks": clk.summary(),
             "gpu_launches": len(timed),
             "e2e": {"value": world / wall_per_step, "unit": "fixpoints/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": int(x.n * 4 + 8), "steps": res2.nodes,
-                    "note": "the whole search on the host's clock: an assignment's inputs are "
-                            "launch parameters (the parent state stays on the device); the "
-                            "child state and its sweep count are read back for the next choice"}}
+                    "d2h_bytes_per_step": int(x.n * 4 + 8), "steps": res2["nodes"],
+                    "note": "the whole search on the host's clock through rac_search: an "
+                            "assignment's inputs are launch parameters (the parent state stays "
+                            "on the device); the kernel writes the child state, its sweep count "
+                            "and status into pinned memory for the next choice"}}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_search_baseline(x)
     if rank == 0:

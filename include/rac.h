@@ -235,6 +235,41 @@ RAC_API rac_status rac_assign_enforce(const rac_network *net, const uint32_t *do
                                       uint32_t flags, rac_stream_t stream);
 
 /*
+ * rac_search -- the backtrack search of Algorithm 2 (`main` / `dfs`): enforce
+ * arc consistency on the initial domains (`tensorAC(Vars, all)`), then pick
+ * a variable, try its values in increasing order, and after each `assign`
+ * enforce with only that variable changed (`tensorAC(Vars, [idx])`, as
+ * rac_assign_enforce), descending while no domain is empty and backtracking
+ * otherwise, until every domain is a singleton (a solution), every
+ * assignment has been tried, or max_nodes assignments have been made.  The
+ * variable order, which the paper leaves open (`heuristics()`), is the
+ * smallest domain of size > 1, lowest index first.  The loop runs on the
+ * host inside the library; every enforcement is one kernel launch that
+ * writes its results straight into pinned host memory, and the call returns
+ * when the search ends (it waits for `stream`).
+ *
+ *  dom0        HOST, n_vars words: the initial domains.
+ *  max_nodes   assignments to make at most (>= 0).
+ *  flags       RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL, for every enforcement.
+ *  solution    HOST, n_vars words: receives the solution when one is found.
+ *  found       HOST int32: 1 when a solution was found, else 0.
+ *  exhausted   HOST int32: 1 when the search stopped at max_nodes.
+ *  nodes       HOST int64: assignments made.
+ *  root        HOST, 2 int32: sweep count and status of the root enforcement
+ *              (the search stops at once unless the status is RAC_OK).
+ *  steps       HOST, 5 x step_cap int32, or NULL with step_cap 0: per
+ *              assignment in order, (level, variable, value, sweep count,
+ *              status); level 0 is the first assignment below the root.
+ * Device memory: one n_vars-word state per search level (allocated as the
+ * search deepens, freed on return) and a pinned staging buffer.
+ * Errors: RAC_EINVAL, RAC_ENOMEM, RAC_ECUDA.
+ */
+RAC_API rac_status rac_search(const rac_network *net, const uint32_t *dom0, int64_t max_nodes,
+                              uint32_t flags, rac_stream_t stream, uint32_t *solution,
+                              int32_t *found, int32_t *exhausted, int64_t *nodes, int32_t *root,
+                              int32_t *steps, int64_t step_cap);
+
+/*
  * rac_enforce_batch -- many independent (network, domain state) items.
  *
  *  nets          HOST array of network handles.

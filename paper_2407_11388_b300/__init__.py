@@ -47,7 +47,7 @@ ABI_FUNCTIONS = ("rac_create_network", "rac_create_network_u8", "rac_destroy", "
                  "rac_predictor_num_params", "rac_predictor_create", "rac_predictor_destroy",
                  "rac_predictor_set_weights", "rac_predictor_get_weights",
                  "rac_predictor_gradient", "rac_predictor_train", "rac_predictor_predict",
-                 "rac_enforce_learned", "rac_combine_partials")
+                 "rac_enforce_learned", "rac_combine_partials", "rac_search")
 NOALLOC_MAX_VARS = 65536
 PREDICTOR_FEATURES = 8
 PREDICTOR_PARAMS = 4801
@@ -100,6 +100,8 @@ def lib():
         L.rac_plan_destroy.argtypes = [vp]
         L.rac_assign_enforce.restype = i32
         L.rac_assign_enforce.argtypes = [vp, vp, vp, i32, i32, vp, vp, i32, u32, vp]
+        L.rac_search.restype = i32
+        L.rac_search.argtypes = [vp, vp, i64, u32, vp, vp, vp, vp, vp, vp, vp, i64]
         L.rac_combine_partials.restype = i32
         L.rac_combine_partials.argtypes = [i32, i32, vp, vp, vp, vp, vp]
         L.rac_network_info.restype = i32
@@ -279,6 +281,29 @@ def enforce_noalloc(net, dom_in, dom_out, iterations, status, max_sweeps=0, flag
     _check(lib().rac_enforce_noalloc(net.handle, _ptr(dom_in), _ptr(dom_out), _ptr(iterations),
                                      _ptr(status), int(max_sweeps), int(flags), _stream(stream)),
            "rac_enforce_noalloc")
+
+
+def search(net, dom0, max_nodes=10_000, flags=0, stream=None):
+    """rac_search: Algorithm 2's backtrack search with the loop inside the
+    library.  dom0: host uint32 words (n).  Returns a dict: solution (uint32
+    words or None), found, exhausted, nodes, root (sweeps, status) and steps
+    (nodes x 5 int32: level, variable, value, sweep count, status)."""
+    dom0 = np.ascontiguousarray(dom0, dtype=np.uint32).reshape(-1)
+    if dom0.size != net.n:
+        raise RacError(EINVAL, "search: dom0 must have n words")
+    sol = np.zeros(net.n, np.uint32)
+    found, exhausted = ctypes.c_int32(), ctypes.c_int32()
+    nodes = ctypes.c_int64()
+    root = np.zeros(2, np.int32)
+    steps = np.zeros((max(int(max_nodes), 1), 5), np.int32)
+    _check(lib().rac_search(net.handle, dom0.ctypes.data, int(max_nodes), int(flags),
+                            _stream(stream), sol.ctypes.data, ctypes.byref(found),
+                            ctypes.byref(exhausted), ctypes.byref(nodes), root.ctypes.data,
+                            steps.ctypes.data, int(max_nodes)),
+           "rac_search")
+    return {"solution": sol if found.value else None, "found": bool(found.value),
+            "exhausted": bool(exhausted.value), "nodes": int(nodes.value),
+            "root": (int(root[0]), int(root[1])), "steps": steps[:nodes.value].copy()}
 
 
 def combine_partials(partials, dom_prev, dom_next, flags, stream=None):

@@ -167,6 +167,8 @@ bool check_device(const rac_network *net) {
   return true;
 }
 
+}  // namespace
+
 LaunchParams base_params(const rac_network *net, Workspace *w, int n_states, int32_t max_sweeps,
                          uint32_t flags) {
   LaunchParams P = {};
@@ -193,6 +195,8 @@ LaunchParams base_params(const rac_network *net, Workspace *w, int n_states, int
   for (int32_t i = 0; i < P.n_first; ++i) P.first[i] = net->first[size_t(i)];
   return P;
 }
+
+namespace {
 
 constexpr uint32_t kKnownFlags =
     RAC_STOP_ON_WIPEOUT | RAC_INCREMENTAL | RAC_KERNEL_TENSOR | RAC_TEST_WITHHOLD_ARRIVAL;

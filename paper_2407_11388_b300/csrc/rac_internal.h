@@ -290,6 +290,11 @@ void set_error(const std::string &msg);
 void set_error_nothrow(const char *msg) noexcept;
 rac_status cuda_fail(cudaError_t e, const char *what);
 NetDev net_dev(const rac_network *net);
+// Launch parameters of n_states states of net on workspace w: the flag
+// slots, sync words and first slab descriptors; the caller sets the domain,
+// result and seed fields.
+LaunchParams base_params(const rac_network *net, Workspace *w, int n_states, int32_t max_sweeps,
+                         uint32_t flags);
 // Launch the bit-packed kernel for P (grid sized by the callee).
 rac_status launch_bits(const LaunchParams &P, cudaStream_t stream);
 // Launch the tensor-core kernel for P (at most 128 states; P.net.fp8 set).
