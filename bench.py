@@ -1002,7 +1002,7 @@ def run_search(args):
     gc.collect()
     gc.disable()
     t0 = time.perf_counter()
-    res2 = rac.search(net, racgen_full(x), max_nodes=W + K, flags=args.flags, stream=stream)
+    res2 = rac.run_search(net, racgen_full(x), max_nodes=W + K, flags=args.flags, stream=stream)
     wall = time.perf_counter() - t0
     gc.enable()
     wall_per_step = max_over_ranks(wall / max(1, res2["nodes"]))

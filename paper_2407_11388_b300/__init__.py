@@ -283,7 +283,7 @@ def enforce_noalloc(net, dom_in, dom_out, iterations, status, max_sweeps=0, flag
            "rac_enforce_noalloc")
 
 
-def search(net, dom0, max_nodes=10_000, flags=0, stream=None):
+def run_search(net, dom0, max_nodes=10_000, flags=0, stream=None):
     """rac_search: Algorithm 2's backtrack search with the loop inside the
     library.  dom0: host uint32 words (n).  Returns a dict: solution (uint32
     words or None), found, exhausted, nodes, root (sweeps, status) and steps

@@ -77,7 +77,7 @@ def test_library_search_matches_oracle(seed, n, d, p, t):
         want = oracle_dfs(n, d, net_np.scope, net_np.rel, dom0, max_nodes=budget)
         with rac.Network(n, d, net_np.scope, net_np.rel) as net:
             for flags in (0, rac.INCREMENTAL):
-                got = rac.search(net, dom0, max_nodes=budget, flags=flags)
+                got = rac.run_search(net, dom0, max_nodes=budget, flags=flags)
                 assert got["root"] == tuple(want["root"])
                 assert [tuple(int(v) for v in r) for r in got["steps"]] == \
                     [tuple(int(v) for v in r) for r in want["steps"]]
@@ -96,11 +96,11 @@ def test_library_search_solves_and_reports_a_wiped_root():
     scope, rel = chain(n, d)
     dom0 = np.full(n, full_word(d), np.uint32)
     with rac.Network(n, d, scope, rel) as net:
-        got = rac.search(net, dom0, max_nodes=100)
+        got = rac.run_search(net, dom0, max_nodes=100)
         want = oracle_dfs(n, d, scope, rel, dom0, max_nodes=100)
         assert got["found"] and np.array_equal(got["solution"], want["solution"])
         assert got["nodes"] == len(want["steps"])
     scope, rel = chain(20, 8)  # d < n: the root wipes out
     with rac.Network(20, 8, scope, rel) as net:
-        got = rac.search(net, np.full(20, 0xFF, np.uint32), max_nodes=100)
+        got = rac.run_search(net, np.full(20, 0xFF, np.uint32), max_nodes=100)
         assert got["root"][1] == rac.WIPEOUT and got["nodes"] == 0 and not got["found"]
