@@ -6,6 +6,7 @@
 // (the instance the host entry point uses), so the loop waits on that word
 // and never synchronises the stream.  The levels' states stay on the device;
 // the host keeps a copy of each for the variable choice.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <string>
@@ -30,12 +31,15 @@ int choose_variable(const uint32_t *dom, int n) {
 }
 
 struct SearchBuffers {
-  std::vector<uint32_t *> levels;  // device, n words each (level k: after k assignments)
-  int32_t *res = nullptr;          // device: iterations, status
-  uint32_t *pin = nullptr;         // pinned host: n words, iterations, status, completion
+  // device, n words per level (level k: the state after k assignments), in
+  // blocks of levels allocated as the search deepens
+  std::vector<uint32_t *> blocks;
+  std::vector<uint32_t *> levels;
+  int32_t *res = nullptr;   // device: iterations, status
+  uint32_t *pin = nullptr;  // pinned host: n words, iterations, status, completion
   uint32_t *pin_dev = nullptr;
   ~SearchBuffers() {
-    for (uint32_t *p : levels) cudaFree(p);
+    for (uint32_t *p : blocks) cudaFree(p);
     cudaFree(res);
     cudaFreeHost(pin);
   }
@@ -78,14 +82,21 @@ extern "C" rac_status rac_search(const rac_network *net, const uint32_t *dom0, i
 
   SearchBuffers buf;
   const size_t words = size_t(n);
+  // levels come in blocks (the first of up to 64 MiB, then doubling), so the
+  // loop seldom allocates (an allocation waits for the device)
   auto level_buffer = [&](size_t k) -> uint32_t * {
     while (buf.levels.size() <= k) {
+      const size_t have = buf.levels.size();
+      size_t count = have ? have : std::max<size_t>(1, (size_t(64) << 20) / (words * 4 + 1));
+      count = std::min(count, size_t(n) + 1 - std::min(have, size_t(n)));
+      count = std::max<size_t>(count, 1);
       uint32_t *p = nullptr;
-      if (cudaMalloc(&p, words * sizeof(uint32_t)) != cudaSuccess) {
+      if (cudaMalloc(&p, count * words * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
       }
-      buf.levels.push_back(p);
+      buf.blocks.push_back(p);
+      for (size_t i = 0; i < count; ++i) buf.levels.push_back(p + i * words);
     }
     return buf.levels[k];
   };
