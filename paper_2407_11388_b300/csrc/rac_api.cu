@@ -712,9 +712,6 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
     }
     w0->host_pin_dev = static_cast<uint32_t *>(dp);
     w0->host_cap = total;
-    // the completion word starts at the number of direct launches this
-    // workspace has completed (Sync::done_seq on the device)
-    w0->host_pin[total - 1] = w0->host_seq;
   }
   uint32_t *d_dom = w0->host_dom;
   int32_t *d_res = reinterpret_cast<int32_t *>(d_dom + words);
@@ -755,6 +752,10 @@ rac_status rac_enforce_host(const rac_network *net, int32_t n_states, const uint
   };
   // the caller's buffers meet only host copies
   std::memcpy(pin, dom_in, words * 4);
+  // this call's completion word (its place depends on n_states) starts at
+  // the number of launches with host results the workspace has completed
+  // (Sync::done_seq on the device), whatever an earlier call left there
+  reinterpret_cast<volatile uint32_t *>(w0->host_pin)[total - 1] = w0->host_seq;
   const bool same = w0->graph_states == n_states && w0->graph_max_sweeps == max_sweeps &&
                     w0->graph_flags == flags;
   if (same && w0->host_graph) {

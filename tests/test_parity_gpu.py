@@ -460,3 +460,23 @@ def test_grid_cap_does_not_change_results(ctas):
         T.cuda.synchronize()
         assert np.array_equal(from_dev(dout), want[0][0])
         assert (int(its.item()), int(sts.item())) == (want[1][0], want[2][0])
+
+
+def test_host_entry_point_with_changing_state_counts():
+    """rac_enforce_host on one (network, stream) with 3, 1, 2, 3, 1 states in
+    turn: the results of up to three states are published with a completion
+    number whose place in the pinned buffer moves with the state count; every
+    call must wait for its own launch."""
+    n, d = 300, 12
+    net_np = racgen.random_network(17, 0, n, d, 0.5, 0.5)
+    pool = np.array([racgen.assignment_state(17, 0, s, n, d) for s in range(12)])
+    want = oracle_enforce(n, d, net_np.scope, net_np.rel, pool)
+    with rac.Network(n, d, net_np.scope, net_np.rel) as net:
+        pos = 0
+        for B in (3, 1, 2, 3, 1, 2):
+            sel = np.arange(pos, pos + B) % len(pool)
+            pos += B
+            out, it, st = rac.enforce_host(net, pool[sel])
+            assert np.array_equal(out.reshape(B, n), want[0][sel]), B
+            assert list(it) == list(want[1][sel]) and list(st) == list(want[2][sel])
+    assert want[1].max() >= 3
