@@ -460,6 +460,7 @@ __device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char
     }
   }
   jc += uint32_t(n_jobs);
+  __syncwarp();                   // the single-lane roles rejoin their warps
   named_bar(kConsumersBar, nct);  // S.dom free for the next slab
 }
 
