@@ -39,6 +39,11 @@ WORKLOADS = {
     "dense_n500_d20": dict(n=500, d=20, density=1.0, tightness=0.35, states="full", n_states=1),
     "rb_n50_d10": dict(n=50, d=10, density=0.5, tightness=0.3, states="full", n_states=1),
     "dense_n2000_d32": dict(n=2000, d=32, density=0.9, tightness=0.3, states="full", n_states=1),
+    # the same graph at narrower domains: single-state launches that stream a
+    # store larger than L2, where packed relation rows (--layout packed) read
+    # 13 / 18 words per relation instead of 20 / 24
+    "dense_n2000_d20": dict(n=2000, d=20, density=0.9, tightness=0.3, states="full", n_states=1),
+    "dense_n2000_d24": dict(n=2000, d=24, density=0.9, tightness=0.3, states="full", n_states=1),
     "n1000_d24_b32": dict(n=1000, d=24, density=0.8, tightness=0.3, states="assign",
                           n_states=32),
     "n1000_d24_b64": dict(n=1000, d=24, density=0.8, tightness=0.3, states="assign",
@@ -76,7 +81,16 @@ def parse():
     p.add_argument("--flags", type=int, default=0, help="enforce flags (1 stop, 2 incremental)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--layout", default="auto", choices=["auto", "words", "packed"],
+                   help="relation rows: the tuned table's choice, a word per row, or packed")
+    p.add_argument("--rows", type=int, default=None,
+                   help="tile rows (a power of two); default: the tuned table's choice")
     return p.parse_args()
+
+
+def profile_key(args):
+    """The traffic.json entry of this run's workload and relation layout."""
+    return args.workload + ("+packed" if getattr(args, "packed", False) else "")
 
 
 def make_inputs(wl, seed):
@@ -161,8 +175,8 @@ def _code_only(text):
 # The sources a kernel's recorded counters depend on: the kernel, the device
 # helpers and the host code that lays out the relation store and launches it.
 KERNEL_SOURCES = {
-    "rac_bits_kernel": ("rac_bits_kernel.cu", "rac_device.cuh", "rac_internal.h",
-                        "rac_mlp.cuh", "rac_api.cu"),
+    "rac_bits_kernel": ("rac_bits_kernel.cu", "rac_bits_packed.cu", "rac_device.cuh",
+                        "rac_internal.h", "rac_mlp.cuh", "rac_api.cu"),
     "rac_batch_kernel": ("rac_batch_kernel.cu", "rac_plan.cu", "rac_device.cuh",
                          "rac_internal.h", "rac_api.cu"),
 }
@@ -506,8 +520,15 @@ class Prepared:
         self.nets_np, self.items, self.offs, self.doms = nets_np, items, offs, doms
         self.B = len(items)
         per_launch = spec.get("states_per_net", spec.get("n_states", 1))
-        self.nets = [rac.Network(x.n, x.d, x.scope, x.rel, states=per_launch,
-                                 plan=len(nets_np) > 1) for x in nets_np]
+        layout = rac.LAYOUT_BITS | (rac.LAYOUT_PACKED if args.layout == "packed" else 0)
+        self.nets = [rac.Network(x.n, x.d, x.scope, x.rel, layout=layout, states=per_launch,
+                                 plan=len(nets_np) > 1, rows=args.rows,
+                                 packed=None if args.layout == "auto" else args.layout == "packed")
+                     for x in nets_np]
+        args.packed = any(net.info()["words_per_relation"] < (x.d + 3) // 4 * 4
+                          for net, x in zip(self.nets, nets_np))
+        self.cfg["relation_rows"] = "packed" if args.packed else "a word per row"
+        self.cfg["tile_rows"] = sorted({int(net.info()["rows_per_slab"]) for net in self.nets})
         self.flat = flat
         self.din = torch.from_numpy(np.ascontiguousarray(flat).view(np.int32)).to(dev)
         self.dout = torch.empty_like(self.din)
@@ -862,7 +883,7 @@ def run_ours(args):
     hbm_peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6400.0
     alg_bytes_per_launch = W.alg_bytes(its)
     achieved = alg_bytes_per_launch / per_step_s / 1e9
-    traffic = traffic_from_profiles(args.workload)
+    traffic = traffic_from_profiles(profile_key(args))
     clocks = clk.summary()
     kernel = "rac_batch_kernel" if W.plan is not None else (
         "rac_tc_kernel" if args.flags & 0x10 else "rac_bits_kernel")
@@ -880,7 +901,7 @@ def run_ours(args):
         # many states: the per-state support tests bound the launch, not the
         # one read of the store per sweep; the binding roofline is the SM
         # issue rate (one warp instruction per cycle per scheduler)
-        roof = issue_roofline(args.workload, per_step_s, torch, dev, peaks, kernel)
+        roof = issue_roofline(profile_key(args), per_step_s, torch, dev, peaks, kernel)
         roof["hbm"] = hbm_line
     line = {"metric": METRIC, "value": value, "unit": "fixpoints/s", "n_gpus": world,
             "steps": K, "warmup": warm + RESUME_STEPS, "ms_per_step": per_step_s * 1000.0,

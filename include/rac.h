@@ -79,13 +79,23 @@ typedef int32_t rac_status;
  * slab rows (1.1 GB for n = 1000).  Without it the first RAC_KERNEL_TENSOR
  * call on the network builds it (an allocation and a wait on its stream). */
 #define RAC_LAYOUT_FP8 0x2u
+/* Packed relation rows: row a of a relation takes bits [w a, w a + w) of the
+ * relation's words, w = round_up(d, 4), instead of a word of its own, so a
+ * relation takes ceil(w^2 / 32) words instead of w (d = 20: 13 words instead
+ * of 20; d = 24: 18 instead of 24) and every sweep reads that much less.
+ * Each row is shifted out of its word (or out of two, when it straddles
+ * them) before the support test, one more instruction per row.  Every entry
+ * point and kernel reads both layouts; the results and sweep counts do not
+ * depend on it.  For d > 28 a row is a whole word already and the flag
+ * changes nothing. */
+#define RAC_LAYOUT_PACKED 0x4u
 /* Rows of the relation tiles ("slabs": 32 column variables x `rows` row
  * variables of one block pair, read as one unit): RAC_LAYOUT_ROWS(l) asks
  * for 2^l rows, 1 <= l <= 5 (a tile's header of 2 x rows words keeps the
  * relations and the tile 16-byte aligned only from 2 rows on); without it the
  * largest power of two whose slab fits the kernels' 32 KiB staging buffer
- * (rows x 32 x round_up(d, 4) x 4 bytes) is used.  The result and the sweep
- * count do not depend on it. */
+ * (rows x 32 x 4 bytes x the words of a relation) is used.  The result and
+ * the sweep count do not depend on it. */
 #define RAC_LAYOUT_ROWS(l) ((uint32_t)((l) + 1) << 8)
 #define RAC_LAYOUT_ROWS_MASK 0xF00u
 /* CTAs of the network's persistent launches (the bit-packed kernel):
@@ -151,8 +161,9 @@ typedef int32_t rac_status;
  *             zero.  Variables with no constraint between them are
  *             unconstrained (only real constraints are in C_x).
  *  layout_flags  RAC_LAYOUT_BITS (0 means the same), optionally |
- *             RAC_LAYOUT_ROWS(l); a tile too large for the staging buffer is
- *             rejected with RAC_EINVAL.
+ *             RAC_LAYOUT_PACKED, RAC_LAYOUT_FP8, RAC_LAYOUT_ROWS(l),
+ *             RAC_LAYOUT_MAX_CTAS(c); a tile too large for the staging
+ *             buffer is rejected with RAC_EINVAL.
  *  out        receives the network handle.
  *
  * The library keeps its own copy; the host arrays may be freed on return.
@@ -554,7 +565,8 @@ RAC_API rac_status rac_enforce_learned(const rac_network *net, int32_t n_states,
  * rac_network_info -- describe a network: writes up to n_info int64 values
  * to info, in this order: n_vars, d, n_cons, relation-slab bytes on the
  * device, number of relation slabs, rows per slab, words per stored relation
- * row group (d rounded up to a multiple of 4).  Returns the number written.
+ * (round_up(d, 4), or ceil(round_up(d, 4)^2 / 32) with RAC_LAYOUT_PACKED and
+ * d <= 28).  Returns the number written.
  */
 RAC_API int32_t rac_network_info(const rac_network *net, int64_t *info, int32_t n_info);
 

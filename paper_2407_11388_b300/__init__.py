@@ -22,6 +22,7 @@ OK, WIPEOUT = 0, 1
 EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBARRIER, ENOTSUP = -1, -2, -3, -4, -5, -6
 LAYOUT_BITS = 0x1
 LAYOUT_FP8 = 0x2  # the tensor-core kernel's FP8 operand store, built at creation
+LAYOUT_PACKED = 0x4  # relation rows packed back to back (d <= 28: fewer bytes per sweep)
 
 
 def LAYOUT_ROWS(log2_rows):
@@ -175,14 +176,16 @@ class Network:
     R_xy[a][b] (packed by the library: rac_create_network_u8)."""
 
     def __init__(self, n, d, scope, rel, layout=LAYOUT_BITS, rows=None, max_ctas=None,
-                 states=None, plan=False):
+                 states=None, plan=False, packed=None):
         """rows: tile rows (a power of two); max_ctas: grid cap of the
-        network's launches.  None takes the autotuned table's choice for
-        this (d, density, states per launch) if one is installed
-        (tile_table.json), else the library default; `states` is the number
-        of domain states the caller expects to enforce per launch (1 if
-        not given), `plan` whether the network is to be enforced with others
-        in multi-network plans."""
+        network's launches; packed: relation rows packed back to back
+        (LAYOUT_PACKED) or a word each.  None takes the autotuned table's
+        choice for this (d, density, states per launch) if one is installed
+        (tile_table.json), else the library default (a word per row unless
+        `layout` has LAYOUT_PACKED); `states` is the number of domain states
+        the caller expects to enforce per launch (1 if not given), `plan`
+        whether the network is to be enforced with others in multi-network
+        plans."""
         scope = np.ascontiguousarray(scope, dtype=np.int32).reshape(-1, 2)
         rel = np.asarray(rel)
         if rel.ndim == 3:
@@ -197,11 +200,18 @@ class Network:
             create = lib().rac_create_network
         if rel.shape[0] != scope.shape[0]:
             raise RacError(EINVAL, "scope and rel disagree on the number of constraints")
+        if packed is None and not (int(layout) & LAYOUT_PACKED):
+            from .autotune import table_packed
+            packed = table_packed(int(d), scope.shape[0] / max(1.0, n * (n - 1) / 2.0),
+                                  int(states or 1), kind="plan" if plan else "single")
+        if packed:
+            layout = int(layout) | LAYOUT_PACKED
         if (rows is None and not (int(layout) & 0xF00)) or \
                 (max_ctas is None and not (int(layout) & 0xFFFF0000)):
             from .autotune import table_choice
             t_rows, t_ctas = table_choice(int(d), scope.shape[0] / max(1.0, n * (n - 1) / 2.0),
-                                          int(states or 1), kind="plan" if plan else "single")
+                                          int(states or 1), kind="plan" if plan else "single",
+                                          packed=bool(int(layout) & LAYOUT_PACKED))
             if rows is None and not (int(layout) & 0xF00):
                 rows = t_rows
             if max_ctas is None and not (int(layout) & 0xFFFF0000):

@@ -1,4 +1,5 @@
-"""Autotuned launch table: tile rows and grid cap per (d, density, states).
+"""Autotuned launch table: tile rows, grid cap and relation layout per (d,
+density, states).
 
 A network's relations are stored in tiles ("slabs") of 32 column variables by
 `rows` row variables of one block pair; the kernels stream one tile at a time
@@ -7,19 +8,21 @@ persistent launch owns tiles c, c + G, ...  (RAC_LAYOUT_MAX_CTAS caps G).
 Small tiles spread the work more evenly over the CTAs and let Proposition 2
 skip finer pieces; large tiles pay the per-tile overhead (stage hand-off,
 domain staging, pipeline latency) fewer times.  A smaller grid makes each
-sweep's grid barrier cheaper and leaves each CTA more tiles to overlap.  The
-best pair depends on d, the density, the number of states per launch and the
-GPU, so it is measured:
+sweep's grid barrier cheaper and leaves each CTA more tiles to overlap.
+Packed relation rows (RAC_LAYOUT_PACKED, d <= 28) move fewer bytes per sweep
+and let taller tiles fit a stage, for one more instruction per row of every
+support test.  The best choice depends on d, the density, the number of
+states per launch and the GPU, so it is measured:
 
     python -m paper_2407_11388_b300.autotune [--out FILE] [--runs 20]
 
-For every (d, density, states) bucket it times every admissible row count
-and grid cap on seeded synthetic networks of the bucket (120, 360 and 700
+For every (d, density, states) bucket it times every admissible row count,
+grid cap and relation layout on seeded synthetic networks of the bucket (120, 360 and 700
 variables at the bucket's middle d and density, tightness 0.3, assignment
 states; one launch per network -- rac_enforce for one state, rac_enforce_batch
 for more -- CUDA events, L2 flushed before each launch, median of `runs`),
-and, for networks enforced together, every row count of one multi-network
-plan launch of the three networks with 64 states each; it writes the
+and, for networks enforced together, every row count and layout of one
+multi-network plan launch of the three networks with 64 states each; it writes the
 fastest choice per bucket to a JSON table.  Network() consults that table
 (tile_table.json next to this file) for what its caller leaves open.
 """
@@ -41,9 +44,16 @@ STAGE_BYTES = 32768  # relation bytes of one tile the kernels can stage
 _table = None
 
 
-def admissible_rows(d):
-    dp = (d + 3) & ~3
-    return [r for r in (2, 4, 8, 16, 32) if r * 32 * dp * 4 <= STAGE_BYTES]
+def words_per_relation(d, packed=False):
+    """Stored words of one relation: a word per row (round_up(d, 4) rows), or
+    packed rows (4q rows of 4q bits, q = ceil(d / 4)) for d <= 28."""
+    q = (d + 3) // 4
+    return (16 * q * q + 31) // 32 if packed and q < 8 else 4 * q
+
+
+def admissible_rows(d, packed=False):
+    w = words_per_relation(d, packed)
+    return [r for r in (2, 4, 8, 16, 32) if r * 32 * w * 4 <= STAGE_BYTES]
 
 
 def load_table(path=TABLE):
@@ -60,10 +70,7 @@ def load_table(path=TABLE):
     return _table
 
 
-def table_choice(d, density, states=1, path=TABLE, kind="single"):
-    """(rows, max_ctas) tuned for this shape; None for what the table does
-    not fix (the library default).  kind: "single" for a network enforced in
-    launches of its own, "plan" for one enforced in multi-network plans."""
+def _entry(d, density, states, path, kind):
     for e in load_table(path).get("entries", []):
         if e.get("kind", "single") != kind:
             continue
@@ -71,9 +78,28 @@ def table_choice(d, density, states=1, path=TABLE, kind="single"):
             continue
         if not e.get("st_lo", 1) <= states <= e.get("st_hi", 1 << 30):
             continue
-        r = int(e["rows"])
-        return (r if r in admissible_rows(d) else None), e.get("max_ctas")
-    return None, None
+        return e
+    return None
+
+
+def table_choice(d, density, states=1, path=TABLE, kind="single", packed=False):
+    """(rows, max_ctas) tuned for this shape; None for what the table does
+    not fix (the library default).  kind: "single" for a network enforced in
+    launches of its own, "plan" for one enforced in multi-network plans;
+    packed: the relation layout the network is created with (the tuned rows
+    are taken only when they fit its tiles)."""
+    e = _entry(d, density, states, path, kind)
+    if e is None:
+        return None, None
+    r = int(e["rows"])
+    return (r if r in admissible_rows(d, packed) else None), e.get("max_ctas")
+
+
+def table_packed(d, density, states=1, path=TABLE, kind="single"):
+    """Whether the table found packed relation rows faster for this shape
+    (False where it has no entry or did not time them)."""
+    e = _entry(d, density, states, path, kind)
+    return bool(e and e.get("packed", False))
 
 
 def table_rows(d, density, states=1, path=TABLE, kind="single"):
@@ -96,16 +122,16 @@ def _bucket_networks(d_lo, d_hi, dens_lo, dens_hi, seed, states):
     return d, dens, nets
 
 
-def time_choice(nets, rows, max_ctas, runs):
+def time_choice(nets, rows, max_ctas, runs, packed=False):
     """Median over runs of the summed time (ms) of one launch per network
-    (all of its states) with this tile height and grid cap."""
+    (all of its states) with this tile height, grid cap and relation layout."""
     import numpy as np
     import torch
     from . import Network, enforce, enforce_batch
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
     total = 0.0
     for x, doms in nets:
-        with Network(x.n, x.d, x.scope, x.rel, rows=rows,
+        with Network(x.n, x.d, x.scope, x.rel, rows=rows, packed=packed,
                      max_ctas=max_ctas if max_ctas is not None else 65535) as h:
             B = len(doms)
             din = torch.from_numpy(np.concatenate(doms).astype(np.uint32).view(np.int32)).cuda()
@@ -136,13 +162,15 @@ def time_choice(nets, rows, max_ctas, runs):
     return total
 
 
-def time_plan(nets, rows, runs):
+def time_plan(nets, rows, runs, packed=False):
     """Median time (ms) of one multi-network plan launch of all states of all
-    networks with tiles of `rows` rows (the batched kernel)."""
+    networks with tiles of `rows` rows (the batched kernel) in the given
+    relation layout."""
     import numpy as np
     import torch
     from . import Network, Plan
-    handles = [Network(x.n, x.d, x.scope, x.rel, rows=rows, max_ctas=65535) for x, _ in nets]
+    handles = [Network(x.n, x.d, x.scope, x.rel, rows=rows, max_ctas=65535, packed=packed)
+               for x, _ in nets]
     items, offs, flat, pos = [], [], [], 0
     for i, (x, doms) in enumerate(nets):
         for dom in doms:
@@ -174,6 +202,11 @@ def time_plan(nets, rows, runs):
     return float(np.median(ts))
 
 
+def _layouts(d):
+    """Relation layouts worth timing: packed rows differ only for d <= 28."""
+    return (False, True) if d <= 28 else (False,)
+
+
 def tune(runs=20, seed=7, out=TABLE, log=print):
     import torch
     entries = []
@@ -182,36 +215,42 @@ def tune(runs=20, seed=7, out=TABLE, log=print):
         for d_lo, d_hi in D_BUCKETS:
             for dens_lo, dens_hi in DENSITY_BUCKETS:
                 d, dens, nets = _bucket_networks(d_lo, d_hi, dens_lo, dens_hi, seed, states)
-                times = {(r, c): time_choice(nets, r, c, runs)
-                         for r in admissible_rows(d) for c in CTA_CAPS}
+                times = {(r, c, pk): time_choice(nets, r, c, runs, pk)
+                         for pk in _layouts(d) for r in admissible_rows(d, pk) for c in CTA_CAPS}
                 best = min(times, key=times.get)
-                default = times[(max(admissible_rows(d)), None)]
-                log("states %d d %2d-%2d density %.1f-%.1f: best rows %d ctas %s (%.3f ms; "
+                default = times[(max(admissible_rows(d)), None, False)]
+                log("states %d d %2d-%2d density %.1f-%.1f: best rows %d ctas %s %s (%.3f ms; "
                     "library default %.3f ms)" % (states, d_lo, d_hi, dens_lo, dens_hi, best[0],
-                                                  best[1], times[best], default))
+                                                  best[1], "packed" if best[2] else "words",
+                                                  times[best], default))
                 entries.append({"d_lo": d_lo, "d_hi": d_hi, "dens_lo": dens_lo,
                                 "dens_hi": dens_hi, "st_lo": st_lo, "st_hi": st_hi,
-                                "rows": best[0], "max_ctas": best[1],
-                                "ms": {"%d/%s" % (r, c if c is not None else "all"): round(t, 4)
-                                       for (r, c), t in times.items()}})
+                                "rows": best[0], "max_ctas": best[1], "packed": best[2],
+                                "ms": {"%d/%s/%s" % (r, c if c is not None else "all",
+                                                     "packed" if pk else "words"): round(t, 4)
+                                       for (r, c, pk), t in times.items()}})
     # networks enforced together in multi-network plans (the batched kernel:
     # its grid is every resident CTA, so only the tile rows are tuned)
     for d_lo, d_hi in D_BUCKETS:
         for dens_lo, dens_hi in DENSITY_BUCKETS:
             d, dens, nets = _bucket_networks(d_lo, d_hi, dens_lo, dens_hi, seed, PLAN_STATES)
-            times = {r: time_plan(nets, r, runs) for r in admissible_rows(d)}
+            times = {(r, pk): time_plan(nets, r, runs, pk)
+                     for pk in _layouts(d) for r in admissible_rows(d, pk)}
             best = min(times, key=times.get)
-            log("plan, %d states each: d %2d-%2d density %.1f-%.1f: best rows %d (%.3f ms; "
-                "library default %.3f ms)" % (PLAN_STATES, d_lo, d_hi, dens_lo, dens_hi, best,
-                                              times[best], times[max(admissible_rows(d))]))
+            log("plan, %d states each: d %2d-%2d density %.1f-%.1f: best rows %d %s (%.3f ms; "
+                "library default %.3f ms)" % (PLAN_STATES, d_lo, d_hi, dens_lo, dens_hi, best[0],
+                                              "packed" if best[1] else "words", times[best],
+                                              times[(max(admissible_rows(d)), False)]))
             entries.append({"kind": "plan", "d_lo": d_lo, "d_hi": d_hi, "dens_lo": dens_lo,
-                            "dens_hi": dens_hi, "st_lo": 1, "st_hi": 1 << 30, "rows": best,
-                            "max_ctas": None,
-                            "ms": {str(r): round(t, 4) for r, t in times.items()}})
+                            "dens_hi": dens_hi, "st_lo": 1, "st_hi": 1 << 30, "rows": best[0],
+                            "max_ctas": None, "packed": best[1],
+                            "ms": {"%d/%s" % (r, "packed" if pk else "words"): round(t, 4)
+                                   for (r, pk), t in times.items()}})
     table = {"version": 2, "device": torch.cuda.get_device_name(0),
              "states_timed": {"%d-%d" % k: v for k, v in STATES_TIMED.items()},
              "runs": runs, "seed": seed, "created": time.strftime("%Y-%m-%d %H:%M:%S"),
-             "key": "ms: 'rows/grid cap' -> summed median launch time of the three networks",
+             "key": "ms: 'rows/grid cap/relation rows' -> summed median launch time of the "
+                    "three networks",
              "entries": entries}
     with open(out, "w") as f:
         json.dump(table, f, indent=1)

@@ -31,18 +31,34 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every source to an object in parallel (one nvcc per file), then
+    link the shared library; returns its path."""
     if not force and not _stale():
         return LIB
+    import shutil
+    import tempfile
+    from concurrent.futures import ThreadPoolExecutor
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-shared", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC,
-           "--expt-relaxed-constexpr", "-o", tmp, *sources()]
+    flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+             "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC,
+             "--expt-relaxed-constexpr"]
     if verbose:
-        cmd.insert(1, "-Xptxas")
-        cmd.insert(2, "-v")
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+        flags = ["-Xptxas", "-v", *flags]
+    objdir = tempfile.mkdtemp(prefix="racbuild")
+    try:
+        srcs = sources()
+        objs = [os.path.join(objdir, os.path.basename(p) + ".o") for p in srcs]
+        # the slowest files first, so that the pool ends with the quick ones
+        jobs = sorted(zip(srcs, objs), key=lambda so: -os.path.getsize(so[0]))
+        with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as pool:
+            for f in [pool.submit(subprocess.check_call, [nvcc, *flags, "-c", src, "-o", obj])
+                      for src, obj in jobs]:
+                f.result()
+        tmp = LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+        os.replace(tmp, LIB)
+    finally:
+        shutil.rmtree(objdir, ignore_errors=True)
     return LIB
 
 

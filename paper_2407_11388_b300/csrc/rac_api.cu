@@ -68,6 +68,8 @@ NetDev net_dev(const rac_network *net) {
   N.d = net->d;
   N.dp = net->dp;
   N.q = net->q;
+  N.packed = net->packed;
+  N.rw = net->rw;
   N.nb = net->nb;
   N.rows_per_slab = net->rows_per_slab;
   N.n_slabs = int32_t(net->n_slabs);
@@ -211,10 +213,11 @@ rac_status prepare_for(const rac_network *net, uint32_t flags, cudaStream_t s) {
   return (flags & RAC_KERNEL_TENSOR) ? ensure_fp8(net, s) : RAC_OK;
 }
 
-// Largest power of two rows (<= 32) whose slab fits one ring stage.
-int rows_per_slab_for(int dp) {
+// Largest power of two rows (<= 32) whose slab fits one ring stage, for rw
+// words per stored relation.
+int rows_per_slab_for(int rw) {
   int rows = 32;
-  while (rows > 1 && size_t(rows) * 32 * dp * 4 > size_t(kSlabRelBytes)) rows >>= 1;
+  while (rows > 1 && size_t(rows) * 32 * rw * 4 > size_t(kSlabRelBytes)) rows >>= 1;
   return rows;
 }
 
@@ -252,8 +255,8 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
     set_error("more constraints than pairs of variables (each pair takes at most one)");
     return RAC_EINVAL;
   }
-  if (layout_flags &
-      ~(RAC_LAYOUT_BITS | RAC_LAYOUT_FP8 | RAC_LAYOUT_ROWS_MASK | RAC_LAYOUT_MAX_CTAS_MASK)) {
+  if (layout_flags & ~(RAC_LAYOUT_BITS | RAC_LAYOUT_FP8 | RAC_LAYOUT_PACKED |
+                       RAC_LAYOUT_ROWS_MASK | RAC_LAYOUT_MAX_CTAS_MASK)) {
     set_error("unknown layout flag");
     return RAC_EINVAL;
   }
@@ -261,7 +264,10 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
   const int nb = (n_vars + 31) / 32;
   const int dp = (d + 3) & ~3;
   const int q = dp / 4;
-  int rows = rows_per_slab_for(dp);
+  // packed rows for d <= 28 (at d > 28 a row of 4q = 32 bits is a whole word)
+  const bool packed = (layout_flags & RAC_LAYOUT_PACKED) && q < 8;
+  const int rw = packed ? packed_words(q) : dp;  // words per stored relation
+  int rows = rows_per_slab_for(rw);
   if (const uint32_t code = (layout_flags & RAC_LAYOUT_ROWS_MASK) >> 8) {
     if (code < 2 || code > 6) {
       // l = 0 would give a 2-word tile header: relations and tile sizes that
@@ -270,7 +276,7 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
       return RAC_EINVAL;
     }
     rows = 1 << (code - 1);
-    if (size_t(rows) * 32 * dp * 4 > size_t(kSlabRelBytes)) {
+    if (size_t(rows) * 32 * rw * 4 > size_t(kSlabRelBytes)) {
       set_error("a tile of " + std::to_string(rows) + " rows of width " + std::to_string(d) +
                 " does not fit the 32 KiB staging buffer");
       return RAC_EINVAL;
@@ -329,7 +335,9 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
         ++j;
       const size_t count = j - i;
       const size_t base = relw.size();
-      relw.resize(base + hdr + count * size_t(dp), 0u);
+      // the record padded to whole 16-byte units (packed rows only)
+      const size_t rec_words = (hdr + count * size_t(rw) + 3) & ~size_t(3);
+      relw.resize(base + rec_words, 0u);
       uint32_t *pm = relw.data() + base;
       uint32_t *roff = pm + rows;
       uint32_t *rel = pm + hdr;
@@ -342,18 +350,22 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
         roff[r] = acc;
         acc += uint32_t(__builtin_popcount(pm[r]));
       }
-      // Inside a slab row the relations are stored chunk-major: 16-byte chunk
-      // c (rows 4c..4c+3) of the row's t-th relation sits at chunk c * cnt + t
-      // of the row, so the lanes of a warp, one relation each, read
-      // consecutive chunks (no shared-memory bank conflict).
+      // Inside a slab row the relations are stored chunk-major (whole-word
+      // rows: 16-byte chunk c, rows 4c..4c+3, of the row's t-th relation sits
+      // at chunk c * cnt + t of the row) or word-major (packed rows: word w
+      // of the t-th relation at word w * cnt + t), so the lanes of a warp,
+      // one relation each, read consecutive chunks or words (no shared-memory
+      // bank conflict).
+      uint32_t pk[32];
       for (size_t t = i; t < j; ++t) {
         const uint32_t ri = uint32_t((order[t].first >> 5) & 31u) - row0;
         const uint32_t cnt = uint32_t(__builtin_popcount(pm[ri]));
         const uint32_t rank = uint32_t(t - i) - roff[ri];
-        uint32_t *row_base = rel + size_t(roff[ri]) * dp;
+        uint32_t *row_base = rel + size_t(roff[ri]) * rw;
         // relation rows in the (lo, hi) orientation
         const int64_t c = order[t].second;
         const bool swap = scope[2 * c] > scope[2 * c + 1];
+        if (packed) std::fill(pk, pk + rw, 0u);
         for (int a = 0; a < dp; ++a) {
           uint32_t w = 0;
           if (a < d && !swap) {
@@ -361,8 +373,16 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
           } else if (a < d) {
             for (int b = 0; b < d; ++b) w |= ((rel_bits[c * d + b] >> a) & 1u) << b;
           }
-          row_base[(size_t(a / 4) * cnt + rank) * 4 + (a % 4)] = w;
+          if (!packed) {
+            row_base[(size_t(a / 4) * cnt + rank) * 4 + (a % 4)] = w;
+          } else if (w != 0u) {  // row a at bits [dp a, dp a + dp) of the stream
+            const int off = a * dp, wd = off >> 5, sh = off & 31;
+            pk[wd] |= w << sh;
+            if (sh + dp > 32) pk[wd + 1] |= w >> (32 - sh);
+          }
         }
+        if (packed)
+          for (int wd = 0; wd < rw; ++wd) row_base[size_t(wd) * cnt + rank] = pk[wd];
       }
       // the slab's tightness (disallowed fraction of its d x d relation bits)
       // and density (constraints / (rows x 32))
@@ -376,7 +396,7 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
           float(double(count) / (double(rows) * 32.0))));
       SlabDesc sd;
       sd.rel_off16 = uint32_t(base / 4);
-      sd.nbytes = uint32_t((hdr + count * size_t(dp)) * 4);
+      sd.nbytes = uint32_t(rec_words * 4);
       sd.ij = I | (J << 16);
       sd.rows = row0 | (uint32_t(rows) << 8);
       slabs.push_back(sd);
@@ -400,6 +420,8 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
   net->d = d;
   net->dp = dp;
   net->q = q;
+  net->packed = packed ? 1 : 0;
+  net->rw = rw;
   net->nb = nb;
   net->rows_per_slab = rows;
   net->max_ctas = int32_t(layout_flags >> 16);
@@ -503,7 +525,7 @@ void rac_destroy(rac_network *net) try {
 int32_t rac_network_info(const rac_network *net, int64_t *info, int32_t n_info) try {
   if (!net || !info || n_info <= 0) return 0;
   const int64_t v[7] = {net->n, net->d, net->m, int64_t(net->rel_bytes), net->n_slabs,
-                        net->rows_per_slab, net->dp};
+                        net->rows_per_slab, net->rw};
   const int32_t k = std::min<int32_t>(n_info, 7);
   for (int32_t i = 0; i < k; ++i) info[i] = v[i];
   return k;

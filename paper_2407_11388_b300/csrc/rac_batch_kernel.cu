@@ -115,14 +115,16 @@ __device__ void batch_barrier(const BatchParams &P, unsigned long long *w,
   out = v;
 }
 
-template <int Q>
-__device__ __forceinline__ void support_dispatch_q(const uint4 *mine, uint32_t stride, uint32_t Dx,
-                                                   uint32_t Dy, uint32_t dfull, uint32_t &fwd,
-                                                   uint32_t &rev) {
+// The support test of relation t of a slab row (first relation roff, cnt
+// relations) in relation layout L (rac_device.cuh: whole-word or packed rows).
+template <int L>
+__device__ __forceinline__ void support_dispatch_q(const uint4 *rel, uint32_t roff, uint32_t t,
+                                                   uint32_t cnt, uint32_t Dx, uint32_t Dy,
+                                                   uint32_t dfull, uint32_t &fwd, uint32_t &rev) {
   if (Dx == dfull)
-    support_relation<Q, true>(mine, stride, Dx, Dy, fwd, rev);
+    support_at<L, true>(rel, roff, t, cnt, Dx, Dy, fwd, rev);
   else
-    support_relation<Q, false>(mine, stride, Dx, Dy, fwd, rev);
+    support_at<L, false>(rel, roff, t, cnt, Dx, Dy, fwd, rev);
 }
 
 // Apply a removal to state t: D_k[v] &= keep.  As in kernel (a), only
@@ -166,7 +168,7 @@ __device__ __forceinline__ void batch_mark(BSmem &S, const BatchParams &P, const
 // chunk is read once for both, and the two support tests give the warp
 // independent work.  State u: index t_u, D_k buffer T_u, chg offset co_u,
 // column word Dy_u and row words Dx_ul (lane r: row r).
-template <int Q, bool kTwo>
+template <int L, bool kTwo>
 __device__ __forceinline__ void batch_eval(BSmem &S, const BatchParams &P, const BatchJob &J,
                                            int slot_w, const uint32_t *hdr, const uint4 *rel,
                                            uint32_t I, uint32_t Jb, uint32_t row0, uint32_t nrows,
@@ -184,13 +186,13 @@ __device__ __forceinline__ void batch_eval(BSmem &S, const BatchParams &P, const
     uint32_t f1 = kFull, v1 = kFull, f2 = kFull, v2 = kFull;
     if ((pm >> lane) & 1u) {
       const uint32_t tt = __popc(pm & lanemask_lt());
-      const uint4 *mine = rel + hdr[nrows + r] * uint32_t(Q) + tt;
+      const uint32_t roff = hdr[nrows + r], cnt = __popc(pm);
       if (!kTwo)
-        support_dispatch_q<Q>(mine, __popc(pm), Dx1, Dy1, dfull, f1, v1);
+        support_dispatch_q<L>(rel, roff, tt, cnt, Dx1, Dy1, dfull, f1, v1);
       else if (Dx1 == dfull && Dx2 == dfull)
-        support_relation_pair<Q, true>(mine, __popc(pm), Dx1, Dy1, Dx2, Dy2, f1, v1, f2, v2);
+        support_pair_at<L, true>(rel, roff, tt, cnt, Dx1, Dy1, Dx2, Dy2, f1, v1, f2, v2);
       else
-        support_relation_pair<Q, false>(mine, __popc(pm), Dx1, Dy1, Dx2, Dy2, f1, v1, f2, v2);
+        support_pair_at<L, false>(rel, roff, tt, cnt, Dx1, Dy1, Dx2, Dy2, f1, v1, f2, v2);
     }
     const uint32_t x = I * 32u + row0 + uint32_t(r);
     const uint32_t keep1 = __reduce_and_sync(kFull, f1) & Dx1;
@@ -236,7 +238,7 @@ __device__ __forceinline__ void batch_eval(BSmem &S, const BatchParams &P, const
 // wps, ...; the reverse masks meet in shared memory, and the group's first
 // warp applies the column removals.  The caller has the consumer group meet
 // before the call, which also frees the reduction slots of the previous one.
-template <int Q>
+template <int L>
 __device__ __forceinline__ void batch_eval_split(BSmem &S, const BatchParams &P, const BatchJob &J,
                                                  int slot_w, const uint32_t *hdr,
                                                  const uint4 *rel, uint32_t I, uint32_t Jb,
@@ -253,7 +255,7 @@ __device__ __forceinline__ void batch_eval_split(BSmem &S, const BatchParams &P,
     uint32_t f = kFull, v = kFull;
     if ((pm >> lane) & 1u) {
       const uint32_t tt = __popc(pm & lanemask_lt());
-      support_dispatch_q<Q>(rel + hdr[nrows + r] * uint32_t(Q) + tt, __popc(pm), Dx, Dy, dfull, f,
+      support_dispatch_q<L>(rel, hdr[nrows + r], tt, __popc(pm), Dx, Dy, dfull, f,
                             v);
     }
     const uint32_t keep = __reduce_and_sync(kFull, f) & Dx;
@@ -288,7 +290,7 @@ __device__ __forceinline__ void batch_eval_split(BSmem &S, const BatchParams &P,
 // state's column words (lane = column) and row words (lane = row) come in two
 // coalesced loads, issued for the next pair while the current one is
 // evaluated.
-template <int Q>
+template <int L>
 __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &J,
                                 const unsigned char *stage, const BStage &si, int k, int slot_r,
                                 int slot_w, int cg, int lw, int lane) {
@@ -344,7 +346,7 @@ __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &
       const uint32_t *C = Cbase + cc;
       const uint32_t Dy = y_ok ? ld_dom(C + y) : 0u;
       const uint32_t Dxl = x_ok ? ld_dom(C + x_l) : 0u;
-      batch_eval_split<Q>(S, P, J, slot_w, hdr, rel, I, Jb, row0, nrows, y, y_ok, lane,
+      batch_eval_split<L>(S, P, J, slot_w, hdr, rel, I, Jb, row0, nrows, y, y_ok, lane,
                           cg * kBGroupWarps + lw, cg, g2, sub, wps, ts, Tbase + to, co, Dy, Dxl);
       continue;
     }
@@ -382,10 +384,10 @@ __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &
       const int64_t to2 = __shfl_sync(kFull, t_off, j2);
       const int64_t co2 = __shfl_sync(kFull, chgoff, j2);
       if (i2 >= 0)
-        batch_eval<Q, true>(S, P, J, slot_w, hdr, rel, I, Jb, row0, nrows, y, y_ok, lane, t1,
+        batch_eval<L, true>(S, P, J, slot_w, hdr, rel, I, Jb, row0, nrows, y, y_ok, lane, t1,
                             Tbase + to1, co1, Dy1, Dx1, t2, Tbase + to2, co2, Dy2, Dx2);
       else
-        batch_eval<Q, false>(S, P, J, slot_w, hdr, rel, I, Jb, row0, nrows, y, y_ok, lane, t1,
+        batch_eval<L, false>(S, P, J, slot_w, hdr, rel, I, Jb, row0, nrows, y, y_ok, lane, t1,
                              Tbase + to1, co1, Dy1, Dx1, -1, nullptr, 0, 0u, 0u);
       if (n1 < 0) break;
       i1 = n1;
@@ -402,7 +404,7 @@ __device__ void batch_consume(BSmem &S, const BatchParams &P, const unsigned cha
                               const BStage &si, int k, int slot_r, int slot_w, int cg, int lw,
                               int lane) {
   const BatchJob J = P.jobs[si.job];
-  switch (J.q) {
+  switch (J.lcode) {
     case 1: batch_consume_q<1>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
     case 2: batch_consume_q<2>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
     case 3: batch_consume_q<3>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
@@ -410,6 +412,13 @@ __device__ void batch_consume(BSmem &S, const BatchParams &P, const unsigned cha
     case 5: batch_consume_q<5>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
     case 6: batch_consume_q<6>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
     case 7: batch_consume_q<7>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
+    case 17: batch_consume_q<17>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
+    case 18: batch_consume_q<18>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
+    case 19: batch_consume_q<19>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
+    case 20: batch_consume_q<20>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
+    case 21: batch_consume_q<21>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
+    case 22: batch_consume_q<22>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
+    case 23: batch_consume_q<23>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
     default: batch_consume_q<8>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
   }
 }

@@ -43,6 +43,11 @@
 #include "rac_mlp.cuh"
 
 namespace rac {
+
+// The instances for packed relation rows (rac_bits_packed.cu): variant var
+// (kVar below), with the completion word when done.
+rac_status launch_bits_packed(const LaunchParams &P, cudaStream_t stream, int var, bool done);
+
 namespace {
 
 using namespace dev;
@@ -314,7 +319,7 @@ __device__ __forceinline__ uint32_t warp_share(uint32_t m, int g, int groups, in
 // when a state's rows are split over several warps).  With kLabel, the state
 // group's first warp (sub == 0) gets back whether the evaluation removed a
 // value.
-template <int Q, bool kLabel, bool kPre>
+template <int L, bool kLabel, bool kPre>
 __device__ __forceinline__ bool eval_state(Smem &S, const LaunchParams &P, int s, int k,
                                            int slot_w, const uint32_t *hdr, const uint4 *rel,
                                            uint32_t I, uint32_t row0, uint32_t nrows, int y,
@@ -346,11 +351,10 @@ __device__ __forceinline__ bool eval_state(Smem &S, const LaunchParams &P, int s
     if ((pm >> lane) & 1u) {
       // this lane's relation: rank t in the row, chunk c at c * cnt + t
       const uint32_t t = __popc(pm & lanemask_lt());
-      const uint4 *mine = rel + hdr[nrows + r] * Q + t;
       if (Dx == dfull)
-        support_relation<Q, true>(mine, __popc(pm), Dx, Dy, fwd, rev);
+        support_at<L, true>(rel, hdr[nrows + r], t, __popc(pm), Dx, Dy, fwd, rev);
       else
-        support_relation<Q, false>(mine, __popc(pm), Dx, Dy, fwd, rev);
+        support_at<L, false>(rel, hdr[nrows + r], t, __popc(pm), Dx, Dy, fwd, rev);
     }
     const uint32_t keep_x = __reduce_and_sync(kFull, fwd) & Dx;  // warp-uniform
     if (keep_x != Dx) {
@@ -393,7 +397,7 @@ __device__ __forceinline__ bool eval_state(Smem &S, const LaunchParams &P, int s
 // the two support tests give the warp independent work.  Dy*, Dx*l as in
 // eval_state with kPre.  Returns, in rem1 / rem2, whether each removed a
 // value.
-template <int Q>
+template <int L>
 __device__ __forceinline__ void eval_pair(Smem &S, const LaunchParams &P, int s1, int s2, int k,
                                           int slot_w, const uint32_t *hdr, const uint4 *rel,
                                           uint32_t I, uint32_t row0, uint32_t nrows, int y,
@@ -412,11 +416,12 @@ __device__ __forceinline__ void eval_pair(Smem &S, const LaunchParams &P, int s1
     uint32_t f1 = kFull, v1 = kFull, f2 = kFull, v2 = kFull;
     if ((pm >> lane) & 1u) {
       const uint32_t t = __popc(pm & lanemask_lt());
-      const uint4 *mine = rel + hdr[nrows + r] * Q + t;
       if (Dx1 == dfull && Dx2 == dfull)
-        support_relation_pair<Q, true>(mine, __popc(pm), Dx1, Dy1, Dx2, Dy2, f1, v1, f2, v2);
+        support_pair_at<L, true>(rel, hdr[nrows + r], t, __popc(pm), Dx1, Dy1, Dx2, Dy2, f1, v1,
+                                 f2, v2);
       else
-        support_relation_pair<Q, false>(mine, __popc(pm), Dx1, Dy1, Dx2, Dy2, f1, v1, f2, v2);
+        support_pair_at<L, false>(rel, hdr[nrows + r], t, __popc(pm), Dx1, Dy1, Dx2, Dy2, f1,
+                                  v1, f2, v2);
     }
     const uint32_t keep1 = __reduce_and_sync(kFull, f1) & Dx1;  // warp-uniform
     const uint32_t keep2 = __reduce_and_sync(kFull, f2) & Dx2;
@@ -614,7 +619,7 @@ __device__ void score_stage(Smem &S, const LaunchParams &P, int stg, int sl, uin
 // to evaluate (stage_dec), each warp its own states as in the plain kernel,
 // the next state's words loaded during the current evaluation; evaluated
 // records get their label.
-template <int Q>
+template <int L>
 __device__ void consume_slab_scored(Smem &S, const LaunchParams &P, const uint32_t *hdr,
                                     const uint4 *rel, const StageInfo &si, int stg, int k,
                                     int slot_w, int warp, int lane, int cg, int g, int sub,
@@ -651,7 +656,7 @@ __device__ void consume_slab_scored(Smem &S, const LaunchParams &P, const uint32
         uint32_t Dy, Dxl;
         load_words(S, P, c0 + i, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
         label(c0 + i,
-              eval_state<Q, true, true>(S, P, c0 + i, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok,
+              eval_state<L, true, true>(S, P, c0 + i, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok,
                                         cached, Dy, Dxl, warp, lane, cg, g, sub, wps, red_iter),
               sub == 0);
       }
@@ -668,7 +673,7 @@ __device__ void consume_slab_scored(Smem &S, const LaunchParams &P, const uint32
       uint32_t Dy, Dxl;
       load_words(S, P, s2, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
       label(s2,
-            eval_state<Q, true, true>(S, P, s2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok,
+            eval_state<L, true, true>(S, P, s2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok,
                                       cached, Dy, Dxl, warp, lane, cg, g2, sub2, wps2, red_iter),
             sub2 == 0);
       continue;
@@ -686,13 +691,13 @@ __device__ void consume_slab_scored(Smem &S, const LaunchParams &P, const uint32
       if (n2 >= 0) load_words(S, P, c0 + n2, k, cached, y, y_ok, x_l, x_ok, Ny2, Nx2);
       if (i2 >= 0) {
         bool r1, r2;
-        eval_pair<Q>(S, P, c0 + i1, c0 + i2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, Dy1,
+        eval_pair<L>(S, P, c0 + i1, c0 + i2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, Dy1,
                      Dx1, Dy2, Dx2, lane, r1, r2);
         label(c0 + i1, r1, true);
         label(c0 + i2, r2, true);
       } else {
         label(c0 + i1,
-              eval_state<Q, true, true>(S, P, c0 + i1, k, slot_w, hdr, rel, I, row0, nrows, y,
+              eval_state<L, true, true>(S, P, c0 + i1, k, slot_w, hdr, rel, I, row0, nrows, y,
                                         y_ok, cached, Dy1, Dx1, warp, lane, cg, g, sub, wps,
                                         red_iter),
               true);
@@ -862,7 +867,7 @@ __device__ void score_sweep(Smem &S, const LaunchParams &P, int k, int slot_r, i
   }
 }
 
-template <int Q, int kVar>
+template <int L, int kVar>
 __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char *stage,
                              const StageInfo &si, int stg, int k, int slot_r, int slot_w,
                              int warp, int lane, uint32_t &red_iter) {
@@ -886,7 +891,7 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
   const bool cached = S.dom_cached != 0;
   if (k == 1 && P.seed_var >= 0 && !slab_touches_seed(P, I, J, row0, nrows)) return;
   if constexpr (kVar >= kVarGated1) {
-    consume_slab_scored<Q>(S, P, hdr, rel, si, stg, k, slot_w, warp, lane, cg, g, sub, wps,
+    consume_slab_scored<L>(S, P, hdr, rel, si, stg, k, slot_w, warp, lane, cg, g, sub, wps,
                            groups, red_iter);
   } else if constexpr (kVar == kVarFew) {
     // one to three states, each split over several warps: a short loop
@@ -895,7 +900,7 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
       if (incr && chg_word(S, P, slot_r, s, J) == 0u &&
           (chg_word(S, P, slot_r, s, I) & rowmask) == 0u)
         continue;
-      eval_state<Q, false, false>(S, P, s, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, cached,
+      eval_state<L, false, false>(S, P, s, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, cached,
                                   0u, 0u, warp, lane, cg, g, sub, wps, red_iter);
     }
   } else {
@@ -927,7 +932,7 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
           const int s2 = c0 + __fns(am, 0, g2 + 1);  // the state of rank g2
           uint32_t Dy, Dxl;
           load_words(S, P, s2, k, cached, y, y_ok, x_l, x_ok, Dy, Dxl);
-          eval_state<Q, false, true>(S, P, s2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok,
+          eval_state<L, false, true>(S, P, s2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok,
                                      cached, Dy, Dxl, warp, lane, cg, g2, sub2, wps2, red_iter);
         } else {
           ++red_iter;  // every warp of the group keeps the same reduction-buffer parity
@@ -949,10 +954,10 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
         if (n2 >= 0) load_words(S, P, c0 + n2, k, cached, y, y_ok, x_l, x_ok, Ny2, Nx2);
         if (i2 >= 0) {
           bool r1, r2;
-          eval_pair<Q>(S, P, c0 + i1, c0 + i2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, Dy1,
+          eval_pair<L>(S, P, c0 + i1, c0 + i2, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok, Dy1,
                        Dx1, Dy2, Dx2, lane, r1, r2);
         } else {
-          eval_state<Q, false, true>(S, P, c0 + i1, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok,
+          eval_state<L, false, true>(S, P, c0 + i1, k, slot_w, hdr, rel, I, row0, nrows, y, y_ok,
                                      cached, Dy1, Dx1, warp, lane, cg, g, sub, wps, red_iter);
         }
         if (n1 < 0) break;
@@ -967,6 +972,8 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
   }
 }
 
+// L: the relation layout (whole-word rows of 4L bits for L = 1..8, packed
+// rows of 4q bits for L = 16 + q), fixed per network.
 // kVar: the plain variants for one to three states (kVarFew: a state's rows
 // split over several warps) and for four or more (kVarMany: a warp per
 // state, words prefetched), and the variants of rac_enforce_learned (learned
@@ -977,7 +984,7 @@ __device__ void consume_slab(Smem &S, const LaunchParams &P, const unsigned char
 // publishes a completion number to host memory at its end (P.host_done); a
 // separate instance keeps that code out of every other launch, where it had
 // cost 1-5% of the time.
-template <int Q, int kVar, bool kDone>
+template <int L, int kVar, bool kDone>
 __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const LaunchParams P) {
   constexpr int kGate = kVar >= kVarGated1 ? 1 : 0;
   constexpr int kGW = group_warps(kVar), kCW = consumer_warps(kVar);
@@ -1174,7 +1181,7 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
           __syncwarp();
           const StageInfo si = S.stage[stg];
           if (si.sl >= 0)
-            consume_slab<Q, kVar>(S, P, ring + size_t(stg) * kStageBytes, si, stg, k, slot_r, slot_w, warp,
+            consume_slab<L, kVar>(S, P, ring + size_t(stg) * kStageBytes, si, stg, k, slot_r, slot_w, warp,
                             lane, red_iter);
           __syncwarp();
           if (lane == 0) mbar_arrive(&S.empty[stg]);
@@ -1328,13 +1335,13 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
   }
 }
 
-template <int Q, int kVar, bool kDone>
+template <int L, int kVar, bool kDone>
 rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
   static LaunchCache cache;
   const size_t smem = size_t(kStages) * kStageBytes + sizeof(Smem);
   int per_sm = 0, sms = 0;
   rac_status rc = persistent_shape(cache,
-                                   reinterpret_cast<const void *>(rac_bits_kernel<Q, kVar, kDone>),
+                                   reinterpret_cast<const void *>(rac_bits_kernel<L, kVar, kDone>),
                                    threads_for(kVar), smem, "bit-packed kernel set-up", &per_sm,
                                    &sms);
   if (rc != RAC_OK) return rc;
@@ -1354,13 +1361,19 @@ rac_status launch_q(const LaunchParams &P, cudaStream_t stream) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, rac_bits_kernel<Q, kVar, kDone>, P);
+  e = cudaLaunchKernelEx(&cfg, rac_bits_kernel<L, kVar, kDone>, P);
   if (e != cudaSuccess) return cuda_fail(e, "launch of the bit-packed kernel");
   return RAC_OK;
 }
 
+// The instance for the network's relation layout: whole-word rows of width
+// q = dp / 4 here; packed rows (layout code 16 + q) in the packed unit, which
+// compiles this file once more with RAC_BITS_PACKED_UNIT defined so that the
+// two halves of the instances build in parallel.
 template <int kVar, bool kDone>
 rac_status launch_width(const LaunchParams &P, cudaStream_t stream) {
+#ifndef RAC_BITS_PACKED_UNIT
+  if (P.net.packed) return launch_bits_packed(P, stream, kVar, kDone);
   switch (P.net.q) {
     case 1: return launch_q<1, kVar, kDone>(P, stream);
     case 2: return launch_q<2, kVar, kDone>(P, stream);
@@ -1370,12 +1383,37 @@ rac_status launch_width(const LaunchParams &P, cudaStream_t stream) {
     case 6: return launch_q<6, kVar, kDone>(P, stream);
     case 7: return launch_q<7, kVar, kDone>(P, stream);
     case 8: return launch_q<8, kVar, kDone>(P, stream);
-    default: set_error("unsupported relation width"); return RAC_EINVAL;
+    default: break;
   }
+#else
+  switch (P.net.q) {
+    case 1: return launch_q<17, kVar, kDone>(P, stream);
+    case 2: return launch_q<18, kVar, kDone>(P, stream);
+    case 3: return launch_q<19, kVar, kDone>(P, stream);
+    case 4: return launch_q<20, kVar, kDone>(P, stream);
+    case 5: return launch_q<21, kVar, kDone>(P, stream);
+    case 6: return launch_q<22, kVar, kDone>(P, stream);
+    case 7: return launch_q<23, kVar, kDone>(P, stream);
+    default: break;
+  }
+#endif
+  set_error("unsupported relation width");
+  return RAC_EINVAL;
 }
 
 }  // namespace
 
+#ifdef RAC_BITS_PACKED_UNIT
+rac_status launch_bits_packed(const LaunchParams &P, cudaStream_t stream, int var, bool done) {
+  if (done) return launch_width<kVarFew, true>(P, stream);
+  switch (var) {
+    case kVarFew: return launch_width<kVarFew, false>(P, stream);
+    case kVarMany: return launch_width<kVarMany, false>(P, stream);
+    case kVarGated1: return launch_width<kVarGated1, false>(P, stream);
+    default: return launch_width<kVarGated2, false>(P, stream);
+  }
+}
+#else
 rac_status launch_bits(const LaunchParams &P, cudaStream_t stream) {
   const bool gate = P.mlp != nullptr || P.tr_count != nullptr || P.tr_evals != nullptr;
   if (P.host_done) {  // the host entry point's one-to-three-state launch
@@ -1392,5 +1430,6 @@ rac_status launch_bits(const LaunchParams &P, cudaStream_t stream) {
   return P.n_states <= 16 ? launch_width<kVarGated1, false>(P, stream)
                           : launch_width<kVarGated2, false>(P, stream);
 }
+#endif
 
 }  // namespace rac

@@ -214,5 +214,132 @@ __device__ __forceinline__ void support_relation_pair(const uint4 *rel, uint32_t
   rev2 = kDxFull ? rev1 : (r2 | q2);
 }
 
+// ---------------------------------------------------------------------------
+// Packed relation rows (RAC_LAYOUT_PACKED): the relation's rows a = 0..4Q-1
+// lie back to back, 4Q bits each, in packed_words(Q) words read `stride`
+// words apart.  Row a is bits [4Q a, 4Q a + 4Q): one shift of its word, or a
+// funnel shift of two words when it straddles them.  The bits above a row's
+// 4Q belong to the next rows: the forward test ANDs them with Dy (no bits >=
+// d), and the reverse mask is cut to 4Q bits at the end.  Same results as
+// support_relation on the whole-word rows.
+template <int Q, int A>
+__device__ __forceinline__ uint32_t packed_row(const uint32_t (&w)[packed_words(Q)]) {
+  constexpr int kBits = 4 * Q, kOff = A * kBits, kWord = kOff >> 5, kShift = kOff & 31;
+  constexpr int kNext = kWord + 1 < packed_words(Q) ? kWord + 1 : kWord;
+  if constexpr (kShift == 0) return w[kWord];
+  else if constexpr (kShift + kBits <= 32) return w[kWord] >> kShift;
+  else return __funnelshift_r(w[kWord], w[kNext], kShift);
+}
+
+template <int Q, bool kDxFull, int A = 0>
+__device__ __forceinline__ void packed_rows(const uint32_t (&w)[packed_words(Q)], uint32_t Dx,
+                                            uint32_t Dy, uint32_t &f0, uint32_t &f1,
+                                            uint32_t &r0, uint32_t &r1) {
+  if constexpr (A < 4 * Q) {
+    const uint32_t row = packed_row<Q, A>(w);
+    if constexpr (A % 2 == 0) {
+      or_if_bit(f0, 1u << A, row, Dy);
+      if (kDxFull) r0 |= row;
+      else or_if_bit(r0, row, Dx, 1u << A);
+    } else {
+      or_if_bit(f1, 1u << A, row, Dy);
+      if (kDxFull) r1 |= row;
+      else or_if_bit(r1, row, Dx, 1u << A);
+    }
+    packed_rows<Q, kDxFull, A + 1>(w, Dx, Dy, f0, f1, r0, r1);
+  }
+}
+
+template <int Q, bool kDxFull>
+__device__ __forceinline__ void support_relation_packed(const uint32_t *rel, uint32_t stride,
+                                                        uint32_t Dx, uint32_t Dy, uint32_t &fwd,
+                                                        uint32_t &rev) {
+  uint32_t w[packed_words(Q)];
+#pragma unroll
+  for (int j = 0; j < packed_words(Q); ++j) w[j] = rel[j * stride];
+  uint32_t f0 = 0, f1 = 0, r0 = 0, r1 = 0;
+  packed_rows<Q, kDxFull>(w, Dx, Dy, f0, f1, r0, r1);
+  fwd = f0 | f1;
+  rev = (r0 | r1) & ((1u << (4 * Q)) - 1u);
+}
+
+// Two domain states on one packed relation: each row is taken out of its
+// words once and tested for both (as support_relation_pair).
+template <int Q, bool kDxFull, int A = 0>
+__device__ __forceinline__ void packed_rows_pair(const uint32_t (&w)[packed_words(Q)],
+                                                 uint32_t Dx1, uint32_t Dy1, uint32_t Dx2,
+                                                 uint32_t Dy2, uint32_t (&f)[4],
+                                                 uint32_t (&r)[4]) {
+  if constexpr (A < 4 * Q) {
+    constexpr int h = A % 2;
+    const uint32_t row = packed_row<Q, A>(w);
+    or_if_bit(f[h], 1u << A, row, Dy1);
+    or_if_bit(f[2 + h], 1u << A, row, Dy2);
+    if (kDxFull) {
+      r[h] |= row;
+    } else {
+      or_if_bit(r[h], row, Dx1, 1u << A);
+      or_if_bit(r[2 + h], row, Dx2, 1u << A);
+    }
+    packed_rows_pair<Q, kDxFull, A + 1>(w, Dx1, Dy1, Dx2, Dy2, f, r);
+  }
+}
+
+template <int Q, bool kDxFull>
+__device__ __forceinline__ void support_relation_pair_packed(
+    const uint32_t *rel, uint32_t stride, uint32_t Dx1, uint32_t Dy1, uint32_t Dx2, uint32_t Dy2,
+    uint32_t &fwd1, uint32_t &rev1, uint32_t &fwd2, uint32_t &rev2) {
+  uint32_t w[packed_words(Q)];
+#pragma unroll
+  for (int j = 0; j < packed_words(Q); ++j) w[j] = rel[j * stride];
+  uint32_t f[4] = {0u, 0u, 0u, 0u}, r[4] = {0u, 0u, 0u, 0u};
+  packed_rows_pair<Q, kDxFull>(w, Dx1, Dy1, Dx2, Dy2, f, r);
+  constexpr uint32_t kRow = (1u << (4 * Q)) - 1u;
+  fwd1 = f[0] | f[1];
+  fwd2 = f[2] | f[3];
+  rev1 = (r[0] | r[1]) & kRow;
+  rev2 = kDxFull ? rev1 : ((r[2] | r[3]) & kRow);
+}
+
+// ---------------------------------------------------------------------------
+// A kernel's relation layout code L: L = Q (1..8) for whole-word rows, L = 16
+// + Q (Q = 1..7) for packed rows.  The support test of the t-th relation of a
+// slab row whose first relation has index roff (the header's roff[r]) and
+// which holds cnt relations; rel points at the slab's first relation.
+template <int L>
+struct RelLayout {
+  static constexpr bool kPacked = L >= 16;
+  static constexpr int kQ = kPacked ? L - 16 : L;
+  static_assert(kQ >= 1 && kQ <= (kPacked ? 7 : 8), "relation layout code");
+};
+
+template <int L, bool kDxFull>
+__device__ __forceinline__ void support_at(const uint4 *rel, uint32_t roff, uint32_t t,
+                                           uint32_t cnt, uint32_t Dx, uint32_t Dy, uint32_t &fwd,
+                                           uint32_t &rev) {
+  constexpr int Q = RelLayout<L>::kQ;
+  if constexpr (RelLayout<L>::kPacked)
+    support_relation_packed<Q, kDxFull>(
+        reinterpret_cast<const uint32_t *>(rel) + roff * uint32_t(packed_words(Q)) + t, cnt, Dx,
+        Dy, fwd, rev);
+  else
+    support_relation<Q, kDxFull>(rel + roff * uint32_t(Q) + t, cnt, Dx, Dy, fwd, rev);
+}
+
+template <int L, bool kDxFull>
+__device__ __forceinline__ void support_pair_at(const uint4 *rel, uint32_t roff, uint32_t t,
+                                                uint32_t cnt, uint32_t Dx1, uint32_t Dy1,
+                                                uint32_t Dx2, uint32_t Dy2, uint32_t &fwd1,
+                                                uint32_t &rev1, uint32_t &fwd2, uint32_t &rev2) {
+  constexpr int Q = RelLayout<L>::kQ;
+  if constexpr (RelLayout<L>::kPacked)
+    support_relation_pair_packed<Q, kDxFull>(
+        reinterpret_cast<const uint32_t *>(rel) + roff * uint32_t(packed_words(Q)) + t, cnt, Dx1,
+        Dy1, Dx2, Dy2, fwd1, rev1, fwd2, rev2);
+  else
+    support_relation_pair<Q, kDxFull>(rel + roff * uint32_t(Q) + t, cnt, Dx1, Dy1, Dx2, Dy2,
+                                      fwd1, rev1, fwd2, rev2);
+}
+
 }  // namespace dev
 }  // namespace rac

@@ -27,9 +27,15 @@ namespace rac {
 //                         is constrained,
 //              roff[rows] index of row r's first relation in the slab,
 //   relations: row by row; a row's cnt relations (present pairs only, by
-//              increasing column j) take cnt * dp words, dp = round_up(d, 4),
-//              stored chunk-major: 16-byte chunk c (relation rows 4c..4c+3,
-//              rows >= d zero) of the row's t-th relation is chunk c*cnt + t.
+//              increasing column j) take cnt * rw words each.  Whole-word
+//              rows (the default): rw = dp = round_up(d, 4), relation row a
+//              in word a, stored chunk-major: 16-byte chunk c (relation
+//              rows 4c..4c+3, rows >= d zero) of the row's t-th relation is
+//              chunk c*cnt + t.  Packed rows (RAC_LAYOUT_PACKED, d <= 28):
+//              relation row a in bits [dp a, dp a + dp) of the relation's
+//              rw = packed_words(q) words (bit i of the stream = bit i % 32
+//              of word i / 32), stored word-major: word w of the row's t-th
+//              relation is word w*cnt + t.  The record is padded to 16 bytes.
 // so one bulk copy brings everything a slab's evaluation needs.
 // ---------------------------------------------------------------------------
 struct SlabDesc {
@@ -64,8 +70,14 @@ constexpr int kMaxStatesPerLaunch = 1024;
 constexpr int kDescCache = 200;   // slab descriptors a CTA keeps in shared memory
 constexpr int kDomWords = 5040;   // domain words a CTA keeps in shared memory per sweep
 
+// Words of one relation with packed rows: 4q rows of 4q bits (rows >= d and
+// bits >= d zero), rounded up to whole words.
+__host__ __device__ constexpr int packed_words(int q) { return (16 * q * q + 31) / 32; }
+
 struct NetDev {
   int32_t n, d, dp, q, nb, rows_per_slab, n_slabs;
+  int32_t packed;  // 1: packed relation rows (RAC_LAYOUT_PACKED), 0: whole-word rows
+  int32_t rw;      // words per stored relation: packed_words(q) or dp
   int32_t max_ctas;  // > 0: grid cap of the network's launches (RAC_LAYOUT_MAX_CTAS)
   // FP8 operand store of the tensor-core kernel (RAC_LAYOUT_FP8; null until
   // built): fp8_jobs MMA operand tiles of kFp8TileBytes per slab, slab-major
@@ -182,7 +194,8 @@ struct BatchJob {
   int32_t n_slabs, slab_base;    // first global slab index of the job
   int32_t n_states, state_base;  // first state of the job
   int64_t u_off;                 // offset of the job's words in a chgU slot
-  int64_t pad;
+  int32_t lcode;                 // relation layout: q (whole-word rows), 16 + q (packed rows)
+  int32_t pad;
 };
 static_assert(sizeof(BatchJob) == 64, "BatchJob is 64 bytes");
 
@@ -256,6 +269,7 @@ struct Workspace {
 
 struct rac_network {
   int32_t n = 0, d = 0, dp = 0, q = 0, nb = 0, rows_per_slab = 0;
+  int32_t packed = 0, rw = 0;  // packed relation rows; words per stored relation
   int32_t max_ctas = 0;  // RAC_LAYOUT_MAX_CTAS, 0: none
   // the tensor-core kernel's FP8 operand store (RAC_LAYOUT_FP8, or built by
   // the first RAC_KERNEL_TENSOR call under mu)

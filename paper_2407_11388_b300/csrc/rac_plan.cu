@@ -77,6 +77,7 @@ rac_status build_host_plan(const rac_network *const *nets, int32_t n_nets, int32
     J.n = net->n;
     J.d = net->d;
     J.q = net->q;
+    J.lcode = net->q + (net->packed ? 16 : 0);
     J.nb = net->nb;
     J.n_slabs = int32_t(net->n_slabs);
     J.slab_base = H.total_slabs;

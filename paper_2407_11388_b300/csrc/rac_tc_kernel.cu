@@ -200,12 +200,22 @@ __device__ __forceinline__ void tc_remove(TcSmem &S, const LaunchParams &P, int 
   if (P.flags & RAC_INCREMENTAL) atomicOr(P.chgU + int64_t(slot_w) * nb + (v >> 5), bit);
 }
 
-// Relation row `a` (a < 32; rows >= 4Q are zero) of the t-th relation of slab
-// row r, in the chunk-major stage layout.
+// Relation row `a` (a < 32; rows >= 4q are zero) of the t-th relation of slab
+// row r, in the network's store layout: whole-word rows chunk-major, or
+// packed rows (4q bits each) word-major.
 __device__ __forceinline__ uint32_t rel_row(const uint32_t *hdr, const uint32_t *relw,
-                                            uint32_t nrows, int q, int r, uint32_t t, int a) {
+                                            uint32_t nrows, const NetDev &N, int r, uint32_t t,
+                                            int a) {
+  const int q = N.q;
   if (a >= 4 * q) return 0u;
   const uint32_t pm = hdr[r], cnt = __popc(pm);
+  if (N.packed) {
+    const uint32_t *mine = relw + hdr[nrows + r] * uint32_t(N.rw) + t;
+    const int bits = 4 * q, off = a * bits, wd = off >> 5, sh = off & 31;
+    const uint32_t lo = mine[uint32_t(wd) * cnt];
+    const uint32_t hi = sh + bits > 32 ? mine[uint32_t(wd + 1) * cnt] : 0u;
+    return __funnelshift_r(lo, hi, uint32_t(sh)) & ((1u << bits) - 1u);
+  }
   const uint32_t base_chunk = hdr[nrows + r] * uint32_t(q);
   return relw[(base_chunk + uint32_t(a >> 2) * cnt + t) * 4u + uint32_t(a & 3)];
 }
@@ -231,7 +241,7 @@ __global__ void __launch_bounds__(256) rac_fp8_build_kernel(const NetDev N, uint
       const int r = 8 * g + (row >> 5), a = row & 31;
       if (r < int(nrows) && ((hdr[r] >> j) & 1u)) {
         const uint32_t t_rank = __popc(hdr[r] & ((1u << j) - 1u));
-        nib = (rel_row(hdr, relw, nrows, N.q, r, t_rank, a) >> (4 * qq)) & 0xFu;
+        nib = (rel_row(hdr, relw, nrows, N, r, t_rank, a) >> (4 * qq)) & 0xFu;
       }
     } else {  // reverse: rows (j, b) of R_{x_r, y_j} transposed, K = a
       const int ridx = idx - 32 * rg;
@@ -241,7 +251,7 @@ __global__ void __launch_bounds__(256) rac_fp8_build_kernel(const NetDev N, uint
         const uint32_t t_rank = __popc(hdr[r] & ((1u << j) - 1u));
 #pragma unroll
         for (int i2 = 0; i2 < 4; ++i2)
-          nib |= ((rel_row(hdr, relw, nrows, N.q, r, t_rank, 4 * qq + i2) >> b) & 1u) << i2;
+          nib |= ((rel_row(hdr, relw, nrows, N, r, t_rank, 4 * qq + i2) >> b) & 1u) << i2;
       }
     }
     *reinterpret_cast<uint32_t *>(out + t * kFp8TileBytes + tile_off(uint32_t(row), 4u * qq)) =

@@ -36,8 +36,8 @@ import threading
 
 import numpy as np
 
-from . import (EBARRIER, ETIMEOUT, INCREMENTAL, OK, STOP_ON_WIPEOUT, WIPEOUT, Network, RacError,
-               EINVAL, combine_partials, enforce)
+from . import (EBARRIER, EINVAL, ETIMEOUT, INCREMENTAL, LAYOUT_BITS, OK, STOP_ON_WIPEOUT, WIPEOUT,
+               Network, RacError, combine_partials, enforce)
 
 
 def partition_constraints(n, scope, n_parts):
@@ -146,12 +146,12 @@ class GpuShare:
     constraints as a library network, and the buffers of its sweeps.  All of
     its work goes to torch's current stream of the calling thread."""
 
-    def __init__(self, n, d, scope, rel, cons):
+    def __init__(self, n, d, scope, rel, cons, layout=LAYOUT_BITS):
         import torch
         scope = np.asarray(scope, dtype=np.int32).reshape(-1, 2)
         rel = np.asarray(rel)
         self.n, self.d = int(n), int(d)
-        self.net = Network(n, d, scope[cons], rel[cons])
+        self.net = Network(n, d, scope[cons], rel[cons], layout=layout)
         dev = torch.device("cuda", torch.cuda.current_device())
         self.partial = torch.empty(self.n, dtype=torch.int32, device=dev)
         self.bufs = [torch.empty(self.n, dtype=torch.int32, device=dev) for _ in range(2)]

@@ -199,3 +199,35 @@ def test_more_constraints_than_pairs_rejected(L):
         assert L.rac_create_network_u8(4, 3, n_cons, scope.ctypes.data, mats.ctypes.data, 1,
                                        ctypes.byref(h)) == rac.EINVAL
         assert h.value is None
+
+
+def test_binding_constants_match_the_header():
+    """Every flag and status constant of the binding has the value rac.h
+    defines for it."""
+    src = open(os.path.join(ROOT, "include", "rac.h")).read()
+    defs = {k: int(v, 0) for k, v in
+            re.findall(r"^#define RAC_(\w+)\s+\(?(-?(?:0x[0-9A-Fa-f]+|\d+))u?\)?", src, flags=re.M)}
+    checked = 0
+    for name, value in defs.items():
+        if hasattr(rac, name) and isinstance(getattr(rac, name), int):
+            assert getattr(rac, name) == value, name
+            checked += 1
+    assert checked >= 12
+    assert rac.LAYOUT_PACKED == defs["LAYOUT_PACKED"]
+
+
+def test_packed_rows_change_the_tile_size_rule(L):
+    """A tile's size counts the words of its relations: 16 rows of d = 20
+    take 40 KiB with a word per row (rejected before anything is allocated)
+    but 26 KiB packed (accepted by the size rule; without a GPU the call then
+    fails on the device, not on the size)."""
+    scope, rel = np.array([[0, 1]], np.int32), np.zeros((1, 20), np.uint32)
+    rc, h = _create(L, 4, 20, scope, rel, flags=1 | (5 << 8))
+    assert rc == rac.EINVAL and "staging buffer" in L.rac_last_error().decode()
+    rc, h = _create(L, 4, 20, scope, rel, flags=1 | rac.LAYOUT_PACKED | (5 << 8))
+    assert "staging buffer" not in L.rac_last_error().decode()
+    if rc == rac.OK:
+        L.rac_destroy(h)
+    # 32 rows of d = 20 do not fit even packed (53 KiB)
+    rc, h = _create(L, 4, 20, scope, rel, flags=1 | rac.LAYOUT_PACKED | (6 << 8))
+    assert rc == rac.EINVAL and "staging buffer" in L.rac_last_error().decode()

@@ -47,3 +47,25 @@ def test_plan_entries_are_looked_up_apart(tmp_path):
     assert autotune.table_choice(6, 0.5, 64, path, kind="plan") == (32, None)
     assert autotune.table_choice(6, 0.5, 64, path) == (8, None)
     assert autotune.table_choice(6, 0.5, 1, path) == (None, None)
+
+
+def test_relation_layout_entries(tmp_path):
+    """An entry's packed flag is looked up with its rows; the rows of a packed
+    entry are checked against the packed tile size (16 rows of d = 20 fit a
+    stage only packed)."""
+    path = _write(tmp_path, [
+        {"d_lo": 17, "d_hi": 24, "dens_lo": 0.6, "dens_hi": 1.0, "st_lo": 1, "st_hi": 1,
+         "rows": 16, "max_ctas": None, "packed": True},
+        {"d_lo": 17, "d_hi": 24, "dens_lo": 0.6, "dens_hi": 1.0, "st_lo": 2, "st_hi": 1 << 30,
+         "rows": 8, "max_ctas": None, "packed": False},
+    ])
+    assert autotune.table_packed(20, 0.9, 1, path) is True
+    assert autotune.table_packed(20, 0.9, 32, path) is False
+    assert autotune.table_packed(20, 0.3, 1, path) is False          # no density bucket
+    assert autotune.table_choice(20, 0.9, 1, path, packed=True) == (16, None)
+    assert autotune.table_choice(20, 0.9, 1, path, packed=False) == (None, None)
+    assert autotune.admissible_rows(20) == [2, 4, 8]
+    assert autotune.admissible_rows(20, packed=True) == [2, 4, 8, 16]
+    assert autotune.admissible_rows(12, packed=True) == [2, 4, 8, 16, 32]
+    assert autotune.words_per_relation(24, packed=True) == 18
+    assert autotune.words_per_relation(30, packed=True) == 32

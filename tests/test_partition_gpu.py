@@ -58,14 +58,14 @@ def test_combine_partials_in_place_and_empty():
     assert flags.cpu().tolist() == [0, 0]
 
 
-def _partitioned(n, d, scope, rel, dom, G, flags=0, max_sweeps=0):
+def _partitioned(n, d, scope, rel, dom, G, flags=0, max_sweeps=0, layout=rac.LAYOUT_BITS):
     parts, _ = partition_constraints(n, scope, G)
     group = ThreadGroup(G)
     res, errs = [None] * G, []
 
     def body(g):
         try:
-            share = GpuShare(n, d, scope, rel, parts[g])
+            share = GpuShare(n, d, scope, rel, parts[g], layout=layout)
             try:
                 out, it, st = enforce_partitioned(share, group.rank_view(g), to_dev(dom),
                                                   max_sweeps=max_sweeps, flags=flags)
@@ -85,7 +85,7 @@ def _partitioned(n, d, scope, rel, dom, G, flags=0, max_sweeps=0):
     return res
 
 
-def _check(n, d, x, doms, G, flags=0, max_sweeps=0):
+def _check(n, d, x, doms, G, flags=0, max_sweeps=0, layout=rac.LAYOUT_BITS):
     doms = np.asarray(doms, np.uint32).reshape(-1, n)
     want = oracle_enforce(n, d, x.scope, x.rel, doms, flags=flags, max_sweeps=max_sweeps)
     whole = [gpu_enforce(n, d, x.scope, x.rel, doms[s], flags=flags, max_sweeps=max_sweeps)
@@ -93,7 +93,7 @@ def _check(n, d, x, doms, G, flags=0, max_sweeps=0):
     for s in range(doms.shape[0]):
         assert_same(whole[s], tuple(a[s:s + 1] for a in want), "rac_enforce")
         for g, (out, it, st) in enumerate(_partitioned(n, d, x.scope, x.rel, doms[s], G,
-                                                       flags, max_sweeps)):
+                                                       flags, max_sweeps, layout)):
             got = (out[None, :], np.array([it]), np.array([st]))
             assert_same(got, whole[s], "rank %d of %d, state %d" % (g, G, s))
     return want
@@ -117,6 +117,16 @@ def test_cascades_wipeouts_and_the_cap(G):
     assert want[1].max() >= 3
     _check(n, d, x, doms[:2], G, flags=rac.STOP_ON_WIPEOUT)
     _check(n, d, x, doms[:2], G, max_sweeps=2)
+
+
+def test_packed_shares_over_three_ranks():
+    """Each rank's share stored with packed relation rows (d = 20)."""
+    n, d = 700, 20
+    x = racgen.random_network(33, 0, n, d, 0.5, 0.4)
+    doms = [racgen.full_domain(n, d)] + [racgen.assignment_state(33, 0, s, n, d) for s in range(3)]
+    _check(n, d, x, doms, 3, layout=rac.LAYOUT_BITS | rac.LAYOUT_PACKED)
+    _check(n, d, x, doms[1:3], 3, flags=rac.STOP_ON_WIPEOUT,
+           layout=rac.LAYOUT_BITS | rac.LAYOUT_PACKED)
 
 
 def test_nccl_group_of_one_rank():

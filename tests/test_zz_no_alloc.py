@@ -48,6 +48,22 @@ def test_noalloc_matches_enforce_on_consecutive_calls():
         assert max(_via(rac.enforce, net, s, 0)[1] for s in states) >= 3
 
 
+def test_noalloc_on_a_packed_network():
+    """The same with the network's relation rows packed (d = 20)."""
+    n, d = 300, 20
+    net_np = racgen.random_network(13, 0, n, d, 0.6, 0.45)
+    states = [racgen.full_domain(n, d)] + [racgen.assignment_state(13, 0, s, n, d)
+                                            for s in range(3)]
+    with rac.Network(n, d, net_np.scope, net_np.rel,
+                     layout=rac.LAYOUT_BITS | rac.LAYOUT_PACKED) as net:
+        for flags in (0, rac.INCREMENTAL):
+            for dom in states:
+                want = oracle_enforce(n, d, net_np.scope, net_np.rel, dom, flags)
+                got = _via(rac.enforce_noalloc, net, dom, flags)
+                assert np.array_equal(got[0], want[0][0]), flags
+                assert got[1:] == (want[1][0], want[2][0]), (flags, got[1:])
+
+
 def test_noalloc_rejects_networks_above_its_limit():
     n = rac.NOALLOC_MAX_VARS + 1
     scope = np.array([[0, n - 1]], np.int32)
