@@ -33,7 +33,9 @@ import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 TABLE = os.path.join(HERE, "tile_table.json")
-D_BUCKETS = [(1, 8), (9, 16), (17, 24), (25, 32)]
+# one bucket per relation width q = ceil(d / 4): every d of a bucket runs the
+# same kernel instance and has the same tile sizes in both layouts
+D_BUCKETS = [(4 * q - 3, 4 * q) for q in range(1, 9)]
 DENSITY_BUCKETS = [(0.0, 0.6), (0.6, 1.0)]
 STATE_BUCKETS = [(1, 1), (2, 16), (17, 1 << 30)]
 STATES_TIMED = {(1, 1): 1, (2, 16): 8, (17, 1 << 30): 32}
