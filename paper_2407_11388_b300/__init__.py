@@ -200,18 +200,19 @@ class Network:
             create = lib().rac_create_network
         if rel.shape[0] != scope.shape[0]:
             raise RacError(EINVAL, "scope and rel disagree on the number of constraints")
+        m = scope.shape[0]
         if packed is None and not (int(layout) & LAYOUT_PACKED):
             from .autotune import table_packed
-            packed = table_packed(int(d), scope.shape[0] / max(1.0, n * (n - 1) / 2.0),
-                                  int(states or 1), kind="plan" if plan else "single")
+            packed = table_packed(int(d), m / max(1.0, n * (n - 1) / 2.0), int(states or 1),
+                                  kind="plan" if plan else "single", m=m)
         if packed:
             layout = int(layout) | LAYOUT_PACKED
         if (rows is None and not (int(layout) & 0xF00)) or \
                 (max_ctas is None and not (int(layout) & 0xFFFF0000)):
             from .autotune import table_choice
-            t_rows, t_ctas = table_choice(int(d), scope.shape[0] / max(1.0, n * (n - 1) / 2.0),
+            t_rows, t_ctas = table_choice(int(d), m / max(1.0, n * (n - 1) / 2.0),
                                           int(states or 1), kind="plan" if plan else "single",
-                                          packed=bool(int(layout) & LAYOUT_PACKED))
+                                          packed=bool(int(layout) & LAYOUT_PACKED), m=m)
             if rows is None and not (int(layout) & 0xF00):
                 rows = t_rows
             if max_ctas is None and not (int(layout) & 0xFFFF0000):

@@ -16,11 +16,14 @@ states per launch and the GPU, so it is measured:
 
     python -m paper_2407_11388_b300.autotune [--out FILE] [--runs 20]
 
-For every (d, density, states) bucket it times every admissible row count,
-grid cap and relation layout on seeded synthetic networks of the bucket (120, 360 and 700
+For every (d, density, states) bucket -- one-state buckets also split at
+SIZE_SPLIT constraints -- it times every admissible row count, grid cap and
+relation layout on seeded synthetic networks of the bucket (120, 360 and 700
 variables at the bucket's middle d and density, tightness 0.3, assignment
-states; one launch per network -- rac_enforce for one state, rac_enforce_batch
-for more -- CUDA events, L2 flushed before each launch, median of `runs`),
+states; for one state 120, 250 and 400 variables below the split, 1000 and
+2000 above it; one launch per network -- rac_enforce for one state,
+rac_enforce_batch for more -- CUDA events, L2 flushed before each launch,
+median of `runs`),
 and, for networks enforced together, every row count and layout of one
 multi-network plan launch of the three networks with 64 states each; it writes the
 fastest choice per bucket to a JSON table.  Network() consults that table
@@ -38,6 +41,14 @@ TABLE = os.path.join(HERE, "tile_table.json")
 D_BUCKETS = [(4 * q - 3, 4 * q) for q in range(1, 9)]
 DENSITY_BUCKETS = [(0.0, 0.6), (0.6, 1.0)]
 STATE_BUCKETS = [(1, 1), (2, 16), (17, 1 << 30)]
+# One-state launches are also split by size (constraints): a network of a few
+# hundred tiles is done in one round of the CTAs' static tiles, a large one
+# streams most of its tiles through the dynamic claims, and the two regimes
+# prefer different tiles and layouts.  Representatives per class: networks of
+# these variable counts at the bucket's middle d and density.
+SIZE_SPLIT = 100_000
+SIZE_CLASSES = [(0, SIZE_SPLIT - 1, (120, 250, 400)), (SIZE_SPLIT, 1 << 62, (1000, 2000))]
+MULTI_STATE_SIZES = (120, 360, 700)
 STATES_TIMED = {(1, 1): 1, (2, 16): 8, (17, 1 << 30): 32}
 PLAN_STATES = 64  # states per network in the multi-network plans timed
 CTA_CAPS = (None, 74, 37)  # every resident CTA (capped at the tile count), or fewer
@@ -72,7 +83,7 @@ def load_table(path=TABLE):
     return _table
 
 
-def _entry(d, density, states, path, kind):
+def _entry(d, density, states, path, kind, m=None):
     for e in load_table(path).get("entries", []):
         if e.get("kind", "single") != kind:
             continue
@@ -80,27 +91,30 @@ def _entry(d, density, states, path, kind):
             continue
         if not e.get("st_lo", 1) <= states <= e.get("st_hi", 1 << 30):
             continue
+        if m is not None and not e.get("m_lo", 0) <= m <= e.get("m_hi", 1 << 62):
+            continue
         return e
     return None
 
 
-def table_choice(d, density, states=1, path=TABLE, kind="single", packed=False):
+def table_choice(d, density, states=1, path=TABLE, kind="single", packed=False, m=None):
     """(rows, max_ctas) tuned for this shape; None for what the table does
     not fix (the library default).  kind: "single" for a network enforced in
     launches of its own, "plan" for one enforced in multi-network plans;
     packed: the relation layout the network is created with (the tuned rows
-    are taken only when they fit its tiles)."""
-    e = _entry(d, density, states, path, kind)
+    are taken only when they fit its tiles); m: the number of constraints
+    (None: the first entry of any size)."""
+    e = _entry(d, density, states, path, kind, m)
     if e is None:
         return None, None
     r = int(e["rows"])
     return (r if r in admissible_rows(d, packed) else None), e.get("max_ctas")
 
 
-def table_packed(d, density, states=1, path=TABLE, kind="single"):
+def table_packed(d, density, states=1, path=TABLE, kind="single", m=None):
     """Whether the table found packed relation rows faster for this shape
     (False where it has no entry or did not time them)."""
-    e = _entry(d, density, states, path, kind)
+    e = _entry(d, density, states, path, kind, m)
     return bool(e and e.get("packed", False))
 
 
@@ -109,15 +123,15 @@ def table_rows(d, density, states=1, path=TABLE, kind="single"):
     return table_choice(d, density, states, path, kind)[0]
 
 
-def _bucket_networks(d_lo, d_hi, dens_lo, dens_hi, seed, states):
-    """Seeded representatives of a bucket: networks of 120, 360 and 700
-    variables at the bucket's middle d and density, tightness 0.3, with
-    `states` assignment states each."""
+def _bucket_networks(d_lo, d_hi, dens_lo, dens_hi, seed, states, sizes=MULTI_STATE_SIZES):
+    """Seeded representatives of a bucket: networks of `sizes` variables at
+    the bucket's middle d and density, tightness 0.3, with `states`
+    assignment states each."""
     import racgen
     d = (d_lo + d_hi + 1) // 2
     dens = 0.5 * (dens_lo + dens_hi)
     nets = []
-    for i, n in enumerate((120, 360, 700)):
+    for i, n in enumerate(sizes):
         net = racgen.random_network(seed, 100 + i, n, d, dens, 0.3)
         doms = [racgen.assignment_state(seed, 100 + i, s, n, d) for s in range(states)]
         nets.append((net, doms))
@@ -204,6 +218,16 @@ def time_plan(nets, rows, runs, packed=False):
     return float(np.median(ts))
 
 
+MARGIN = 0.01  # a choice replaces the library default only when this much faster
+
+
+def select(times, default):
+    """The fastest choice, unless the library default is within MARGIN of it
+    (timing noise should not move a network off the default)."""
+    best = min(times, key=times.get)
+    return default if times[default] <= times[best] * (1.0 + MARGIN) else best
+
+
 def _layouts(d):
     """Relation layouts worth timing: packed rows differ only for d <= 28."""
     return (False, True) if d <= 28 else (False,)
@@ -214,23 +238,34 @@ def tune(runs=20, seed=7, out=TABLE, log=print):
     entries = []
     for st_lo, st_hi in STATE_BUCKETS:
         states = STATES_TIMED[(st_lo, st_hi)]
-        for d_lo, d_hi in D_BUCKETS:
-            for dens_lo, dens_hi in DENSITY_BUCKETS:
-                d, dens, nets = _bucket_networks(d_lo, d_hi, dens_lo, dens_hi, seed, states)
-                times = {(r, c, pk): time_choice(nets, r, c, runs, pk)
-                         for pk in _layouts(d) for r in admissible_rows(d, pk) for c in CTA_CAPS}
-                best = min(times, key=times.get)
-                default = times[(max(admissible_rows(d)), None, False)]
-                log("states %d d %2d-%2d density %.1f-%.1f: best rows %d ctas %s %s (%.3f ms; "
-                    "library default %.3f ms)" % (states, d_lo, d_hi, dens_lo, dens_hi, best[0],
-                                                  best[1], "packed" if best[2] else "words",
-                                                  times[best], default))
-                entries.append({"d_lo": d_lo, "d_hi": d_hi, "dens_lo": dens_lo,
-                                "dens_hi": dens_hi, "st_lo": st_lo, "st_hi": st_hi,
-                                "rows": best[0], "max_ctas": best[1], "packed": best[2],
-                                "ms": {"%d/%s/%s" % (r, c if c is not None else "all",
-                                                     "packed" if pk else "words"): round(t, 4)
-                                       for (r, c, pk), t in times.items()}})
+        classes = SIZE_CLASSES if st_hi == 1 else [(None, None, MULTI_STATE_SIZES)]
+        for m_lo, m_hi, sizes in classes:
+            for d_lo, d_hi in D_BUCKETS:
+                for dens_lo, dens_hi in DENSITY_BUCKETS:
+                    d, dens, nets = _bucket_networks(d_lo, d_hi, dens_lo, dens_hi, seed, states,
+                                                     sizes)
+                    # the grid cap only for networks too small to fill every
+                    # CTA with tiles of their own
+                    caps = CTA_CAPS if not m_lo else (None,)
+                    times = {(r, c, pk): time_choice(nets, r, c, runs, pk)
+                             for pk in _layouts(d) for r in admissible_rows(d, pk)
+                             for c in caps}
+                    best = select(times, (max(admissible_rows(d)), None, False))
+                    default = times[(max(admissible_rows(d)), None, False)]
+                    log("states %d%s d %2d-%2d density %.1f-%.1f: best rows %d ctas %s %s "
+                        "(%.3f ms; library default %.3f ms)"
+                        % (states, "" if m_lo is None else " m %d-%d" % (m_lo, min(m_hi, 10**9)),
+                           d_lo, d_hi, dens_lo, dens_hi, best[0], best[1],
+                           "packed" if best[2] else "words", times[best], default))
+                    e = {"d_lo": d_lo, "d_hi": d_hi, "dens_lo": dens_lo, "dens_hi": dens_hi,
+                         "st_lo": st_lo, "st_hi": st_hi, "rows": best[0], "max_ctas": best[1],
+                         "packed": best[2], "sizes": list(sizes),
+                         "ms": {"%d/%s/%s" % (r, c if c is not None else "all",
+                                              "packed" if pk else "words"): round(t, 4)
+                                for (r, c, pk), t in times.items()}}
+                    if m_lo is not None:
+                        e["m_lo"], e["m_hi"] = m_lo, m_hi
+                    entries.append(e)
     # networks enforced together in multi-network plans (the batched kernel:
     # its grid is every resident CTA, so only the tile rows are tuned)
     for d_lo, d_hi in D_BUCKETS:
@@ -238,7 +273,7 @@ def tune(runs=20, seed=7, out=TABLE, log=print):
             d, dens, nets = _bucket_networks(d_lo, d_hi, dens_lo, dens_hi, seed, PLAN_STATES)
             times = {(r, pk): time_plan(nets, r, runs, pk)
                      for pk in _layouts(d) for r in admissible_rows(d, pk)}
-            best = min(times, key=times.get)
+            best = select(times, (max(admissible_rows(d)), False))
             log("plan, %d states each: d %2d-%2d density %.1f-%.1f: best rows %d %s (%.3f ms; "
                 "library default %.3f ms)" % (PLAN_STATES, d_lo, d_hi, dens_lo, dens_hi, best[0],
                                               "packed" if best[1] else "words", times[best],
@@ -252,7 +287,8 @@ def tune(runs=20, seed=7, out=TABLE, log=print):
              "states_timed": {"%d-%d" % k: v for k, v in STATES_TIMED.items()},
              "runs": runs, "seed": seed, "created": time.strftime("%Y-%m-%d %H:%M:%S"),
              "key": "ms: 'rows/grid cap/relation rows' -> summed median launch time of the "
-                    "three networks",
+                    "bucket's networks (their variable counts under 'sizes'; plans: 120, "
+                    "360 and 700)",
              "entries": entries}
     with open(out, "w") as f:
         json.dump(table, f, indent=1)

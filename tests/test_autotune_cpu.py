@@ -69,3 +69,21 @@ def test_relation_layout_entries(tmp_path):
     assert autotune.admissible_rows(12, packed=True) == [2, 4, 8, 16, 32]
     assert autotune.words_per_relation(24, packed=True) == 18
     assert autotune.words_per_relation(30, packed=True) == 32
+
+
+def test_one_state_entries_split_by_size(tmp_path):
+    """One-state entries may carry a constraint-count range: the lookup takes
+    the entry whose range holds the network's m (and, without m, the first
+    entry of the bucket)."""
+    path = _write(tmp_path, [
+        {"d_lo": 17, "d_hi": 20, "dens_lo": 0.6, "dens_hi": 1.0, "st_lo": 1, "st_hi": 1,
+         "m_lo": 0, "m_hi": 99999, "rows": 8, "max_ctas": None, "packed": False},
+        {"d_lo": 17, "d_hi": 20, "dens_lo": 0.6, "dens_hi": 1.0, "st_lo": 1, "st_hi": 1,
+         "m_lo": 100000, "m_hi": 1 << 62, "rows": 16, "max_ctas": None, "packed": True},
+    ])
+    assert autotune.table_choice(20, 1.0, 1, path, packed=False, m=5000) == (8, None)
+    assert autotune.table_packed(20, 1.0, 1, path, m=5000) is False
+    assert autotune.table_packed(20, 1.0, 1, path, m=124750) is True
+    assert autotune.table_choice(20, 1.0, 1, path, packed=True, m=124750) == (16, None)
+    assert autotune.table_choice(20, 1.0, 1, path, packed=False, m=124750) == (None, None)
+    assert autotune.table_choice(20, 1.0, 1, path) == (8, None)
