@@ -400,11 +400,27 @@ __device__ void batch_consume_q(BSmem &S, const BatchParams &P, const BatchJob &
   }
 }
 
+// kPk: the instance for plans with a packed network, which also dispatches
+// the packed layout codes; plans of whole-word networks only run the other,
+// whose code is that of a kernel without packed rows.
+template <bool kPk>
 __device__ void batch_consume(BSmem &S, const BatchParams &P, const unsigned char *stage,
                               const BStage &si, int k, int slot_r, int slot_w, int cg, int lw,
                               int lane) {
   const BatchJob J = P.jobs[si.job];
-  switch (J.lcode) {
+  if constexpr (kPk) {
+    switch (J.lcode) {
+      case 17: batch_consume_q<17>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); return;
+      case 18: batch_consume_q<18>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); return;
+      case 19: batch_consume_q<19>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); return;
+      case 20: batch_consume_q<20>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); return;
+      case 21: batch_consume_q<21>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); return;
+      case 22: batch_consume_q<22>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); return;
+      case 23: batch_consume_q<23>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); return;
+      default: break;
+    }
+  }
+  switch (J.q) {
     case 1: batch_consume_q<1>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
     case 2: batch_consume_q<2>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
     case 3: batch_consume_q<3>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
@@ -412,17 +428,11 @@ __device__ void batch_consume(BSmem &S, const BatchParams &P, const unsigned cha
     case 5: batch_consume_q<5>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
     case 6: batch_consume_q<6>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
     case 7: batch_consume_q<7>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
-    case 17: batch_consume_q<17>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
-    case 18: batch_consume_q<18>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
-    case 19: batch_consume_q<19>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
-    case 20: batch_consume_q<20>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
-    case 21: batch_consume_q<21>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
-    case 22: batch_consume_q<22>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
-    case 23: batch_consume_q<23>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
     default: batch_consume_q<8>(S, P, J, stage, si, k, slot_r, slot_w, cg, lw, lane); break;
   }
 }
 
+template <bool kPk>
 __global__ void __launch_bounds__(kBThreads, 1) rac_batch_kernel(const BatchParams P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *ring = smem_raw;
@@ -625,7 +635,7 @@ __global__ void __launch_bounds__(kBThreads, 1) rac_batch_kernel(const BatchPara
           __syncwarp();
           const BStage si = S.stage[stg];
           if (si.job >= 0)
-            batch_consume(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_r, slot_w, cg, lw,
+            batch_consume<kPk>(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_r, slot_w, cg, lw,
                           lane);
           __syncwarp();
           if (lane == 0) mbar_arrive(&S.empty[stg]);
@@ -740,11 +750,12 @@ __global__ void __launch_bounds__(kBThreads, 1) rac_batch_kernel(const BatchPara
 
 }  // namespace
 
-rac_status launch_batch(const BatchParams &P, cudaStream_t stream) {
+template <bool kPk>
+rac_status launch_batch_instance(const BatchParams &P, cudaStream_t stream) {
   static LaunchCache cache;
   const size_t smem = size_t(kBStages) * kStageBytes + sizeof(BSmem);
   int per_sm = 0, sms = 0;
-  rac_status rc = persistent_shape(cache, reinterpret_cast<const void *>(rac_batch_kernel),
+  rac_status rc = persistent_shape(cache, reinterpret_cast<const void *>(rac_batch_kernel<kPk>),
                                    kBThreads, smem, "batched kernel set-up", &per_sm, &sms);
   if (rc != RAC_OK) return rc;
   const int grid = per_sm * sms;
@@ -759,9 +770,14 @@ rac_status launch_batch(const BatchParams &P, cudaStream_t stream) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, rac_batch_kernel, P);
+  e = cudaLaunchKernelEx(&cfg, rac_batch_kernel<kPk>, P);
   if (e != cudaSuccess) return cuda_fail(e, "launch of the batched kernel");
   return RAC_OK;
+}
+
+rac_status launch_batch(const BatchParams &P, cudaStream_t stream) {
+  return P.any_packed ? launch_batch_instance<true>(P, stream)
+                      : launch_batch_instance<false>(P, stream);
 }
 
 }  // namespace rac

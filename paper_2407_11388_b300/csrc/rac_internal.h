@@ -232,6 +232,7 @@ struct BatchParams {
   uint32_t flags;
   uint64_t wait_limit_ns;
   uint32_t rel_evict_first;    // the relation stores exceed L2: stream them evict-first
+  uint32_t any_packed;         // some job's relation rows are packed (RAC_LAYOUT_PACKED)
 };
 constexpr size_t kEvictFirstBytes = size_t(96) << 20;  // relation bytes above which streams go evict-first
 

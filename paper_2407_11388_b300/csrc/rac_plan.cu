@@ -19,6 +19,7 @@ struct rac_plan {
   int32_t n_items = 0, n_jobs = 0, total_states = 0, total_slabs = 0;
   int64_t chg_slot_words = 0, u_slot_words = 0, bufB_words = 0;
   size_t rel_bytes = 0;  // relation stores of the jobs
+  bool any_packed = false;  // some network's relation rows are packed
   // device tables
   BatchJob *jobs = nullptr;
   int64_t *state_off = nullptr, *scratch_off = nullptr, *chg_off = nullptr;
@@ -41,6 +42,7 @@ struct PlanHost {
   int32_t total_slabs = 0;
   int64_t chg_slot_words = 0, u_slot_words = 0, bufB_words = 0;
   size_t rel_bytes = 0;
+  bool any_packed = false;
 };
 
 rac_status build_host_plan(const rac_network *const *nets, int32_t n_nets, int32_t n_items,
@@ -87,6 +89,7 @@ rac_status build_host_plan(const rac_network *const *nets, int32_t n_nets, int32
     H.u_slot_words += net->nb;
     H.total_slabs += J.n_slabs;
     H.rel_bytes += net->rel_bytes;
+    H.any_packed = H.any_packed || net->packed != 0;
     const int32_t job = int32_t(H.jobs.size());
     for (int32_t item : g) {
       H.state_off.push_back(item_dom_off[item]);
@@ -181,6 +184,7 @@ rac_status plan_upload(rac_plan *p, const PlanHost &H, cudaStream_t s) {
   p->u_slot_words = H.u_slot_words;
   p->bufB_words = H.bufB_words;
   p->rel_bytes = H.rel_bytes;
+  p->any_packed = H.any_packed;
   return RAC_OK;
 }
 
@@ -217,6 +221,7 @@ rac_status plan_launch(const rac_plan *p, const uint32_t *dom_in, uint32_t *dom_
   P.flags = flags;
   P.wait_limit_ns = wait_limit_for(flags);
   P.rel_evict_first = p->rel_bytes > kEvictFirstBytes ? 1u : 0u;
+  P.any_packed = p->any_packed ? 1u : 0u;
   return launch_batch(P, s);
 }
 

@@ -36,16 +36,21 @@ def test_packed_every_width(d):
     """Every width (every packed instance, and the unchanged store at d > 28),
     ragged n, dense and sparse graphs, three kinds of input domain, one state
     and several, all flag combinations."""
+    from paper_2407_11388_b300.autotune import admissible_rows
+    rows = max(admissible_rows(d))  # the whole-word default, which packed rows also fit
     for n, scope, rel, doms in width_cases(d):
-        with rac.Network(n, d, scope, rel, layout=PK) as net, \
-                rac.Network(n, d, scope, rel) as plain:
+        with rac.Network(n, d, scope, rel, layout=PK, rows=rows) as net, \
+                rac.Network(n, d, scope, rel, packed=False, rows=rows) as plain:
             info, pinfo = net.info(), plain.info()
             assert info["words_per_relation"] == words_per_relation(d)
-            assert info["n_slabs"] <= pinfo["n_slabs"]
+            assert pinfo["words_per_relation"] == (d + 3) // 4 * 4
+            assert info["n_slabs"] == pinfo["n_slabs"]
             if d > 28:
                 assert info["rel_bytes"] == pinfo["rel_bytes"]
-            elif scope.shape[0] > 0:
-                assert info["rel_bytes"] < pinfo["rel_bytes"]
+            else:
+                assert info["rel_bytes"] <= pinfo["rel_bytes"]
+                if scope.shape[0] >= 64:
+                    assert info["rel_bytes"] < pinfo["rel_bytes"]
             for flags in FLAG_SETS:
                 ref = oracle_enforce(n, d, scope, rel, doms, flags)
                 assert_same(gpu_enforce(n, d, scope, rel, doms[:1], flags, net=net),
@@ -159,7 +164,7 @@ def test_packed_and_whole_word_networks_in_one_plan():
     for i, (n, d) in enumerate(shapes):
         x = racgen.random_network(21, i, n, d, 0.6, 0.3)
         nets_np.append(x)
-        nets.append(rac.Network(n, d, x.scope, x.rel, layout=PK if i % 2 == 0 else rac.LAYOUT_BITS))
+        nets.append(rac.Network(n, d, x.scope, x.rel, packed=i % 2 == 0))
         for s in range(4):
             items.append(i)
             offs.append(pos)
