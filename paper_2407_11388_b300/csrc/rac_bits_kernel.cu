@@ -1109,12 +1109,26 @@ __global__ void __launch_bounds__(threads_for(kVar), 1) rac_bits_kernel(const La
       } else {
         const int64_t stride = P.flag_stride;
         // this sweep's domains D_{k-1} into shared memory
+        // (eight independent loads per thread before any store, so that a
+        // thread waits about one round trip, not one per word)
         if (S.dom_cached) {
-          for (int i = ctid; i < B * n; i += kCW * 32) {
-            const int s = i / n;
-            if (S.st_info[s] & kInfoSweepMask) continue;
-            const uint32_t v = ld_dom(state_view(P, s, k).C + (i - s * n));
-            S.dom[i] = k == 1 ? input_word(P, i - s * n, v) : v;
+          constexpr int kU = 8;
+          const int total = B * n;
+          for (int i0 = ctid; i0 < total; i0 += kU * kCW * 32) {
+            uint32_t v[kU];
+#pragma unroll
+            for (int j = 0; j < kU; ++j) {
+              const int i = i0 + j * kCW * 32, s = i / n;
+              v[j] = i < total && !(S.st_info[s] & kInfoSweepMask)
+                         ? ld_dom(state_view(P, s, k).C + (i - s * n))
+                         : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < kU; ++j) {
+              const int i = i0 + j * kCW * 32, s = i / n;
+              if (i < total && !(S.st_info[s] & kInfoSweepMask))
+                S.dom[i] = k == 1 ? input_word(P, i - s * n, v[j]) : v[j];
+            }
           }
         }
         // clear the slot written next sweep (last read two sweeps ago)
