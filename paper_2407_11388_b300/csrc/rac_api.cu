@@ -74,8 +74,11 @@ NetDev net_dev(const rac_network *net) {
   N.rows_per_slab = net->rows_per_slab;
   N.n_slabs = int32_t(net->n_slabs);
   N.max_ctas = net->max_ctas;
-  N.fp8 = net->d_fp8;
-  N.fp8_jobs = net->fp8_jobs;
+  const size_t tiles = size_t(net->tc_tiles);
+  N.tc_ops = net->d_tc;
+  N.tc_pm = net->d_tc ? net->d_tc + tiles * kTcStoreWordsPerTile : nullptr;
+  N.tc_ij = net->d_tc ? N.tc_pm + tiles * 32 : nullptr;
+  N.tc_tiles = net->tc_tiles;
   N.rel = static_cast<const uint4 *>(net->d_rel);
   N.slabs = net->d_slabs;
   N.slab_feat = net->d_slab_feat;
@@ -207,10 +210,10 @@ rac_status launch_for(const LaunchParams &P, uint32_t flags, cudaStream_t s) {
   return (flags & RAC_KERNEL_TENSOR) ? launch_tc(P, s) : launch_bits(P, s);
 }
 
-// The tensor-core kernel reads the network's FP8 operand store: build it
-// (once) before the launch parameters are taken from the network.
+// The tensor-core kernel reads the network's operand store: build it (once)
+// before the launch parameters are taken from the network.
 rac_status prepare_for(const rac_network *net, uint32_t flags, cudaStream_t s) {
-  return (flags & RAC_KERNEL_TENSOR) ? ensure_fp8(net, s) : RAC_OK;
+  return (flags & RAC_KERNEL_TENSOR) ? ensure_tc_store(net, s) : RAC_OK;
 }
 
 // Largest power of two rows (<= 32) whose slab fits one ring stage, for rw
@@ -425,7 +428,6 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
   net->nb = nb;
   net->rows_per_slab = rows;
   net->max_ctas = int32_t(layout_flags >> 16);
-  net->fp8_jobs = fp8_jobs_for(rows);
   net->m = n_cons;
   net->n_slabs = int64_t(slabs.size());
   net->first.assign(slabs.begin(), slabs.begin() + std::min<size_t>(slabs.size(), kMaxFirst));
@@ -453,7 +455,7 @@ rac_status rac_create_network(int32_t n_vars, int32_t d, int64_t n_cons, const i
                   slab_feat.size() * sizeof(float2))) != cudaSuccess)
     return fail(e, "upload of the slab features");
   if (layout_flags & RAC_LAYOUT_FP8) {
-    const rac_status rc = ensure_fp8(net, nullptr);
+    const rac_status rc = ensure_tc_store(net, nullptr);
     if (rc != RAC_OK) {
       const std::string msg = rac_last_error();
       rac_destroy(net);
@@ -515,7 +517,7 @@ void rac_destroy(rac_network *net) try {
   if (!net) return;
   for (auto &kv : net->ws) free_workspace(kv.second);
   net->ws.clear();
-  cudaFree(net->d_fp8);
+  cudaFree(net->d_tc);
   cudaFree(net->d_rel);
   cudaFree(net->d_slabs);
   cudaFree(net->d_slab_feat);

@@ -79,10 +79,14 @@ struct NetDev {
   int32_t packed;  // 1: packed relation rows (RAC_LAYOUT_PACKED), 0: whole-word rows
   int32_t rw;      // words per stored relation: packed_words(q) or dp
   int32_t max_ctas;  // > 0: grid cap of the network's launches (RAC_LAYOUT_MAX_CTAS)
-  // FP8 operand store of the tensor-core kernel (RAC_LAYOUT_FP8; null until
-  // built): fp8_jobs MMA operand tiles of kFp8TileBytes per slab, slab-major
-  const uint8_t *fp8;
-  int32_t fp8_jobs;
+  // operand store of the tensor-core kernel (RAC_LAYOUT_FP8; null until
+  // built): per tile holding a constraint, kTcStoreWordsPerTile relation
+  // words (both orientations, in the kernel's unit order), 32 presence rows
+  // and the tile's I | J << 16
+  const uint32_t *tc_ops;
+  const uint32_t *tc_pm;
+  const uint32_t *tc_ij;
+  int32_t tc_tiles;
   const uint4 *rel;
   const SlabDesc *slabs;
   const float2 *slab_feat;  // per slab: (tightness, density), the predictor's f3 and f4
@@ -272,11 +276,12 @@ struct rac_network {
   int32_t n = 0, d = 0, dp = 0, q = 0, nb = 0, rows_per_slab = 0;
   int32_t packed = 0, rw = 0;  // packed relation rows; words per stored relation
   int32_t max_ctas = 0;  // RAC_LAYOUT_MAX_CTAS, 0: none
-  // the tensor-core kernel's FP8 operand store (RAC_LAYOUT_FP8, or built by
-  // the first RAC_KERNEL_TENSOR call under mu)
-  mutable uint8_t *d_fp8 = nullptr;
-  mutable size_t fp8_bytes = 0;
-  int32_t fp8_jobs = 0;
+  // the tensor-core kernel's operand store (RAC_LAYOUT_FP8, or built by the
+  // first RAC_KERNEL_TENSOR call under mu): relation words, then presence
+  // rows, then tile coordinates, in one allocation
+  mutable uint32_t *d_tc = nullptr;
+  mutable size_t tc_bytes = 0;
+  mutable int32_t tc_tiles = 0;
   int64_t m = 0;
   int64_t n_slabs = 0;
   size_t rel_bytes = 0;
@@ -312,18 +317,15 @@ LaunchParams base_params(const rac_network *net, Workspace *w, int n_states, int
                          uint32_t flags);
 // Launch the bit-packed kernel for P (grid sized by the callee).
 rac_status launch_bits(const LaunchParams &P, cudaStream_t stream);
-// Launch the tensor-core kernel for P (at most 128 states; P.net.fp8 set).
+// Launch the tensor-core kernel for P (at most 128 states; P.net.tc_ops set).
 rac_status launch_tc(const LaunchParams &P, cudaStream_t stream);
 constexpr int kTensorMaxStates = 128;
-// The tensor-core kernel's operand tiles: 256 rows (8 relations x 32 values)
-// of 32 one-byte E4M3 entries (K = 32 values), 8 KiB each.
-constexpr int kFp8TileBytes = 8192;
-// MMA jobs of a slab of `rows` rows: a forward job per (8-row group, column),
-// a reverse job per (row, 8-column group).
-inline int fp8_jobs_for(int rows) { return 32 * ((rows + 7) / 8) + 4 * rows; }
-// Builds net's FP8 operand store if it has none yet (thread-safe; the first
-// call allocates and expands the bit-packed store on `stream` and waits).
-rac_status ensure_fp8(const rac_network *net, cudaStream_t stream);
+// The tensor-core kernel's relation words of one 32 x 32-variable tile: two
+// directions x 8 units x 32 groups x 4 relations x 32 rows.
+constexpr int kTcStoreWordsPerTile = 2 * 8 * 32 * 128;
+// Builds net's tensor-core operand store if it has none yet (thread-safe;
+// the first call allocates and fills it on `stream` and waits).
+rac_status ensure_tc_store(const rac_network *net, cudaStream_t stream);
 const uint4 *predictor_pack(const rac_predictor *p);  // fragment-packed weights
 int predictor_device(const rac_predictor *p);
 Workspace *get_workspace(const rac_network *net, cudaStream_t stream, int n_states, int n_items,

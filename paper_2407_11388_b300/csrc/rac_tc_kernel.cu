@@ -1,46 +1,64 @@
 // Kernel (b): the support counts of Eq. 1 on the 5th-generation tensor cores
-// (tcgen05.mma, FP8 E4M3 0/1 operands, FP32 accumulation in tensor memory),
-// for up to 128 domain states of one network, swept to the fixpoint in one
-// persistent cooperative launch.
+// (tcgen05.mma kind::f8f6f4, E5M2 0/1 operands, FP32 accumulation in tensor
+// memory), for up to 128 domain states of one network, swept to the fixpoint
+// in one persistent cooperative launch.
 //
-// For every relation R_xy of a slab and every state s the counts are
-//   forward  Sup_xy[a](s) = sum_b R[a][b] D_s[y][b]     (Fig. 1)
+// For a relation R_xy and a state s the counts of Fig. 1 are
+//   forward  Sup_xy[a](s) = sum_b R[a][b] D_s[y][b]
 //   reverse  Sup_yx[b](s) = sum_a R[a][b] D_s[x][a]
-// computed as MMAs with M = 128 states, K = 32 values and N = 256 = 8
-// relations x 32 rows: a forward job per (group of 8 rows, column y) takes
-// D_s[y] as A and the 8 relations R_{x,y} as B; a reverse job per (row x,
-// group of 8 columns) takes D_s[x] as A and the 8 transposed relations as B.
-// Counts are exact in FP32 (at most 32).  The epilogue reads the accumulator
-// lanes (one state per lane), clamps every count to {0,1} (only Sup > 0
-// matters, as in the paper's listing), packs the 32 values of a relation row
-// into one word and ANDs it over the row's or column's constraints; the
-// removals then follow kernel (a) (atomicAnd into the next domain buffer).
+// and only whether a count is positive matters (the clamp of the paper's
+// listing).  Here the relation rows are the MMA's M axis and the states its N
+// axis, so every tensor-memory lane quarter (and every SM sub-partition)
+// works whatever the number of states:
+//   M = 128 rows: four relations x 32 rows (rows >= d are zero), their FP8
+//       entries written straight into tensor memory by the A-operand warps
+//       (tcgen05.st) from the relation's bit words -- no shared-memory copy;
+//   K = 32 values of the other variable, in three K-blocks;
+//   N = 16, 32 or 48 columns, each holding THREE states: state slot 3c + j
+//       sits in K-block j of column c with the entry weight 2^-13, 2^-7 or
+//       2^1 (one bit of an E5M2 byte each), and the A entries are 2.0, so
+//       column c accumulates 2^-12 (n_0 + 64 n_1 + 16384 n_2) with the three
+//       counts n_j <= 32 in separate 6-bit fields, exactly (integers below
+//       2^20 scaled by a power of two).
+// The epilogue turns a column into its three tests with one FFMA, which adds
+// 2^23 + 31 (1 + 64 + 16384) and puts the sum's integer in the mantissa bits,
+// where field j's bit 5 is set iff n_j >= 1; one AND per column then folds a
+// constraint into the running AND over C_x -- two instructions per three
+// (row, state) tests.  After a unit's 32 constraints every row's bit per
+// state is gathered with a warp ballot and removals follow kernel (a)
+// (atomicAnd into the next domain buffer, change marks).
 //
-// The B operands are the network's FP8 operand store (RAC_LAYOUT_FP8: every
-// job's tile expanded once, on the device, in the MMA's shared-memory layout),
-// brought in by bulk copies.  A slab's jobs run through a pipeline of warps
-// that wait on mbarriers only (no CTA-wide barrier per MMA):
-//   warps 0-15   epilogue: TMEM lane quarter warp % 4 (32 states), a
-//                quarter of each job's 8 relations (warp / 4); they keep a
-//                slab's AND masks in registers and make its removals;
-//   warps 16-19  A tiles: the states' domain word of the job's column (or
-//                row) expanded to E4M3 bytes, 32 states each;
-//   warp 20      B tiles: one bulk copy of 8 KiB per job;
-//   warp 21      MMA issuer: waits for the job's A and B tiles and a free
-//                accumulator, issues the MMA, and commits its completion to
-//                the A and B stages it frees and to the accumulator's full
-//                barrier;
-//   warp 22      helps stage the slab's domain words;
-//   warp 23      streams the bit-packed slabs (their headers name the
-//                relations present) into a small ring, as in kernel (a).
-// Four epilogue warps per quarter keep several tensor-memory loads in
-// flight on each SM sub-partition.
-// An A ring of four stages, a B ring of eight (64 KiB of copies in flight)
-// and two accumulators of 256 columns let the roles run apart by several
-// jobs.
+// Work: the network's variables form blocks of 32; a constraint lies in tile
+// (I, J) = (min/32, max/32).  An item is one direction of one tile: forward
+// (rows x of block I against the 32 variables y of block J) or reverse (rows
+// y of block J against the x of block I).  Its 8 units take four variables
+// each (one MMA row group of 128), and a unit's 32 groups are the 32
+// variables of the other block -- three MMAs each (one per K-block), whose
+// B operands (the other variable's domain words of every running state,
+// expanded to E5M2 with the field weights) are built once per item in shared
+// memory.  Items are claimed from a grid-wide counter.
+//
+// Roles (one CTA per SM, 448 threads):
+//   warps 0-3   A operands: lane quarter q = warp; lane a writes row a of
+//               the group's relation q into a 16-slot ring of tensor-memory
+//               A tiles (8 columns each);
+//   warps 4-11  epilogue: quarter warp % 4, two parts taking alternate
+//               groups (accumulator slots of one parity) with their own
+//               running ANDs; each part makes the removals its AND implies
+//               (two partial ANDs applied by atomicAnd give the full AND);
+//   warp 12     lane 0 issues the MMAs and commits their completion to the
+//               A slot and the accumulator;
+//   warp 13     claims items, publishes them through a two-deep queue and
+//               streams each unit's 16 KiB of relation words into a
+//               three-stage ring (cp.async.bulk).
+// Every role waits on mbarriers only; the consumer warps meet on a named
+// barrier four times per item (the B operands are rebuilt per item).  Every
+// wait is bounded, and one that runs out aborts the launch (RAC_EBARRIER).
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <unordered_map>
+#include <vector>
 
 #include "rac_device.cuh"
 #include "rac_internal.h"
@@ -51,52 +69,79 @@ namespace {
 using namespace dev;
 
 // warp roles (see the file comment)
-constexpr int kTcEpiParts = 4;                   // epilogue warps per TMEM lane quarter
-constexpr int kTcEpiWarps = 4 * kTcEpiParts;      // warps 0-15
-constexpr int kRelPerPart = 8 / kTcEpiParts;      // a job's relations per epilogue warp
-constexpr int kTcAWarp0 = kTcEpiWarps, kTcAWarps = 4;  // warps 16-19
-constexpr int kTcBWarp = kTcAWarp0 + kTcAWarps;        // warp 20
-constexpr int kTcMmaWarp = kTcBWarp + 1;               // warp 21
-constexpr int kTcConsumerWarps = kTcMmaWarp + 2;  // warps 0-22 (22 helps stage the domains);
-                                                  // warp 23 streams the bit-packed slabs
-constexpr int kTcThreads = (kTcConsumerWarps + 1) * 32;
-constexpr int kTcStages = 2;   // bit-packed slab ring
-constexpr int kTcAStages = 4;  // A operand ring (built on chip)
-constexpr int kTcBStages = 8;  // B operand ring (8 KiB copies in flight from HBM)
-constexpr int kTcMaxStates = 128;  // M of the MMA
-constexpr int kTcN = 256;          // N of the MMA: 8 relations x 32 rows
-constexpr uint32_t kTmemCols = 512;  // two accumulators of 256 columns
-constexpr int kATileBytes = kTcMaxStates * 32;  // 4 KB
-constexpr int kBTileBytes = kFp8TileBytes;      // 8 KB
-static_assert(kBTileBytes == kTcN * 32, "a B tile is N rows of 32 bytes");
-constexpr int kTcDomWords = 64;  // per state: 32 columns + up to 32 rows
+constexpr int kTcAWarps = 4;                             // warps 0-3
+constexpr int kTcEpiParts = 2;                           // epilogue warps per lane quarter
+constexpr int kTcEpiWarp0 = kTcAWarps;                   // warps 4-11
+constexpr int kTcEpiWarps = 4 * kTcEpiParts;
+constexpr int kTcMmaWarp = kTcEpiWarp0 + kTcEpiWarps;    // warp 12
+constexpr int kTcConsumerWarps = kTcMmaWarp + 1;         // warps 0-12
+constexpr int kTcThreads = (kTcConsumerWarps + 1) * 32;  // + warp 13, the producer
+constexpr int kTcCT = kTcConsumerWarps * 32;             // consumer threads
 
-struct TcStage {
-  int32_t sl;
-  uint32_t ij, rows, pad;
-};
+constexpr int kF = 3;                           // states per accumulator column
+constexpr int kTcMaxStates = kTensorMaxStates;  // 128
+constexpr int kNMax = 48;                       // N for up to 144 state slots
+static_assert(kNMax * kF >= kTcMaxStates && kNMax % 16 == 0, "N covers the states");
+constexpr int kAccSlots = 6, kAccCols = 64;  // accumulators: 6 x 64 columns
+constexpr int kASlots = 16, kACols = 8;      // A tiles: 128 lanes x 32 bytes
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kACol0 = kAccSlots * kAccCols;
+static_assert(kACol0 + kASlots * kACols <= kTmemCols, "tensor memory of one CTA");
+static_assert(kAccSlots % kTcEpiParts == 0 && kTcEpiParts == 2,
+              "a part owns the accumulator slots of one parity");
+constexpr int kGroups = 32;                 // groups (constraint columns) per unit
+constexpr int kUnitWords = kGroups * 128;   // a unit's relation words
+constexpr uint32_t kUnitBytes = kUnitWords * 4;
+constexpr int kRing = 3;
+constexpr int kBTileBytes = (kNMax / 8) * 256;    // one (variable, K-block) B tile
+constexpr int kBSetBytes = 32 * kF * kBTileBytes;  // the item's 32 variables
+constexpr int kDStride = 33;                       // staged domain words, padded
+static_assert(kTcStoreWordsPerTile == 2 * 8 * kUnitWords, "store layout");
+
+// E5M2 entries: A = 2.0 (0x40, bit 6); B of K-block j = 2^-13, 2^-7, 2^1
+// (0x08, 0x20, 0x40: bits 3, 5, 6), so A x B = 2^-12 x {1, 64, 16384}.
+constexpr int kABit = 6;
+__device__ __forceinline__ int field_bit(int j) { return j == 0 ? 3 : (j == 1 ? 5 : 6); }
+// field j of X = n_0 + 64 n_1 + 16384 n_2 starts at bit 0, 6, 14; with
+// kC = 31 in every field, bit 5 of field j of X + kC is set iff n_j >= 1
+constexpr uint32_t kC = 31u + (31u << 6) + (31u << 14);
+constexpr float kMagic = float(8388608u + kC);  // 2^23 + kC, exact in FP32
+__device__ __forceinline__ int guard_bit(int j) { return j == 0 ? 5 : (j == 1 ? 11 : 19); }
+// instruction descriptor: FP32 accumulator, E5M2 A and B, K-major, M = 128
+__device__ __forceinline__ uint32_t idesc_for(int ncols) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(ncols >> 3) << 17) |
+         (uint32_t(128 >> 4) << 24);
+}
+
+// Four bits (bit i of nib) -> four bytes, each 1 << t or 0.  The four
+// shifted copies of nib land at distinct bit positions (7 i + t for bit i),
+// so the product has no carries.
+__device__ __forceinline__ uint32_t spread4(uint32_t nib, int t) {
+  return (nib * (0x00204081u << t)) & (0x01010101u << t);
+}
 
 struct TcSmem {
-  uint8_t a_tile[kTcAStages][kATileBytes];
-  uint8_t b_tile[kTcBStages][kBTileBytes];
-  uint32_t dom[kTcMaxStates][kTcDomWords];  // staged D_{k-1} words of the slab
-  uint64_t full[kTcStages];
-  uint64_t empty[kTcStages];
-  uint64_t a_full[kTcAStages], a_empty[kTcAStages];
-  uint64_t b_full[kTcBStages], b_empty[kTcBStages];
-  uint64_t acc_full[2], acc_empty[2];
-  TcStage stage[kTcStages];
-  uint32_t stage_ok[kTcStages];
+  uint8_t bset[kBSetBytes];          // B tiles of the item's 32 variables
+  uint32_t ring[kRing][kUnitWords];  // relation words of a unit
+  uint32_t dstage[kNMax * kF][kDStride];  // domain words of the item's 32 variables
+  uint64_t ring_full[kRing], ring_empty[kRing];
+  uint64_t a_full[kASlots], a_empty[kASlots];
+  uint64_t acc_full[kAccSlots], acc_empty[kAccSlots];
+  uint64_t item_full[2], item_empty[2];
+  int32_t item_q[2];
+  int32_t cur_item;
+  uint32_t active;  // units of the current item with a constraint
+  uint32_t pm[32];  // presence rows of the current item's tile
   uint32_t tmem_base;
-  uint32_t mma_issued, b_issued;
+  uint32_t mma_issued, ring_issued;
   uint32_t base, poisoned, abort, failed, all_done;
   uint32_t any_total, wipe_total, cta_any, cta_wipe;
+  int32_t n_slots, ncols;
+  uint8_t slot_state[kNMax * kF];
   uint32_t st_info[kTcMaxStates];
   uint8_t any_loc[kTcMaxStates], wipe_loc[kTcMaxStates];
 };
-static_assert(size_t(kTcStages) * kStageBytes + sizeof(TcSmem) + 1024 <= 232448,
-              "shared memory of the tensor-core kernel exceeds 227 KB");
-static_assert((size_t(kTcStages) * kStageBytes) % 128 == 0, "operand tiles 128-byte aligned");
+static_assert(sizeof(TcSmem) + 1024 <= 232448, "shared memory of the tensor-core kernel");
 
 constexpr uint32_t kInfoSweepMask = 0xFFFFFFu;
 constexpr uint32_t kInfoResB = 1u << 24;
@@ -107,8 +152,8 @@ constexpr int kConsumersBar = 1;
 
 // ------------------------------ tcgen05 helpers ------------------------------
 // Shared-memory matrix descriptor: K-major, no swizzle; LBO = 128 B between
-// core matrices along K, SBO = 256 B between 8-row groups (bits 46-47 hold the
-// descriptor version of this architecture).
+// the two 16-byte K halves of a row group, SBO = 256 B between 8-row groups
+// (bits 46-47 hold the descriptor version of this architecture).
 __device__ __forceinline__ uint64_t umma_desc(const void *tile) {
   uint64_t d = uint64_t((smem_u32(tile) >> 4) & 0x3FFFu);
   d |= uint64_t(128u >> 4) << 16;
@@ -116,15 +161,13 @@ __device__ __forceinline__ uint64_t umma_desc(const void *tile) {
   d |= uint64_t(1) << 46;
   return d;
 }
-// Instruction descriptor: FP32 accumulator, E4M3 A and B, both K-major,
-// N = 256, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (uint32_t(kTcN >> 3) << 17) | (uint32_t(128 >> 4) << 24);
-
-__device__ __forceinline__ void umma_f8(uint32_t tmem_d, uint64_t da, uint64_t db) {
+// D[tmem] (+)= A[tmem] x B[smem]
+__device__ __forceinline__ void umma_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t db,
+                                        uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(da), "l"(db), "r"(kIdesc), "r"(0)
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(db), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
@@ -142,28 +185,30 @@ __device__ __forceinline__ void tc_fence_after() {
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-// 32 consecutive accumulator columns of this warp's 32 lanes.
-__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32]) {
+// 16 consecutive columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t *v) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
         "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
-        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
-        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        "=r"(v[14]), "=r"(v[15])
       : "r"(addr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// 8 consecutive columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_st8(uint32_t addr, const uint32_t (&v)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(addr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
 
-// Byte offset of element (row, k) in a K-major 32-byte-K tile.
-__device__ __forceinline__ uint32_t tile_off(uint32_t row, uint32_t k) {
-  return (row >> 3) * 256u + (k >> 4) * 128u + (row & 7u) * 16u + (k & 15u);
-}
-// Four bits (bit i of nib) -> four bytes, 0x38 (E4M3 1.0) or 0.
-__device__ __forceinline__ uint32_t expand4(uint32_t nib) {
-  return ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
-}
 struct TcView {
   const uint32_t *C;
   uint32_t *T;
@@ -220,42 +265,41 @@ __device__ __forceinline__ uint32_t rel_row(const uint32_t *hdr, const uint32_t 
   return relw[(base_chunk + uint32_t(a >> 2) * cnt + t) * 4u + uint32_t(a & 3)];
 }
 
-// The FP8 operand store: word w of tile (slab sl, job idx), job order as in
-// tc_consume (forward jobs g * 32 + j, then reverse jobs 32 rg + g nrows + r).
-__global__ void __launch_bounds__(256) rac_fp8_build_kernel(const NetDev N, uint8_t *out) {
-  const int64_t total = int64_t(N.n_slabs) * N.fp8_jobs * (kFp8TileBytes / 4);
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += stride) {
-    const int64_t t = i / (kFp8TileBytes / 4);
-    const int w = int(i % (kFp8TileBytes / 4));
-    const int sl = int(t / N.fp8_jobs), idx = int(t % N.fp8_jobs);
+// The operand store, one warp per (slab, row, column) relation slot: lane a
+// writes the forward word (row a of R_xy, bits over b) and, after a ballot
+// per b, lane b the reverse word (column b of R_xy, bits over a), and the
+// relation's presence bit.  Unit (tile, dir, mt) holds words [g][q][lane] of
+// its 32 groups g (the other block's variables) and 4 relations q.
+__global__ void __launch_bounds__(256) rac_tc_store_kernel(const NetDev N,
+                                                           const int32_t *slab_tile,
+                                                           uint32_t *ops, uint32_t *pmt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t total = int64_t(N.n_slabs) * 1024;
+  const int64_t stride = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t w = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total;
+       w += stride) {
+    const int sl = int(w >> 10), r = int((w >> 5) & 31), j = int(w & 31);
     const SlabDesc sd = N.slabs[sl];
+    const uint32_t nrows = sd.rows >> 8, row0 = sd.rows & 0xFFu;
+    if (uint32_t(r) >= nrows) continue;
     const uint32_t *hdr = reinterpret_cast<const uint32_t *>(N.rel + sd.rel_off16);
-    const uint32_t nrows = sd.rows >> 8;
+    if (!((hdr[r] >> j) & 1u)) continue;  // warp-uniform
     const uint32_t *relw = hdr + 2 * nrows;
-    const int rg = int(nrows + 7) / 8;
-    const int row = w >> 3, qq = w & 7;
-    uint32_t nib = 0u;
-    if (idx < 32 * rg) {  // forward: rows (r, a) of R_{x_r, y_j}, K = b
-      const int j = idx & 31, g = idx >> 5;
-      const int r = 8 * g + (row >> 5), a = row & 31;
-      if (r < int(nrows) && ((hdr[r] >> j) & 1u)) {
-        const uint32_t t_rank = __popc(hdr[r] & ((1u << j) - 1u));
-        nib = (rel_row(hdr, relw, nrows, N, r, t_rank, a) >> (4 * qq)) & 0xFu;
-      }
-    } else {  // reverse: rows (j, b) of R_{x_r, y_j} transposed, K = a
-      const int ridx = idx - 32 * rg;
-      const int r = ridx % int(nrows), g = ridx / int(nrows);
-      const int j = 8 * g + (row >> 5), b = row & 31;
-      if ((hdr[r] >> j) & 1u) {
-        const uint32_t t_rank = __popc(hdr[r] & ((1u << j) - 1u));
-#pragma unroll
-        for (int i2 = 0; i2 < 4; ++i2)
-          nib |= ((rel_row(hdr, relw, nrows, N, r, t_rank, 4 * qq + i2) >> b) & 1u) << i2;
-      }
+    const uint32_t t_rank = __popc(hdr[r] & ((1u << j) - 1u));
+    const uint32_t row = rel_row(hdr, relw, nrows, N, r, t_rank, lane);
+    uint32_t col = 0u;
+#pragma unroll 8
+    for (int b = 0; b < 32; ++b) {
+      const uint32_t bal = __ballot_sync(kFull, (row >> b) & 1u);
+      if (lane == b) col = bal;
     }
-    *reinterpret_cast<uint32_t *>(out + t * kFp8TileBytes + tile_off(uint32_t(row), 4u * qq)) =
-        expand4(nib);
+    const int64_t t = slab_tile[sl];
+    const int xl = int(row0) + r, yl = j;
+    uint32_t *fw = ops + ((t * 2 + 0) * 8 + xl / 4) * kUnitWords;
+    uint32_t *rv = ops + ((t * 2 + 1) * 8 + yl / 4) * kUnitWords;
+    fw[yl * 128 + (xl & 3) * 32 + lane] = row;
+    rv[xl * 128 + (yl & 3) * 32 + lane] = col;
+    if (lane == 0) atomicOr(pmt + t * 32 + xl, 1u << yl);
   }
 }
 
@@ -278,219 +322,209 @@ __device__ __forceinline__ bool warp_wait(TcSmem &S, const LaunchParams &P, uint
   }
   return __shfl_sync(kFull, ok, 0) != 0u;
 }
-
-// Packs the 32 counts of one relation row (one state per lane) into a word:
-// bit a set iff count a > 0 (the listing's clamp).  FP32 counts are >= 0, so
-// a count is positive iff its bits are not all zero.
-__device__ __forceinline__ uint32_t pack_positive(const uint32_t (&v)[32]) {
-  uint32_t m = 0u;
-#pragma unroll
-  for (int a = 0; a < 32; ++a) m |= (v[a] != 0u ? 1u : 0u) << a;
-  return m;
+__device__ __forceinline__ bool lane_wait(TcSmem &S, const LaunchParams &P, uint64_t *bar,
+                                          uint32_t parity) {
+  if (aborted(S) || !mbar_wait(bar, parity, &P.sync->err, P.wait_limit_ns)) {
+    S.abort = 1u;
+    return false;
+  }
+  return true;
 }
 
-// The whole slab for every running state: 32 rg forward jobs and 4 nrows
-// reverse jobs, each through the A / B / MMA / epilogue pipeline.  jc counts
-// the CTA's jobs so far (the same in every role: ring stages and phases).
-__device__ void tc_consume(TcSmem &S, const LaunchParams &P, const unsigned char *stage,
-                           const TcStage &si, int k, int slot_w, int warp, int lane,
-                           uint32_t &jc) {
-  const NetDev &N = P.net;
-  const int n = N.n, B = P.n_states;
-  const uint32_t I = si.ij & 0xFFFFu, J = si.ij >> 16;
-  const uint32_t row0 = si.rows & 0xFFu, nrows = si.rows >> 8;
-  const uint32_t *hdr = reinterpret_cast<const uint32_t *>(stage);
-  const int ct = warp * 32 + lane;  // consumer thread
-  constexpr int nct = kTcConsumerWarps * 32;
-
-  // stage this slab's domain words of every state: [0,32) columns, [32,..) rows
-  for (int i = ct; i < B * kTcDomWords; i += nct) {
-    const int st = i / kTcDomWords, w = i % kTcDomWords;
-    const TcView V = tc_view(P, st, k);
-    uint32_t val = 0u;
-    if (w < 32) {
-      const int yy = int(J) * 32 + w;
-      if (yy < n) val = ld_dom(V.C + yy);
-    } else if (uint32_t(w - 32) < nrows) {
-      const int xx = int(I) * 32 + int(row0) + (w - 32);
-      if (xx < n) val = ld_dom(V.C + xx);
-    }
-    S.dom[st][w] = val;
-  }
-  named_bar(kConsumersBar, nct);
-
-  const int rg = int(nrows + 7) / 8;
-  const int n_jobs = 32 * rg + 4 * int(nrows);
-  if (warp >= kTcAWarp0 && warp < kTcAWarp0 + kTcAWarps) {
-    // A tiles: state s's word of the job's column (forward) or row (reverse)
-    const int s = (warp - kTcAWarp0) * 32 + lane;
-    for (int idx = 0; idx < n_jobs; ++idx) {
-      const uint32_t c = jc + uint32_t(idx);
-      const int st = int(c % kTcAStages);
-      if (!warp_wait(S, P, &S.a_empty[st], ((c / kTcAStages) & 1u) ^ 1u, lane)) break;
-      const int word = idx < 32 * rg ? (idx & 31) : 32 + (idx - 32 * rg) % int(nrows);
-      const uint32_t w = s < B ? S.dom[s][word] : 0u;
-      uint8_t *At = S.a_tile[st];
+// The B operands of an item: tile (v, j) holds, in row c, the domain word of
+// variable vbase + v in the state of slot 3c + j, expanded to E5M2 bytes of
+// weight bit field_bit(j) (zero rows for slots without a running state).
+__device__ void build_bset(TcSmem &S, const LaunchParams &P, int k, int vbase, int ct) {
+  const int n = P.net.n, R = S.n_slots, ncols = S.ncols, nslots = ncols * kF;
+  // the words, coalesced over the 32 variables, into dstage[slot][v]
+  const int total = 32 * nslots;
+  constexpr int kPer = (32 * kNMax * kF + kTcCT - 1) / kTcCT;
+  uint32_t w[kPer];
 #pragma unroll
-      for (int qq = 0; qq < 8; ++qq)
-        *reinterpret_cast<uint32_t *>(At + tile_off(uint32_t(s), 4u * qq)) =
-            expand4((w >> (4 * qq)) & 0xFu);
-      fence_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&S.a_full[st]);
-    }
-  } else if (warp == kTcBWarp) {
-    // B tiles: the job's 8 KiB of the FP8 operand store
-    if (lane == 0) {
-      const uint8_t *tiles = N.fp8 + size_t(si.sl) * size_t(N.fp8_jobs) * kFp8TileBytes;
-      for (int idx = 0; idx < n_jobs; ++idx) {
-        const uint32_t c = jc + uint32_t(idx);
-        const int st = int(c % kTcBStages);
-        if (aborted(S) || !mbar_wait(&S.b_empty[st], ((c / kTcBStages) & 1u) ^ 1u,
-                                     &P.sync->err, P.wait_limit_ns)) {
-          S.abort = 1u;
-          break;
-        }
-        mbar_arrive_expect_tx(&S.b_full[st], kBTileBytes);
-        bulk_copy_g2s(S.b_tile[st], tiles + size_t(idx) * kFp8TileBytes, kBTileBytes,
-                      &S.b_full[st]);
-        S.b_issued = c + 1u;
+  for (int r = 0; r < kPer; ++r) {
+    const int t = ct + r * kTcCT;
+    const int v = t & 31, i = t >> 5;
+    w[r] = (t < total && i < R && vbase + v < n)
+               ? ld_dom(tc_view(P, S.slot_state[i], k).C + vbase + v)
+               : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kPer; ++r) {
+    const int t = ct + r * kTcCT;
+    if (t < total) S.dstage[t >> 5][t & 31] = w[r];
+  }
+  named_bar(kConsumersBar, kTcCT);
+  // rows of the B tiles, 16-byte chunks of consecutive rows per thread group
+  for (int t = ct; t < total; t += kTcCT) {
+    const int c = t % ncols, vj = t / ncols;
+    const int j = vj % kF, v = vj / kF;
+    const uint32_t word = S.dstage[kF * c + j][v];
+    const int fb = field_bit(j);
+    uint32_t e[8];
+#pragma unroll
+    for (int h = 0; h < 8; ++h) e[h] = spread4((word >> (4 * h)) & 0xFu, fb);
+    uint8_t *row = S.bset + (v * kF + j) * kBTileBytes + (c >> 3) * 256 + (c & 7) * 16;
+    *reinterpret_cast<uint4 *>(row) = make_uint4(e[0], e[1], e[2], e[3]);
+    *reinterpret_cast<uint4 *>(row + 128) = make_uint4(e[4], e[5], e[6], e[7]);
+  }
+}
+
+// One item (a direction of a tile) through the A / MMA / epilogue pipeline.
+// gc counts the CTA's groups so far and rc its ring stages (the same in
+// every role: slots and phases).
+__device__ void tc_item(TcSmem &S, const LaunchParams &P, int item, int k, int slot_w, int warp,
+                        int lane, uint32_t gc, uint32_t rc) {
+  const NetDev &N = P.net;
+  const int tile = item >> 1, dir = item & 1;
+  const uint32_t ij = N.tc_ij[tile];
+  const int I = int(ij & 0xFFFFu), J = int(ij >> 16);
+  const uint32_t active = S.active;
+  const int R = S.n_slots, ncols = S.ncols;
+
+  if (warp < kTcAWarps) {
+    // A tiles: lane a writes row a of relation q = warp of each group
+    const int q = warp;
+    const uint32_t arow = S.tmem_base + (uint32_t(q * 32) << 16) + kACol0;
+    bool ok = true;
+    for (int mt = 0; mt < 8; ++mt) {
+      if (!((active >> mt) & 1u)) continue;
+      const int r = int(rc % kRing);
+      if (ok) ok = warp_wait(S, P, &S.ring_full[r], (rc / kRing) & 1u, lane);
+      const uint32_t *U = S.ring[r];
+      for (int g = 0; g < kGroups; ++g, ++gc) {
+        const uint32_t sa = gc % kASlots;
+        if (ok) ok = warp_wait(S, P, &S.a_empty[sa], ((gc / kASlots) & 1u) ^ 1u, lane);
+        if (!ok) continue;
+        const uint32_t wrd = U[g * 128 + q * 32 + lane];
+        uint32_t e[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) e[h] = spread4((wrd >> (4 * h)) & 0xFu, kABit);
+        tmem_st8(arow + sa * kACols, e);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.a_full[sa]);
       }
+      __syncwarp();
+      if (ok && lane == 0) mbar_arrive(&S.ring_empty[r]);
+      ++rc;
     }
   } else if (warp == kTcMmaWarp) {
     if (lane == 0) {
-      for (int idx = 0; idx < n_jobs; ++idx) {
-        const uint32_t c = jc + uint32_t(idx);
-        const int sa = int(c % kTcAStages), sb = int(c % kTcBStages);
-        const int ab = int(c & 1u);
-        if (aborted(S) ||
-            !mbar_wait(&S.a_full[sa], (c / kTcAStages) & 1u, &P.sync->err, P.wait_limit_ns) ||
-            !mbar_wait(&S.b_full[sb], (c / kTcBStages) & 1u, &P.sync->err, P.wait_limit_ns) ||
-            !mbar_wait(&S.acc_empty[ab], ((c >> 1) & 1u) ^ 1u, &P.sync->err, P.wait_limit_ns)) {
-          S.abort = 1u;
-          break;
+      const uint32_t idesc = idesc_for(ncols);
+      const uint64_t bdesc0 = umma_desc(S.bset);
+      bool ok = true;
+      for (int mt = 0; mt < 8 && ok; ++mt) {
+        if (!((active >> mt) & 1u)) continue;
+        for (int g = 0; g < kGroups; ++g, ++gc) {
+          const uint32_t sa = gc % kASlots, sc = gc % kAccSlots;
+          if (!(ok = lane_wait(S, P, &S.a_full[sa], (gc / kASlots) & 1u) &&
+                     lane_wait(S, P, &S.acc_empty[sc], ((gc / kAccSlots) & 1u) ^ 1u)))
+            break;
+          tc_fence_after();
+          const uint32_t d = S.tmem_base + sc * kAccCols;
+          const uint32_t a = S.tmem_base + kACol0 + sa * kACols;
+#pragma unroll
+          for (int j = 0; j < kF; ++j)
+            umma_ts(d, a, bdesc0 + uint64_t(((g * kF + j) * kBTileBytes) >> 4), idesc,
+                    j > 0 ? 1u : 0u);
+          umma_commit(&S.a_empty[sa]);
+          umma_commit(&S.acc_full[sc]);
+          S.mma_issued = gc + 1u;
         }
-        tc_fence_after();
-        umma_f8(S.tmem_base + uint32_t(ab) * 256u, umma_desc(S.a_tile[sa]),
-                umma_desc(S.b_tile[sb]));
-        umma_commit(&S.a_empty[sa]);
-        umma_commit(&S.b_empty[sb]);
-        umma_commit(&S.acc_full[ab]);
-        S.mma_issued = c + 1u;
       }
     }
-  } else if (warp < kTcEpiWarps) {
-    const int quarter = warp & 3, part = warp >> 2;
-    const int s = quarter * 32 + lane;  // this thread's state
-    const bool s_ok = s < B && !(S.st_info[s] & kInfoSweepMask);
-    // a quarter without running states only keeps the accumulators moving
-    const bool live = __any_sync(kFull, s_ok);
-    const uint32_t tq = S.tmem_base + (uint32_t(quarter * 32) << 16);
-    // AND masks of this part's rows (forward) and columns (reverse): with
-    // R = kRelPerPart, facc[R g + i] for row 8 g + R part + i and racc[R g + i]
-    // for column 8 g + R part + i
-    constexpr int R = kRelPerPart;
-    uint32_t facc[4 * R], racc[4 * R];
-#pragma unroll
-    for (int i = 0; i < 4 * R; ++i) {
-      facc[i] = kFull;
-      racc[i] = kFull;
-    }
+    __syncwarp();
+  } else if (warp < kTcEpiWarp0 + kTcEpiWarps) {
+    const int q = warp & 3, part = (warp - kTcEpiWarp0) >> 2;
+    const uint32_t tq = S.tmem_base + (uint32_t(q * 32) << 16);
     bool ok = true;
-    int idx = 0;
+    for (int mt = 0; mt < 8; ++mt) {
+      if (!((active >> mt) & 1u)) continue;
+      // constraints of this unit's relation q: presence over the groups g
+      const uint32_t pres =
+          dir == 0 ? S.pm[4 * mt + q] : __ballot_sync(kFull, (S.pm[lane] >> (4 * mt + q)) & 1u);
+      const int var_m = dir == 0 ? 32 * I + 4 * mt + q : 32 * J + 4 * mt + q;
+      // this lane's slots' D_{k-1} words of var_m, in flight during the unit
+      uint32_t dprev[4];
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {  // forward jobs g * 32 + j
-      if (g >= rg) break;
-      for (int j = 0; j < 32; ++j, ++idx) {
-        const uint32_t c = jc + uint32_t(idx);
-        const int ab = int(c & 1u);
-        if (!ok || !(ok = warp_wait(S, P, &S.acc_full[ab], (c >> 1) & 1u, lane))) continue;
+      for (int u = 0; u < 4; ++u) {
+        const int i = lane + 32 * u;
+        dprev[u] = (pres != 0u && i < R) ? ld_dom(tc_view(P, S.slot_state[i], k).C + var_m) : 0u;
+      }
+      uint32_t andv[kNMax];
+#pragma unroll
+      for (int c = 0; c < kNMax; ++c) andv[c] = kFull;
+      for (int g = 0; g < kGroups; ++g, ++gc) {
+        if (int(gc & 1u) != part) continue;
+        const uint32_t sc = gc % kAccSlots;
+        if (ok) ok = warp_wait(S, P, &S.acc_full[sc], (gc / kAccSlots) & 1u, lane);
+        if (!ok) continue;
         tc_fence_after();
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          const int rr = R * part + i, r = 8 * g + rr;
-          if (live && r < int(nrows) && ((hdr[r] >> j) & 1u)) {  // warp-uniform
-            uint32_t v[32];
-            tmem_ld32(tq + uint32_t(ab) * 256u + uint32_t(rr * 32), v);
-            facc[R * g + i] &= pack_positive(v);
-          }
+        const bool here = (pres >> g) & 1u;  // warp-uniform
+        uint32_t v[kNMax];
+        if (here) {
+          const uint32_t col = tq + sc * kAccCols;
+          tmem_ld16(col, v);
+          if (ncols > 16) tmem_ld16(col + 16, v + 16);
+          if (ncols > 32) tmem_ld16(col + 32, v + 32);
+          tmem_wait_ld();
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&S.acc_empty[ab]);
+        if (lane == 0) mbar_arrive(&S.acc_empty[sc]);
+        if (here) {
+#pragma unroll
+          for (int c = 0; c < kNMax; ++c)
+            if (c < ncols) andv[c] &= __float_as_uint(fmaf(__uint_as_float(v[c]), 4096.0f, kMagic));
+        }
       }
-    }
-    idx = 32 * rg;
+      if (!ok || pres == 0u || var_m >= N.n) continue;
+      // this part's tests of row a = lane, state slot i: bit guard_bit(i % 3)
+      // of column i / 3; a ballot per slot gives the slot's kept word
+      uint32_t mine[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {  // reverse jobs 32 rg + g nrows + r
-      for (int r = 0; r < int(nrows); ++r, ++idx) {
-        const uint32_t c = jc + uint32_t(idx);
-        const int ab = int(c & 1u);
-        if (!ok || !(ok = warp_wait(S, P, &S.acc_full[ab], (c >> 1) & 1u, lane))) continue;
-        tc_fence_after();
-        const uint32_t pm = hdr[r];
+      for (int c = 0; c < kNMax; ++c) {
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-          const int jj = R * part + i, j = 8 * g + jj;
-          if (live && ((pm >> j) & 1u)) {  // warp-uniform
-            uint32_t v[32];
-            tmem_ld32(tq + uint32_t(ab) * 256u + uint32_t(jj * 32), v);
-            racc[R * g + i] &= pack_positive(v);
+        for (int j = 0; j < kF; ++j) {
+          const int i = kF * c + j;
+          if (i < kTcMaxStates && i < R) {
+            const uint32_t bal = __ballot_sync(kFull, (andv[c] >> guard_bit(j)) & 1u);
+            if (lane == (i & 31)) mine[i >> 5] = bal;
           }
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.acc_empty[ab]);
       }
-    }
-    // removals of this thread's state: this part's rows and columns
-    if (ok && s_ok) {
-      uint32_t *T = tc_view(P, s, k).T;
-      uint32_t colmask = 0u;  // columns with at least one constraint in the slab
-      for (int r = 0; r < int(nrows); ++r) colmask |= hdr[r];
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          const int r = 8 * g + R * part + i;
-          if (r < int(nrows) && hdr[r] != 0u) {
-            const uint32_t Dx = S.dom[s][32 + r];
-            const uint32_t keep = facc[R * g + i] & Dx;
-            if (keep != Dx)
-              tc_remove(S, P, s, slot_w, T, uint32_t(int(I) * 32 + int(row0) + r), keep);
-          }
-          const int j = 8 * g + R * part + i;
-          if ((colmask >> j) & 1u) {
-            const uint32_t Dy = S.dom[s][j];
-            const uint32_t keep = racc[R * g + i] & Dy;
-            if (keep != Dy) tc_remove(S, P, s, slot_w, T, uint32_t(int(J) * 32 + j), keep);
+      for (int u = 0; u < 4; ++u) {
+        const int i = lane + 32 * u;
+        if (i < R) {
+          const uint32_t keep = mine[u] & dprev[u];
+          if (keep != dprev[u]) {
+            const int s = S.slot_state[i];
+            tc_remove(S, P, s, slot_w, tc_view(P, s, k).T, uint32_t(var_m), keep);
           }
         }
       }
     }
   }
-  jc += uint32_t(n_jobs);
-  __syncwarp();                   // the single-lane roles rejoin their warps
-  named_bar(kConsumersBar, nct);  // S.dom free for the next slab
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParams P) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char *ring = smem_raw;
-  TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw + size_t(kTcStages) * kStageBytes);
+  TcSmem &S = *reinterpret_cast<TcSmem *>(smem_raw);
   const NetDev &N = P.net;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = gridDim.x, cta = blockIdx.x;
   const int B = P.n_states;
   const int n = N.n;
   const bool is_producer = warp == kTcConsumerWarps;
-  const int my_slabs = cta < N.n_slabs ? (N.n_slabs - cta + G - 1) / G : 0;
+  const int n_items = 2 * N.tc_tiles;
   const int64_t gtid = int64_t(cta) * blockDim.x + tid;
   const int64_t gstride = int64_t(G) * blockDim.x;
-  const int64_t cgtid = int64_t(cta) * (kTcConsumerWarps * 32) + tid;
-  const int64_t cgstride = int64_t(G) * (kTcConsumerWarps * 32);
+  const int64_t cgtid = int64_t(cta) * kTcCT + tid;
+  const int64_t cgstride = int64_t(G) * kTcCT;
 
-  if (warp == 0) {  // the accumulators: 512 tensor-memory columns
+  if (warp == 0) {  // 512 tensor-memory columns: accumulators and A tiles
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&S.tmem_base)),
                  "r"(kTmemCols)
@@ -498,25 +532,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < kTcStages; ++i) {
-      mbar_init(&S.full[i], 1);
-      mbar_init(&S.empty[i], kTcConsumerWarps);
+    for (int i = 0; i < kRing; ++i) {
+      mbar_init(&S.ring_full[i], 1);
+      mbar_init(&S.ring_empty[i], kTcAWarps);
     }
-    for (int i = 0; i < kTcAStages; ++i) {
+    for (int i = 0; i < kASlots; ++i) {
       mbar_init(&S.a_full[i], kTcAWarps);
       mbar_init(&S.a_empty[i], 1);
     }
-    for (int i = 0; i < kTcBStages; ++i) {
-      mbar_init(&S.b_full[i], 1);
-      mbar_init(&S.b_empty[i], 1);
+    for (int i = 0; i < kAccSlots; ++i) {
+      mbar_init(&S.acc_full[i], 1);
+      mbar_init(&S.acc_empty[i], 4);  // the four quarter warps of one part
     }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&S.acc_full[i], 1);
-      mbar_init(&S.acc_empty[i], kTcEpiWarps);
+      mbar_init(&S.item_full[i], 1);
+      mbar_init(&S.item_empty[i], 1);
     }
     fence_mbar_init();
     S.mma_issued = 0;
-    S.b_issued = 0;
+    S.ring_issued = 0;
     S.abort = 0;
     S.failed = 0;
     S.all_done = 0;
@@ -532,7 +566,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
   __syncthreads();
   tc_fence_after();
   const uint32_t base = S.base;
-  uint32_t ring_it = 0, prod_it = 0, jc = 0;
+  uint32_t gc = 0, rc = 0, iq = 0;  // groups, ring stages, queued items (consumers)
+  uint32_t prc = 0, piq = 0;        // ring stages, queued items (producer)
   int k = 0;
   if (S.poisoned) {
     S.failed = 1;
@@ -551,52 +586,86 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
       ++k;
       const int slot_w = int((base + k) % 3), slot_r = int((base + k + 2) % 3);
       const int slot_c = int((base + k + 1) % 3);
+      if (tid == 0) {  // the running states, in slots 0 .. R-1
+        int R = 0;
+        for (int s = 0; s < B; ++s)
+          if (!(S.st_info[s] & kInfoSweepMask)) S.slot_state[R++] = uint8_t(s);
+        S.n_slots = R;
+        S.ncols = 16 * ((R + 16 * kF - 1) / (16 * kF));
+      }
+      __syncthreads();
       if (is_producer) {
-        if (lane == 0) {
-          if (cta == 0) {  // the slot of the next sweep (the bit-packed kernel's claims too)
-            P.sync->bar[slot_c] = 0ull;
-            P.sync->claim[slot_c] = 0u;
-          }
-          const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
-          const uint32_t *cu = P.chgU + int64_t(slot_r) * N.nb;
-          bool ok = true;
-          for (int j = 0; j < my_slabs; ++j) {
-            const int sl = cta + j * G;
-            const SlabDesc sd = N.slabs[sl];
-            if (incr) {
-              const uint32_t I = sd.ij & 0xFFFFu, J = sd.ij >> 16;
-              const uint32_t row0 = sd.rows & 0xFFu, nrows = sd.rows >> 8;
-              const uint32_t rowmask = (nrows >= 32 ? kFull : ((1u << nrows) - 1u)) << row0;
-              if (ld_dom(cu + J) == 0u && (ld_dom(cu + I) & rowmask) == 0u) continue;
-            }
-            const int stg = prod_it % kTcStages;
-            const uint32_t par = (prod_it / kTcStages) & 1u;
-            if (!mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err, P.wait_limit_ns)) {
-              ok = false;
+        if (lane == 0 && cta == 0) {  // the slot of the next sweep
+          P.sync->bar[slot_c] = 0ull;
+          P.sync->claim[slot_c] = 0u;
+        }
+        const bool incr = (P.flags & RAC_INCREMENTAL) && k >= 2;
+        const uint32_t *cu = P.chgU + int64_t(slot_r) * N.nb;
+        bool ok = true;
+        for (;;) {
+          int item = -1;
+          if (lane == 0) {
+            for (;;) {  // claim the next item that needs evaluating
+              const int c = int(atomicAdd(&P.sync->claim[slot_w], 1u));
+              if (c >= n_items) break;
+              if (incr) {  // Prop. 2: neither block changed in sweep k-1
+                const uint32_t tij = N.tc_ij[c >> 1];
+                if (ld_dom(cu + (tij & 0xFFFFu)) == 0u && ld_dom(cu + (tij >> 16)) == 0u)
+                  continue;
+              }
+              item = c;
               break;
             }
-            S.stage[stg].sl = sl;
-            S.stage[stg].ij = sd.ij;
-            S.stage[stg].rows = sd.rows;
-            mbar_arrive_expect_tx(&S.full[stg], sd.nbytes);
-            bulk_copy_g2s(ring + size_t(stg) * kStageBytes, N.rel + size_t(sd.rel_off16),
-                          sd.nbytes, &S.full[stg]);
-            ++prod_it;
-          }
-          if (ok) {
-            const int stg = prod_it % kTcStages;
-            const uint32_t par = (prod_it / kTcStages) & 1u;
-            if (mbar_wait(&S.empty[stg], par ^ 1u, &P.sync->err, P.wait_limit_ns)) {
-              S.stage[stg].sl = -1;
-              mbar_arrive(&S.full[stg]);
-              ++prod_it;
-            } else {
+            const int s = int(piq & 1u);
+            if (!lane_wait(S, P, &S.item_empty[s], ((piq >> 1) & 1u) ^ 1u)) {
               ok = false;
+            } else {
+              S.item_q[s] = item;
+              mbar_arrive(&S.item_full[s]);
             }
           }
-          if (!ok) S.abort = 1;
+          ++piq;
+          ok = __shfl_sync(kFull, ok ? 1u : 0u, 0) != 0u;
+          item = __shfl_sync(kFull, item, 0);
+          if (!ok || item < 0) break;
+          // the item's units with a constraint, as the consumers compute them
+          const uint32_t pmw = N.tc_pm[int64_t(item >> 1) * 32 + lane];
+          uint32_t act = 0u;
+          if ((item & 1) == 0) {
+            const uint32_t b = __ballot_sync(kFull, pmw != 0u);
+#pragma unroll
+            for (int mt = 0; mt < 8; ++mt) act |= ((b >> (4 * mt)) & 0xFu) ? (1u << mt) : 0u;
+          } else {
+            uint32_t cols = pmw;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cols |= __shfl_xor_sync(kFull, cols, o);
+#pragma unroll
+            for (int mt = 0; mt < 8; ++mt) act |= ((cols >> (4 * mt)) & 0xFu) ? (1u << mt) : 0u;
+          }
+          if (lane == 0) {
+            const uint32_t *ops =
+                N.tc_ops + (int64_t(item) * 8) * kUnitWords;  // (tile * 2 + dir) * 8 units
+            for (int mt = 0; mt < 8 && ok; ++mt) {
+              if (!((act >> mt) & 1u)) continue;
+              const int r = int(prc % kRing);
+              if (!lane_wait(S, P, &S.ring_empty[r], ((prc / kRing) & 1u) ^ 1u)) {
+                ok = false;
+                break;
+              }
+              mbar_arrive_expect_tx(&S.ring_full[r], kUnitBytes);
+              bulk_copy_g2s(S.ring[r], ops + int64_t(mt) * kUnitWords, kUnitBytes,
+                            &S.ring_full[r]);
+              ++prc;
+              S.ring_issued = prc;
+            }
+          }
+          prc = __shfl_sync(kFull, prc, 0);
+          ok = __shfl_sync(kFull, ok ? 1u : 0u, 0) != 0u;
+          if (!ok) break;
         }
+        if (!ok && lane == 0) S.abort = 1;
       } else {
+        const int ct = tid;
         const int64_t stride = P.flag_stride;
         for (int64_t i = cgtid; i < stride; i += cgstride) {
           P.any[slot_c * stride + i] = 0u;
@@ -621,26 +690,51 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
           }
         }
         for (;;) {
-          const int stg = ring_it % kTcStages;
-          const uint32_t par = (ring_it / kTcStages) & 1u;
-          // one thread takes the bounded wait; every consumer warp follows its
-          // outcome (and only it), so no warp is left at a named barrier
-          if (tid == 0)
-            S.stage_ok[stg] = mbar_wait(&S.full[stg], par, &P.sync->err, P.wait_limit_ns) ? 1u : 0u;
-          named_bar(kConsumersBar, kTcConsumerWarps * 32);
-          if (!S.stage_ok[stg]) {
-            if (tid == 0) S.abort = 1;
-            break;
+          // the next item from the producer's queue, and its tile's presence
+          if (warp == 0) {
+            int item = -1;
+            if (lane == 0) {
+              const int s = int(iq & 1u);
+              if (lane_wait(S, P, &S.item_full[s], (iq >> 1) & 1u)) {
+                item = S.item_q[s];
+                mbar_arrive(&S.item_empty[s]);
+              }
+            }
+            item = __shfl_sync(kFull, item, 0);
+            if (item >= 0) {
+              const uint32_t pmw = N.tc_pm[int64_t(item >> 1) * 32 + lane];
+              S.pm[lane] = pmw;
+              uint32_t act = 0u;
+              if ((item & 1) == 0) {
+                const uint32_t b = __ballot_sync(kFull, pmw != 0u);
+#pragma unroll
+                for (int mt = 0; mt < 8; ++mt) act |= ((b >> (4 * mt)) & 0xFu) ? (1u << mt) : 0u;
+              } else {
+                uint32_t cols = pmw;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) cols |= __shfl_xor_sync(kFull, cols, o);
+#pragma unroll
+                for (int mt = 0; mt < 8; ++mt)
+                  act |= ((cols >> (4 * mt)) & 0xFu) ? (1u << mt) : 0u;
+              }
+              if (lane == 0) S.active = act;
+            }
+            if (lane == 0) S.cur_item = aborted(S) ? -1 : item;
           }
-          if (lane == 0) mbar_try_wait(&S.full[stg], par);
+          ++iq;
+          named_bar(kConsumersBar, kTcCT);
+          const int item = S.cur_item;
+          if (item < 0) break;
+          const uint32_t ij = N.tc_ij[item >> 1];
+          build_bset(S, P, k, (item & 1) == 0 ? 32 * int(ij >> 16) : 32 * int(ij & 0xFFFFu), ct);
+          fence_async_smem();
+          named_bar(kConsumersBar, kTcCT);
+          tc_item(S, P, item, k, slot_w, warp, lane, gc, rc);
+          const uint32_t units = __popc(S.active);
+          gc += units * kGroups;
+          rc += units;
           __syncwarp();
-          const TcStage si = S.stage[stg];
-          if (si.sl >= 0)
-            tc_consume(S, P, ring + size_t(stg) * kStageBytes, si, k, slot_w, warp, lane, jc);
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&S.empty[stg]);
-          ++ring_it;
-          if (si.sl < 0) break;
+          named_bar(kConsumersBar, kTcCT);  // B tiles and staged words free
         }
       }
       __syncthreads();
@@ -747,24 +841,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
     }
   }
   if (failed && tid == 0) atomicOr(&P.sync->err, kErrCopyWait);
-  if (is_producer && lane == 0) {
-    const uint32_t first = prod_it > uint32_t(kTcStages) ? prod_it - kTcStages : 0u;
-    for (uint32_t j = first; j < prod_it; ++j)
-      mbar_wait(&S.full[j % kTcStages], (j / kTcStages) & 1u, &P.sync->err, P.wait_limit_ns);
-  }
-  // no MMA may still write the accumulators, and no operand copy may still
-  // be in flight, when they are released: wait for the last ones issued (the
-  // phases of a normal run are complete already)
+  // no MMA may still write tensor memory, and no relation copy may still be
+  // in flight, when the CTA releases them: wait for the last ones issued (a
+  // normal run has completed them already)
   if (tid == 0) {
-    const uint32_t mi = S.mma_issued, bi = S.b_issued;
+    const uint32_t mi = S.mma_issued, ri = S.ring_issued;
     if (mi > 0) {
       const uint32_t c = mi - 1u;
-      mbar_wait(&S.acc_full[c & 1u], (c >> 1) & 1u, &P.sync->err, P.wait_limit_ns);
-    }
-    const uint32_t first = bi > uint32_t(kTcBStages) ? bi - kTcBStages : 0u;
-    for (uint32_t c = first; c < bi; ++c)
-      mbar_wait(&S.b_full[c % kTcBStages], (c / kTcBStages) & 1u, &P.sync->err,
+      mbar_wait(&S.acc_full[c % kAccSlots], (c / kAccSlots) & 1u, &P.sync->err,
                 P.wait_limit_ns);
+    }
+    const uint32_t first = ri > uint32_t(kRing) ? ri - kRing : 0u;
+    for (uint32_t c = first; c < ri; ++c)
+      mbar_wait(&S.ring_full[c % kRing], (c / kRing) & 1u, &P.sync->err, P.wait_limit_ns);
   }
   tc_fence_before();
   __syncthreads();
@@ -779,13 +868,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
 
 rac_status launch_tc(const LaunchParams &P, cudaStream_t stream) {
   static LaunchCache cache;
-  const size_t smem = size_t(kTcStages) * kStageBytes + sizeof(TcSmem);
+  const size_t smem = sizeof(TcSmem);
   if (P.n_states > kTcMaxStates) {
     set_error("the tensor-core kernel takes at most 128 states per launch");
     return RAC_EINVAL;
   }
-  if (!P.net.fp8 || P.net.fp8_jobs != fp8_jobs_for(P.net.rows_per_slab)) {
-    set_error("the network's FP8 operand store is missing");
+  if (!P.net.tc_ops) {
+    set_error("the network's tensor-core operand store is missing");
     return RAC_EINVAL;
   }
   int per_sm = 0, sms = 0;
@@ -813,38 +902,72 @@ rac_status launch_tc(const LaunchParams &P, cudaStream_t stream) {
   return RAC_OK;
 }
 
-rac_status ensure_fp8(const rac_network *net, cudaStream_t stream) {
+rac_status ensure_tc_store(const rac_network *net, cudaStream_t stream) {
   std::lock_guard<std::mutex> lock(net->mu);
-  if (net->d_fp8) return RAC_OK;
-  const size_t tiles = size_t(net->n_slabs) * size_t(net->fp8_jobs);
-  const size_t bytes = tiles * size_t(kFp8TileBytes);
+  if (net->d_tc) return RAC_OK;
+  // the tiles holding a constraint, in slab order
+  std::vector<SlabDesc> slabs(size_t(net->n_slabs));
+  cudaError_t e = cudaSuccess;
+  if (!slabs.empty())
+    e = cudaMemcpy(slabs.data(), net->d_slabs, slabs.size() * sizeof(SlabDesc),
+                   cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the slab table");
+  std::unordered_map<uint32_t, int32_t> tile_of;
+  std::vector<uint32_t> tile_ij;
+  std::vector<int32_t> slab_tile(slabs.size());
+  for (size_t i = 0; i < slabs.size(); ++i) {
+    auto it = tile_of.find(slabs[i].ij);
+    if (it == tile_of.end()) {
+      it = tile_of.emplace(slabs[i].ij, int32_t(tile_ij.size())).first;
+      tile_ij.push_back(slabs[i].ij);
+    }
+    slab_tile[i] = it->second;
+  }
+  const size_t tiles = tile_ij.size();
+  const size_t ops_words = tiles * size_t(kTcStoreWordsPerTile);
+  const size_t words = ops_words + tiles * 32 + tiles;
+  const size_t bytes = words * 4;
   if (bytes > (size_t(64) << 30)) {
-    set_error("the FP8 operand store of this network would take " +
+    set_error("the tensor-core operand store of this network would take " +
               std::to_string(bytes >> 30) + " GiB (at most 64)");
     return RAC_ENOTSUP;
   }
   void *p = nullptr;
-  cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+  e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
   if (e != cudaSuccess) {
     cudaGetLastError();
-    set_error("out of device memory for the FP8 operand store (" + std::to_string(bytes) +
-              " bytes)");
+    set_error("out of device memory for the tensor-core operand store (" +
+              std::to_string(bytes) + " bytes)");
     return RAC_ENOMEM;
   }
+  uint32_t *ops = static_cast<uint32_t *>(p);
+  uint32_t *pmt = ops + ops_words, *ijt = pmt + tiles * 32;
+  int32_t *d_slab_tile = nullptr;
+  auto fail = [&](cudaError_t err, const char *what) {
+    cudaFree(d_slab_tile);
+    cudaFree(p);
+    return cuda_fail(err, what);
+  };
   if (tiles > 0) {
+    if ((e = cudaMalloc(&d_slab_tile, slab_tile.size() * sizeof(int32_t))) != cudaSuccess)
+      return fail(e, "building the tensor-core operand store");
+    if ((e = cudaMemcpy(d_slab_tile, slab_tile.data(), slab_tile.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(ijt, tile_ij.data(), tiles * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemsetAsync(ops, 0, (ops_words + tiles * 32) * 4, stream)) != cudaSuccess)
+      return fail(e, "building the tensor-core operand store");
     NetDev N = net_dev(net);
-    const int64_t words = int64_t(tiles) * (kFp8TileBytes / 4);
-    const int64_t blocks = std::min<int64_t>((words + 255) / 256, int64_t(1) << 20);
-    rac_fp8_build_kernel<<<unsigned(blocks), 256, 0, stream>>>(N, static_cast<uint8_t *>(p));
+    const int64_t warps = int64_t(net->n_slabs) * 1024;
+    const int64_t blocks = std::min<int64_t>((warps + 7) / 8, int64_t(1) << 20);
+    rac_tc_store_kernel<<<unsigned(blocks), 256, 0, stream>>>(N, d_slab_tile, ops, pmt);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) {
-      cudaFree(p);
-      return cuda_fail(e, "building the FP8 operand store");
-    }
+    if (e != cudaSuccess) return fail(e, "building the tensor-core operand store");
+    cudaFree(d_slab_tile);
   }
-  net->d_fp8 = static_cast<uint8_t *>(p);
-  net->fp8_bytes = bytes;
+  net->d_tc = ops;
+  net->tc_bytes = bytes;
+  net->tc_tiles = int32_t(tiles);
   return RAC_OK;
 }
 
