@@ -72,12 +72,14 @@ typedef int32_t rac_status;
 /* layout_flags of rac_create_network */
 #define RAC_LAYOUT_BITS 0x1u /* bit-packed relation slabs (always built) */
 /* The tensor-core kernel's operand store (RAC_KERNEL_TENSOR), built on the
- * device at creation: every relation expanded to E4M3 0/1 bytes (1.0 = 0x38)
- * in the MMA's shared-memory tile layout, 8 KiB per MMA job (a slab's forward
- * jobs: 8 relations of one column, a row each of their 32 values; its
- * reverse jobs: 8 relations of one row, transposed), about 64 x 8 KiB per 8
- * slab rows (1.1 GB for n = 1000).  Without it the first RAC_KERNEL_TENSOR
- * call on the network builds it (an allocation and a wait on its stream). */
+ * device at creation: every relation in both orientations (its rows R[a][.]
+ * and its columns R[.][b]), a 32-bit word per row or column, grouped by
+ * 32 x 32-variable tile in the order the kernel's MMAs consume them, plus
+ * each tile's presence rows: 256 KiB per tile that holds a constraint (135
+ * MB for n = 1000, 528 MB for n = 2000).  The kernel expands each word to the
+ * MMA's FP8 (E5M2) operand in tensor memory as it goes.  Without it the
+ * first RAC_KERNEL_TENSOR call on the network builds it (an allocation and a
+ * wait on its stream). */
 #define RAC_LAYOUT_FP8 0x2u
 /* Packed relation rows: row a of a relation takes bits [w a, w a + w) of the
  * relation's words, w = round_up(d, 4), instead of a word of its own, so a
@@ -123,12 +125,14 @@ typedef int32_t rac_status;
                                     evaluates EVERY slab, instead of the slabs
                                     left pending (see rac_enforce_learned). */
 #define RAC_KERNEL_TENSOR 0x10u  /* evaluate the support counts with the tensor-core
-                                    kernel (tcgen05 FP8 GEMMs, FP32 accumulation in
-                                    tensor memory) instead of the bit-packed kernel:
+                                    kernel (tcgen05 FP8 MMAs: 128 relation rows x
+                                    the running states x 32 values, FP32
+                                    accumulation in tensor memory) instead of the
+                                    bit-packed kernel:
                                     rac_enforce, single-network rac_enforce_batch
                                     and rac_enforce_host only, at most 128 states
                                     per launch (larger batches are split).  It
-                                    reads the network's FP8 operand store
+                                    reads the network's operand store
                                     (RAC_LAYOUT_FP8), which the first such call
                                     builds if the network has none: make that
                                     call outside any stream capture.  Results

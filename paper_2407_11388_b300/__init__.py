@@ -21,7 +21,7 @@ from .build import LIB as _LIB_PATH
 OK, WIPEOUT = 0, 1
 EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBARRIER, ENOTSUP = -1, -2, -3, -4, -5, -6
 LAYOUT_BITS = 0x1
-LAYOUT_FP8 = 0x2  # the tensor-core kernel's FP8 operand store, built at creation
+LAYOUT_FP8 = 0x2  # the tensor-core kernel's operand store, built at creation
 LAYOUT_PACKED = 0x4  # relation rows packed back to back (d <= 28: fewer bytes per sweep)
 
 

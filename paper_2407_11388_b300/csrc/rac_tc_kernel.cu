@@ -7,48 +7,44 @@
 //   forward  Sup_xy[a](s) = sum_b R[a][b] D_s[y][b]
 //   reverse  Sup_yx[b](s) = sum_a R[a][b] D_s[x][a]
 // and only whether a count is positive matters (the clamp of the paper's
-// listing).  Here the relation rows are the MMA's M axis and the states its N
+// listing).  The relation rows are the MMA's M axis and the states its N
 // axis, so every tensor-memory lane quarter (and every SM sub-partition)
 // works whatever the number of states:
 //   M = 128 rows: four relations x 32 rows (rows >= d are zero), their FP8
 //       entries written straight into tensor memory by the A-operand warps
 //       (tcgen05.st) from the relation's bit words -- no shared-memory copy;
-//   K = 32 values of the other variable, in three K-blocks;
-//   N = 16, 32 or 48 columns, each holding THREE states: state slot 3c + j
-//       sits in K-block j of column c with the entry weight 2^-13, 2^-7 or
-//       2^1 (one bit of an E5M2 byte each), and the A entries are 2.0, so
-//       column c accumulates 2^-12 (n_0 + 64 n_1 + 16384 n_2) with the three
-//       counts n_j <= 32 in separate 6-bit fields, exactly (integers below
-//       2^20 scaled by a power of two).
-// The epilogue turns a column into its three tests with one FFMA, which adds
-// 2^23 + 31 (1 + 64 + 16384) and puts the sum's integer in the mantissa bits,
-// where field j's bit 5 is set iff n_j >= 1; one AND per column then folds a
-// constraint into the running AND over C_x -- two instructions per three
-// (row, state) tests.  After a unit's 32 constraints every row's bit per
-// state is gathered with a warp ballot and removals follow kernel (a)
-// (atomicAnd into the next domain buffer, change marks).
+//   K = 32 values of the other variable;
+//   N = the running states, rounded up to 16 (at most 128): one MMA per
+//       group, because an MMA of this shape costs the same whatever N up to
+//       128 (about 100 SM cycles).
+// Entries are 2.0 or 0 on both sides, so a count is 4 x the number of
+// supports, an exact small integer in FP32, and its bits are non-zero iff it
+// is.  The epilogue folds a constraint into the running AND over C_x with
+// one unsigned minimum per (row, state): the minimum over the row's
+// constraints is non-zero iff every count is.  After a unit's 32 constraints
+// a warp ballot per state gathers the rows' kept bits, and removals follow
+// kernel (a) (atomicAnd into the next domain buffer, change marks; an
+// emptied domain is found by the next sweep's owner step).
 //
 // Work: the network's variables form blocks of 32; a constraint lies in tile
 // (I, J) = (min/32, max/32).  An item is one direction of one tile: forward
 // (rows x of block I against the 32 variables y of block J) or reverse (rows
 // y of block J against the x of block I).  Its 8 units take four variables
 // each (one MMA row group of 128), and a unit's 32 groups are the 32
-// variables of the other block -- three MMAs each (one per K-block), whose
-// B operands (the other variable's domain words of every running state,
-// expanded to E5M2 with the field weights) are built once per item in shared
-// memory.  Items are claimed from a grid-wide counter.
+// variables of the other block, one MMA each, whose B operands (the other
+// variable's domain words of every running state, expanded to E5M2) are
+// built once per item in shared memory.  Items are claimed from a grid-wide
+// counter.
 //
-// Roles (one CTA per SM, 448 threads):
+// Roles (one CTA per SM, 704 threads):
 //   warps 0-3   A operands: lane quarter q = warp; lane a writes row a of
 //               the group's relation q into a 16-slot ring of tensor-memory
-//               A tiles (8 columns each);
-//   warps 4-11  epilogue: quarter warp % 4, two parts taking alternate
-//               groups (accumulator slots of one parity) with their own
-//               running ANDs; each part makes the removals its AND implies
-//               (two partial ANDs applied by atomicAnd give the full AND);
-//   warp 12     lane 0 issues the MMAs and commits their completion to the
-//               A slot and the accumulator;
-//   warp 13     claims items, publishes them through a two-deep queue and
+//               A tiles (8 columns each), four groups per store wait;
+//   warps 4-19  epilogue: lane quarter warp % 4 and 32 state columns each
+//               (part (warp - 4) / 4), every group;
+//   warp 20     lane 0 issues the MMAs (three accumulators of 128 columns)
+//               and commits their completion to the A slots and accumulators;
+//   warp 21     claims items, publishes them through a two-deep queue and
 //               streams each unit's 16 KiB of relation words into a
 //               three-stage ring (cp.async.bulk).
 // Every role waits on mbarriers only; the consumer warps meet on a named
@@ -70,43 +66,36 @@ using namespace dev;
 
 // warp roles (see the file comment)
 constexpr int kTcAWarps = 4;                             // warps 0-3
-constexpr int kTcEpiParts = 2;                           // epilogue warps per lane quarter
-constexpr int kTcEpiWarp0 = kTcAWarps;                   // warps 4-11
+constexpr int kTcEpiParts = 4;                           // epilogue warps per lane quarter
+constexpr int kTcEpiWarp0 = kTcAWarps;                   // warps 4-19
 constexpr int kTcEpiWarps = 4 * kTcEpiParts;
-constexpr int kTcMmaWarp = kTcEpiWarp0 + kTcEpiWarps;    // warp 12
-constexpr int kTcConsumerWarps = kTcMmaWarp + 1;         // warps 0-12
-constexpr int kTcThreads = (kTcConsumerWarps + 1) * 32;  // + warp 13, the producer
+constexpr int kTcMmaWarp = kTcEpiWarp0 + kTcEpiWarps;    // warp 20
+constexpr int kTcConsumerWarps = kTcMmaWarp + 1;         // warps 0-20
+constexpr int kTcThreads = (kTcConsumerWarps + 1) * 32;  // + warp 21, the producer
 constexpr int kTcCT = kTcConsumerWarps * 32;             // consumer threads
 
-constexpr int kF = 3;                           // states per accumulator column
 constexpr int kTcMaxStates = kTensorMaxStates;  // 128
-constexpr int kNMax = 48;                       // N for up to 144 state slots
-static_assert(kNMax * kF >= kTcMaxStates && kNMax % 16 == 0, "N covers the states");
-constexpr int kAccSlots = 6, kAccCols = 64;  // accumulators: 6 x 64 columns
-constexpr int kASlots = 16, kACols = 8;      // A tiles: 128 lanes x 32 bytes
+constexpr int kNMax = 128;                      // N: one column per state
+static_assert(kNMax >= kTcMaxStates && kNMax == 32 * kTcEpiParts, "a part per 32 columns");
+constexpr int kAccSlots = 3, kAccCols = 128;  // accumulators: 3 x 128 columns
+constexpr int kASlots = 16, kACols = 8;       // A tiles: 128 lanes x 32 bytes
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kACol0 = kAccSlots * kAccCols;
 static_assert(kACol0 + kASlots * kACols <= kTmemCols, "tensor memory of one CTA");
-static_assert(kAccSlots % kTcEpiParts == 0 && kTcEpiParts == 2,
-              "a part owns the accumulator slots of one parity");
 constexpr int kGroups = 32;                 // groups (constraint columns) per unit
+// groups per batch: the A warps store a batch's tiles before one wait
+constexpr int kBatch = 4;
+static_assert(kGroups % kBatch == 0 && kASlots % kBatch == 0, "batches");
 constexpr int kUnitWords = kGroups * 128;   // a unit's relation words
 constexpr uint32_t kUnitBytes = kUnitWords * 4;
 constexpr int kRing = 3;
-constexpr int kBTileBytes = (kNMax / 8) * 256;    // one (variable, K-block) B tile
-constexpr int kBSetBytes = 32 * kF * kBTileBytes;  // the item's 32 variables
-constexpr int kDStride = 33;                       // staged domain words, padded
+constexpr int kBTileBytes = (kNMax / 8) * 256;  // one variable's B tile
+constexpr int kBSetBytes = 32 * kBTileBytes;    // the item's 32 variables
+constexpr int kDStride = 33;                    // staged domain words, padded
 static_assert(kTcStoreWordsPerTile == 2 * 8 * kUnitWords, "store layout");
 
-// E5M2 entries: A = 2.0 (0x40, bit 6); B of K-block j = 2^-13, 2^-7, 2^1
-// (0x08, 0x20, 0x40: bits 3, 5, 6), so A x B = 2^-12 x {1, 64, 16384}.
-constexpr int kABit = 6;
-__device__ __forceinline__ int field_bit(int j) { return j == 0 ? 3 : (j == 1 ? 5 : 6); }
-// field j of X = n_0 + 64 n_1 + 16384 n_2 starts at bit 0, 6, 14; with
-// kC = 31 in every field, bit 5 of field j of X + kC is set iff n_j >= 1
-constexpr uint32_t kC = 31u + (31u << 6) + (31u << 14);
-constexpr float kMagic = float(8388608u + kC);  // 2^23 + kC, exact in FP32
-__device__ __forceinline__ int guard_bit(int j) { return j == 0 ? 5 : (j == 1 ? 11 : 19); }
+// E5M2 entries 2.0 (0x40, bit 6) on both sides: a count is 4 x the supports
+constexpr int kOneBit = 6;
 // instruction descriptor: FP32 accumulator, E5M2 A and B, K-major, M = 128
 __device__ __forceinline__ uint32_t idesc_for(int ncols) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(ncols >> 3) << 17) |
@@ -123,7 +112,7 @@ __device__ __forceinline__ uint32_t spread4(uint32_t nib, int t) {
 struct TcSmem {
   uint8_t bset[kBSetBytes];          // B tiles of the item's 32 variables
   uint32_t ring[kRing][kUnitWords];  // relation words of a unit
-  uint32_t dstage[kNMax * kF][kDStride];  // domain words of the item's 32 variables
+  uint32_t dstage[kNMax][kDStride];  // domain words of the item's 32 variables
   uint64_t ring_full[kRing], ring_empty[kRing];
   uint64_t a_full[kASlots], a_empty[kASlots];
   uint64_t acc_full[kAccSlots], acc_empty[kAccSlots];
@@ -137,7 +126,7 @@ struct TcSmem {
   uint32_t base, poisoned, abort, failed, all_done;
   uint32_t any_total, wipe_total, cta_any, cta_wipe;
   int32_t n_slots, ncols;
-  uint8_t slot_state[kNMax * kF];
+  uint8_t slot_state[kNMax];
   uint32_t st_info[kTcMaxStates];
   uint8_t any_loc[kTcMaxStates], wipe_loc[kTcMaxStates];
 };
@@ -185,18 +174,20 @@ __device__ __forceinline__ void tc_fence_after() {
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-// 16 consecutive columns of this warp's 32 lanes.
-__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t *v) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-        "=r"(v[14]), "=r"(v[15])
-      : "r"(addr));
-}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// 32 consecutive columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(addr));
 }
 // 8 consecutive columns of this warp's 32 lanes.
 __device__ __forceinline__ void tmem_st8(uint32_t addr, const uint32_t (&v)[8]) {
@@ -234,11 +225,20 @@ __device__ __forceinline__ TcView tc_view(const LaunchParams &P, int s, int k) {
   return v;
 }
 
+// A removal: D_k[v] &= keep (keep a strict subset of D_{k-1}[v]).  Only with
+// RAC_STOP_ON_WIPEOUT does the state end in the sweep that empties a domain,
+// so only there does the atomic return the old word; otherwise the next
+// sweep's owner step finds an emptied domain and no removal waits for its
+// atomic's round trip.
 __device__ __forceinline__ void tc_remove(TcSmem &S, const LaunchParams &P, int s, int slot_w,
                                           uint32_t *T, uint32_t v, uint32_t keep) {
-  const uint32_t old = atomicAnd(T + v, keep);
+  if (P.flags & RAC_STOP_ON_WIPEOUT) {
+    const uint32_t old = atomicAnd(T + v, keep);
+    if (old != 0u && (old & keep) == 0u) S.wipe_loc[s] = 1;
+  } else {
+    atomicAnd(T + v, keep);
+  }
   S.any_loc[s] = 1;
-  if (old != 0u && (old & keep) == 0u) S.wipe_loc[s] = 1;
   const int nb = P.net.nb;
   const uint32_t bit = 1u << (v & 31u);
   atomicOr(P.chg + (int64_t(slot_w) * P.flag_stride + s) * nb + (v >> 5), bit);
@@ -331,14 +331,14 @@ __device__ __forceinline__ bool lane_wait(TcSmem &S, const LaunchParams &P, uint
   return true;
 }
 
-// The B operands of an item: tile (v, j) holds, in row c, the domain word of
-// variable vbase + v in the state of slot 3c + j, expanded to E5M2 bytes of
-// weight bit field_bit(j) (zero rows for slots without a running state).
+// The B operands of an item: tile v holds, in row c, the domain word of
+// variable vbase + v in the state of slot c, expanded to E5M2 bytes (zero
+// rows for slots without a running state).
 __device__ void build_bset(TcSmem &S, const LaunchParams &P, int k, int vbase, int ct) {
-  const int n = P.net.n, R = S.n_slots, ncols = S.ncols, nslots = ncols * kF;
+  const int n = P.net.n, R = S.n_slots, ncols = S.ncols;
   // the words, coalesced over the 32 variables, into dstage[slot][v]
-  const int total = 32 * nslots;
-  constexpr int kPer = (32 * kNMax * kF + kTcCT - 1) / kTcCT;
+  const int total = 32 * ncols;
+  constexpr int kPer = (32 * kNMax + kTcCT - 1) / kTcCT;
   uint32_t w[kPer];
 #pragma unroll
   for (int r = 0; r < kPer; ++r) {
@@ -356,14 +356,12 @@ __device__ void build_bset(TcSmem &S, const LaunchParams &P, int k, int vbase, i
   named_bar(kConsumersBar, kTcCT);
   // rows of the B tiles, 16-byte chunks of consecutive rows per thread group
   for (int t = ct; t < total; t += kTcCT) {
-    const int c = t % ncols, vj = t / ncols;
-    const int j = vj % kF, v = vj / kF;
-    const uint32_t word = S.dstage[kF * c + j][v];
-    const int fb = field_bit(j);
+    const int c = t % ncols, v = t / ncols;
+    const uint32_t word = S.dstage[c][v];
     uint32_t e[8];
 #pragma unroll
-    for (int h = 0; h < 8; ++h) e[h] = spread4((word >> (4 * h)) & 0xFu, fb);
-    uint8_t *row = S.bset + (v * kF + j) * kBTileBytes + (c >> 3) * 256 + (c & 7) * 16;
+    for (int h = 0; h < 8; ++h) e[h] = spread4((word >> (4 * h)) & 0xFu, kOneBit);
+    uint8_t *row = S.bset + v * kBTileBytes + (c >> 3) * 256 + (c & 7) * 16;
     *reinterpret_cast<uint4 *>(row) = make_uint4(e[0], e[1], e[2], e[3]);
     *reinterpret_cast<uint4 *>(row + 128) = make_uint4(e[4], e[5], e[6], e[7]);
   }
@@ -391,19 +389,22 @@ __device__ void tc_item(TcSmem &S, const LaunchParams &P, int item, int k, int s
       const int r = int(rc % kRing);
       if (ok) ok = warp_wait(S, P, &S.ring_full[r], (rc / kRing) & 1u, lane);
       const uint32_t *U = S.ring[r];
-      for (int g = 0; g < kGroups; ++g, ++gc) {
-        const uint32_t sa = gc % kASlots;
-        if (ok) ok = warp_wait(S, P, &S.a_empty[sa], ((gc / kASlots) & 1u) ^ 1u, lane);
+      for (int g0 = 0; g0 < kGroups; g0 += kBatch, gc += kBatch) {
+        // a batch's A tiles: slots gc .. gc + kBatch - 1, one barrier each way
+        if (ok) ok = warp_wait(S, P, &S.a_empty[gc % kASlots], ((gc / kASlots) & 1u) ^ 1u, lane);
         if (!ok) continue;
-        const uint32_t wrd = U[g * 128 + q * 32 + lane];
-        uint32_t e[8];
 #pragma unroll
-        for (int h = 0; h < 8; ++h) e[h] = spread4((wrd >> (4 * h)) & 0xFu, kABit);
-        tmem_st8(arow + sa * kACols, e);
+        for (int b = 0; b < kBatch; ++b) {
+          const uint32_t wrd = U[(g0 + b) * 128 + q * 32 + lane];
+          uint32_t e[8];
+#pragma unroll
+          for (int h = 0; h < 8; ++h) e[h] = spread4((wrd >> (4 * h)) & 0xFu, kOneBit);
+          tmem_st8(arow + ((gc + b) % kASlots) * kACols, e);
+        }
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&S.a_full[sa]);
+        if (lane == 0) mbar_arrive(&S.a_full[gc % kASlots]);
       }
       __syncwarp();
       if (ok && lane == 0) mbar_arrive(&S.ring_empty[r]);
@@ -416,28 +417,28 @@ __device__ void tc_item(TcSmem &S, const LaunchParams &P, int item, int k, int s
       bool ok = true;
       for (int mt = 0; mt < 8 && ok; ++mt) {
         if (!((active >> mt) & 1u)) continue;
-        for (int g = 0; g < kGroups; ++g, ++gc) {
-          const uint32_t sa = gc % kASlots, sc = gc % kAccSlots;
-          if (!(ok = lane_wait(S, P, &S.a_full[sa], (gc / kASlots) & 1u) &&
-                     lane_wait(S, P, &S.acc_empty[sc], ((gc / kAccSlots) & 1u) ^ 1u)))
-            break;
-          tc_fence_after();
-          const uint32_t d = S.tmem_base + sc * kAccCols;
-          const uint32_t a = S.tmem_base + kACol0 + sa * kACols;
-#pragma unroll
-          for (int j = 0; j < kF; ++j)
-            umma_ts(d, a, bdesc0 + uint64_t(((g * kF + j) * kBTileBytes) >> 4), idesc,
-                    j > 0 ? 1u : 0u);
-          umma_commit(&S.a_empty[sa]);
-          umma_commit(&S.acc_full[sc]);
-          S.mma_issued = gc + 1u;
+        for (int g0 = 0; g0 < kGroups && ok; g0 += kBatch) {
+          const uint32_t sa = gc % kASlots;
+          if (!(ok = lane_wait(S, P, &S.a_full[sa], (gc / kASlots) & 1u))) break;
+          for (int b = 0; b < kBatch; ++b, ++gc) {
+            const uint32_t sc = gc % kAccSlots;
+            if (!(ok = lane_wait(S, P, &S.acc_empty[sc], ((gc / kAccSlots) & 1u) ^ 1u))) break;
+            tc_fence_after();
+            umma_ts(S.tmem_base + sc * kAccCols, S.tmem_base + kACol0 + (gc % kASlots) * kACols,
+                    bdesc0 + uint64_t(((g0 + b) * kBTileBytes) >> 4), idesc, 0u);
+            umma_commit(&S.acc_full[sc]);
+            S.mma_issued = gc + 1u;
+          }
+          if (ok) umma_commit(&S.a_empty[sa]);
         }
       }
     }
     __syncwarp();
   } else if (warp < kTcEpiWarp0 + kTcEpiWarps) {
     const int q = warp & 3, part = (warp - kTcEpiWarp0) >> 2;
-    const uint32_t tq = S.tmem_base + (uint32_t(q * 32) << 16);
+    const int col0 = 32 * part;             // this warp's state columns
+    const bool cols = col0 < ncols;         // warp-uniform
+    const uint32_t tq = S.tmem_base + (uint32_t(q * 32) << 16) + uint32_t(col0);
     bool ok = true;
     for (int mt = 0; mt < 8; ++mt) {
       if (!((active >> mt) & 1u)) continue;
@@ -445,29 +446,23 @@ __device__ void tc_item(TcSmem &S, const LaunchParams &P, int item, int k, int s
       const uint32_t pres =
           dir == 0 ? S.pm[4 * mt + q] : __ballot_sync(kFull, (S.pm[lane] >> (4 * mt + q)) & 1u);
       const int var_m = dir == 0 ? 32 * I + 4 * mt + q : 32 * J + 4 * mt + q;
-      // this lane's slots' D_{k-1} words of var_m, in flight during the unit
-      uint32_t dprev[4];
+      // D_{k-1}[var_m] of this lane's slot col0 + lane, in flight during the unit
+      const int slot = col0 + lane;
+      const uint32_t dprev = (cols && pres != 0u && slot < R)
+                                 ? ld_dom(tc_view(P, S.slot_state[slot], k).C + var_m)
+                                 : 0u;
+      uint32_t mn[32];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = lane + 32 * u;
-        dprev[u] = (pres != 0u && i < R) ? ld_dom(tc_view(P, S.slot_state[i], k).C + var_m) : 0u;
-      }
-      uint32_t andv[kNMax];
-#pragma unroll
-      for (int c = 0; c < kNMax; ++c) andv[c] = kFull;
+      for (int c = 0; c < 32; ++c) mn[c] = kFull;
       for (int g = 0; g < kGroups; ++g, ++gc) {
-        if (int(gc & 1u) != part) continue;
         const uint32_t sc = gc % kAccSlots;
         if (ok) ok = warp_wait(S, P, &S.acc_full[sc], (gc / kAccSlots) & 1u, lane);
         if (!ok) continue;
         tc_fence_after();
-        const bool here = (pres >> g) & 1u;  // warp-uniform
-        uint32_t v[kNMax];
+        const bool here = cols && ((pres >> g) & 1u);  // warp-uniform
+        uint32_t v[32];
         if (here) {
-          const uint32_t col = tq + sc * kAccCols;
-          tmem_ld16(col, v);
-          if (ncols > 16) tmem_ld16(col + 16, v + 16);
-          if (ncols > 32) tmem_ld16(col + 32, v + 32);
+          tmem_ld32(tq + sc * kAccCols, v);
           tmem_wait_ld();
         }
         tc_fence_before();
@@ -475,34 +470,25 @@ __device__ void tc_item(TcSmem &S, const LaunchParams &P, int item, int k, int s
         if (lane == 0) mbar_arrive(&S.acc_empty[sc]);
         if (here) {
 #pragma unroll
-          for (int c = 0; c < kNMax; ++c)
-            if (c < ncols) andv[c] &= __float_as_uint(fmaf(__uint_as_float(v[c]), 4096.0f, kMagic));
+          for (int c = 0; c < 32; ++c) mn[c] = min(mn[c], v[c]);
         }
       }
-      if (!ok || pres == 0u || var_m >= N.n) continue;
-      // this part's tests of row a = lane, state slot i: bit guard_bit(i % 3)
-      // of column i / 3; a ballot per slot gives the slot's kept word
-      uint32_t mine[4] = {0u, 0u, 0u, 0u};
+      if (!ok || !cols || pres == 0u || var_m >= N.n) continue;
+      // row a = lane keeps value a in slot col0 + c iff mn[c] != 0; a ballot
+      // per column gives the slot's kept word
+      uint32_t mine = 0u;
 #pragma unroll
-      for (int c = 0; c < kNMax; ++c) {
-#pragma unroll
-        for (int j = 0; j < kF; ++j) {
-          const int i = kF * c + j;
-          if (i < kTcMaxStates && i < R) {
-            const uint32_t bal = __ballot_sync(kFull, (andv[c] >> guard_bit(j)) & 1u);
-            if (lane == (i & 31)) mine[i >> 5] = bal;
-          }
+      for (int c = 0; c < 32; ++c) {
+        if (col0 + c < R) {
+          const uint32_t bal = __ballot_sync(kFull, mn[c] != 0u);
+          if (lane == c) mine = bal;
         }
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = lane + 32 * u;
-        if (i < R) {
-          const uint32_t keep = mine[u] & dprev[u];
-          if (keep != dprev[u]) {
-            const int s = S.slot_state[i];
-            tc_remove(S, P, s, slot_w, tc_view(P, s, k).T, uint32_t(var_m), keep);
-          }
+      if (slot < R) {
+        const uint32_t keep = mine & dprev;
+        if (keep != dprev) {
+          const int s = S.slot_state[slot];
+          tc_remove(S, P, s, slot_w, tc_view(P, s, k).T, uint32_t(var_m), keep);
         }
       }
     }
@@ -536,13 +522,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
       mbar_init(&S.ring_full[i], 1);
       mbar_init(&S.ring_empty[i], kTcAWarps);
     }
-    for (int i = 0; i < kASlots; ++i) {
+    for (int i = 0; i < kASlots; ++i) {  // used by the first slot of each batch
       mbar_init(&S.a_full[i], kTcAWarps);
       mbar_init(&S.a_empty[i], 1);
     }
     for (int i = 0; i < kAccSlots; ++i) {
       mbar_init(&S.acc_full[i], 1);
-      mbar_init(&S.acc_empty[i], 4);  // the four quarter warps of one part
+      mbar_init(&S.acc_empty[i], kTcEpiWarps);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&S.item_full[i], 1);
@@ -591,7 +577,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
         for (int s = 0; s < B; ++s)
           if (!(S.st_info[s] & kInfoSweepMask)) S.slot_state[R++] = uint8_t(s);
         S.n_slots = R;
-        S.ncols = 16 * ((R + 16 * kF - 1) / (16 * kF));
+        S.ncols = 16 * ((R + 15) / 16);
       }
       __syncthreads();
       if (is_producer) {
@@ -685,7 +671,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) rac_tc_kernel(const LaunchParam
               const int b = __ffs(w) - 1;
               w &= w - 1u;
               const int x = blk * 32 + b;
-              atomicAnd(V.T + x, ld_dom(V.C + x));
+              const uint32_t c = ld_dom(V.C + x);
+              atomicAnd(V.T + x, c);
+              if (c == 0u) S.wipe_loc[s] = 1;  // emptied in sweep k-1
             }
           }
         }

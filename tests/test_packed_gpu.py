@@ -197,7 +197,7 @@ def test_packed_and_whole_word_networks_in_one_plan():
 
 @pytest.mark.parametrize("d", [3, 12, 20, 24])
 def test_packed_tensor_core_kernel(d):
-    """The tensor-core kernel's FP8 operand store built from packed rows."""
+    """The tensor-core kernel's operand store built from packed rows."""
     T = torch()
     n = 180
     net_np = racgen.random_network(30 + d, 0, n, d, 0.6, 0.3)

@@ -73,7 +73,7 @@ def test_tensor_dense_500():
 
 
 def test_fp8_store_built_at_creation():
-    """RAC_LAYOUT_FP8 builds the FP8 operand store when the network is
+    """RAC_LAYOUT_FP8 builds the tensor-core operand store when the network is
     created; the tensor-core kernel then reads it (the other tests build it
     on their first tensor-core call)."""
     n, d = 300, 24
