@@ -41,7 +41,8 @@
 //               the group's relation q into a 16-slot ring of tensor-memory
 //               A tiles (8 columns each), four groups per store wait;
 //   warps 4-19  epilogue: lane quarter warp % 4 and 32 state columns each
-//               (part (warp - 4) / 4), every group;
+//               (part (warp - 4) / 4), every group (parts beyond the running
+//               states idle);
 //   warp 20     lane 0 issues the MMAs (three accumulators of 128 columns)
 //               and commits their completion to the A slots and accumulators;
 //   warp 21     claims items, publishes them through a two-deep queue and
@@ -170,6 +171,12 @@ __device__ __forceinline__ void tc_fence_before() {
 }
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Arrive on an mbarrier for `count` threads at once.
+__device__ __forceinline__ void mbar_arrive_n(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(count)
+               : "memory");
 }
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -438,9 +445,12 @@ __device__ void tc_item(TcSmem &S, const LaunchParams &P, int item, int k, int s
     const int q = warp & 3, part = (warp - kTcEpiWarp0) >> 2;
     const int col0 = 32 * part;             // this warp's state columns
     const bool cols = col0 < ncols;         // warp-uniform
+    // parts without state columns sit the item out; part 0 of each quarter
+    // releases the accumulators for them
+    const uint32_t idle_parts = uint32_t(kTcEpiParts - (ncols + 31) / 32);
     const uint32_t tq = S.tmem_base + (uint32_t(q * 32) << 16) + uint32_t(col0);
-    bool ok = true;
-    for (int mt = 0; mt < 8; ++mt) {
+    bool ok = cols;
+    for (int mt = 0; mt < 8 && cols; ++mt) {
       if (!((active >> mt) & 1u)) continue;
       // constraints of this unit's relation q: presence over the groups g
       const uint32_t pres =
@@ -467,7 +477,7 @@ __device__ void tc_item(TcSmem &S, const LaunchParams &P, int item, int k, int s
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&S.acc_empty[sc]);
+        if (lane == 0) mbar_arrive_n(&S.acc_empty[sc], part == 0 ? 1u + idle_parts : 1u);
         if (here) {
 #pragma unroll
           for (int c = 0; c < 32; ++c) mn[c] = min(mn[c], v[c]);
