@@ -51,12 +51,14 @@ def test_tensor_many_states_vs_oracle(B):
     assert ref[1].max() >= 3
 
 
-def test_tensor_learned_shape_config():
-    """n=1000, d=24, density 0.8, tightness 0.3, 32 assignment states: the
-    tensor path equals kernel (a) bit for bit, and a sample equals the oracle."""
+@pytest.mark.parametrize("seed", range(5))
+def test_tensor_learned_shape_config(seed):
+    """n=1000, d=24, density 0.8, tightness 0.3, 32 assignment states, seeds
+    0-4: the tensor path equals kernel (a) bit for bit, and a sample equals
+    the oracle."""
     n, d = 1000, 24
-    net = racgen.random_network(0, 0, n, d, 0.8, 0.3)
-    doms = np.array([racgen.assignment_state(0, 0, s, n, d) for s in range(32)])
+    net = racgen.random_network(seed, 0, n, d, 0.8, 0.3)
+    doms = np.array([racgen.assignment_state(seed, 0, s, n, d) for s in range(32)])
     a = gpu_enforce(n, d, net.scope, net.rel, doms, 0, shuffle_seed=1)
     b = gpu_enforce(n, d, net.scope, net.rel, doms, TC, shuffle_seed=2)
     assert_same(b, a, "tensor vs bit-packed")
