@@ -75,7 +75,7 @@ typedef int32_t rac_status;
  * device at creation: every relation in both orientations (its rows R[a][.]
  * and its columns R[.][b]), a 32-bit word per row or column, grouped by
  * 32 x 32-variable tile in the order the kernel's MMAs consume them, plus
- * each tile's presence rows: 256 KiB per tile that holds a constraint (135
+ * each tile's presence rows: 256 KiB per tile that holds a constraint (138
  * MB for n = 1000, 528 MB for n = 2000).  The kernel expands each word to the
  * MMA's FP8 (E5M2) operand in tensor memory as it goes.  Without it the
  * first RAC_KERNEL_TENSOR call on the network builds it (an allocation and a
