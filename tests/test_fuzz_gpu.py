@@ -101,3 +101,46 @@ def test_random_configuration(i):
         T.cuda.synchronize()
         got = (from_dev(dout).reshape(B, n), it.cpu().numpy(), st.cpu().numpy())
         assert_same(got, want, what)
+
+
+@pytest.mark.parametrize("i", range(24))
+def test_random_configuration_tensor(i):
+    """The same draws through the tensor-core kernel (RAC_KERNEL_TENSOR) with
+    its operand store built from whole-word or packed rows of any tile
+    height, through rac_enforce, rac_enforce_batch and rac_enforce_host."""
+    rng, n, d, dens, tight, B, flags, cap, rows, ctas, _ = _draw(i)
+    packed = bool(rng.integers(0, 2))
+    entry = str(rng.choice(["enforce", "batch", "host"]))
+    x = racgen.random_network(9000 + i, 0, n, d, dens, tight)
+    doms = _states(rng, 9000 + i, n, d, B)
+    want = oracle_enforce(n, d, x.scope, x.rel, doms, flags=flags, max_sweeps=cap)
+    what = "tensor case %d: n=%d d=%d density %.1f B=%d flags %d cap %d rows %s packed %s %s" % (
+        i, n, d, dens, B, flags, cap, rows, packed, entry)
+    fl = flags | rac.KERNEL_TENSOR
+    T = torch()
+    with rac.Network(n, d, x.scope, x.rel, rows=None if rows is None else int(rows),
+                     packed=packed) as net:
+        if entry == "host":
+            out, it, st = rac.enforce_host(net, doms, max_sweeps=cap, flags=fl)
+            assert_same((out.reshape(B, n), it, st), want, what)
+            return
+        if entry == "enforce":
+            for s in range(B):
+                din = to_dev(doms[s])
+                dout = T.empty_like(din)
+                it = T.empty(1, dtype=T.int32, device="cuda:0")
+                st = T.empty(1, dtype=T.int32, device="cuda:0")
+                rac.enforce(net, din, dout, it, st, max_sweeps=cap, flags=fl)
+                T.cuda.synchronize()
+                got = (from_dev(dout)[None, :], it.cpu().numpy(), st.cpu().numpy())
+                assert_same(got, tuple(a[s:s + 1] for a in want), what)
+            return
+        din = to_dev(doms.reshape(-1))
+        dout = T.empty_like(din)
+        it = T.full((B,), -7, dtype=T.int32, device="cuda:0")
+        st = T.full((B,), -7, dtype=T.int32, device="cuda:0")
+        rac.enforce_batch([net], np.zeros(B, np.int32), np.arange(B, dtype=np.int64) * n, din,
+                          dout, it, st, max_sweeps=cap, flags=fl)
+        T.cuda.synchronize()
+        got = (from_dev(dout).reshape(B, n), it.cpu().numpy(), st.cpu().numpy())
+        assert_same(got, want, what)
